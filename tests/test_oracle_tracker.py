@@ -1,0 +1,199 @@
+"""Pins of the oracle tracker (CPU): Kalman closed forms, gating, assignment, lifecycle."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg
+import scipy.optimize
+import scipy.stats
+
+import synth
+from oracle import network as net
+from oracle import postprocess as pp
+from oracle import tracker as tk
+
+
+def test_gate_constant_is_chi2_95_4dof():
+    assert tk.GATE_CHI2 == pytest.approx(scipy.stats.chi2.ppf(0.95, 4), rel=0, abs=1e-12)
+
+
+def test_predict_without_noise_is_exact():
+    g = np.random.default_rng(1)
+    mean = g.standard_normal(8)
+    A = g.standard_normal((8, 8))
+    cov = A @ A.T
+    m2, c2 = tk.predict(mean, cov, q=np.zeros((8, 8)))
+    np.testing.assert_array_equal(m2[:4], mean[:4] + mean[4:])
+    np.testing.assert_array_equal(m2[4:], mean[4:])
+    np.testing.assert_allclose(c2, tk.F @ cov @ tk.F.T, rtol=0, atol=0)
+
+
+def test_update_with_zero_measurement_noise_returns_measurement():
+    mean, cov = tk.initiate(np.array([100.0, 50.0, 0.4, 120.0]))
+    mean, cov = tk.predict(mean, cov)
+    z = np.array([104.0, 47.0, 0.41, 118.0])
+    m2, c2 = tk.update(mean, cov, z, r=np.zeros((4, 4)))
+    np.testing.assert_allclose(m2[:4], z, rtol=1e-12)
+    np.testing.assert_allclose(c2[:4, :4], 0, atol=1e-9)
+
+
+def test_kalman_gain_matches_inverse_route():
+    g = np.random.default_rng(2)
+    mean, cov = tk.initiate(np.array([300.0, 200.0, 0.45, 90.0]))
+    for _ in range(3):
+        mean, cov = tk.predict(mean, cov)
+        mean, cov = tk.update(mean, cov, tk.H @ mean + g.normal(0, 2, 4) * [1, 1, 0.01, 1])
+    mean, cov = tk.predict(mean, cov)
+    z = tk.H @ mean + np.array([3.0, -2.0, 0.01, 1.5])
+    S = tk.H @ cov @ tk.H.T + tk.measurement_noise(mean[3])
+    K = cov @ tk.H.T @ np.linalg.inv(S)
+    m2, c2 = tk.update(mean, cov, z)
+    np.testing.assert_allclose(m2, mean + K @ (z - tk.H @ mean), rtol=1e-12)
+    np.testing.assert_allclose(c2, (np.eye(8) - K @ tk.H) @ cov, rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(c2, c2.T, rtol=0, atol=1e-9)
+    assert np.all(np.linalg.eigvalsh(c2) > 0)
+    y = z - tk.H @ mean
+    assert tk.mahalanobis2(mean, cov, z) == pytest.approx(float(y @ np.linalg.solve(S, y)), rel=1e-12)
+
+
+def _dare_axes(h):
+    Fa = np.array([[1.0, 1.0], [0.0, 1.0]])
+    Ha = np.array([[1.0, 0.0]])
+    sp, sv = tk.STD_POS * h, tk.STD_VEL * h
+    out = []
+    for ax, (qp, qv), r in [(0, (sp, sv), sp), (1, (sp, sv), sp), (2, (1e-2, 1e-5), 1e-1), (3, (sp, sv), sp)]:
+        Q = np.diag([qp ** 2, qv ** 2])
+        R = np.array([[r ** 2]])
+        out.append((ax, scipy.linalg.solve_discrete_are(Fa.T, Ha.T, Q, R)))
+    return out
+
+
+def test_steady_state_covariance_solves_dare():
+    """With h frozen each axis is a 2-state constant-velocity filter; the prior covariance
+    converges to the discrete algebraic Riccati solution (cx, cy, h axes: fast)."""
+    h = 150.0
+    mean, cov = tk.initiate(np.array([100.0, 200.0, 0.4, h]))
+    g = np.random.default_rng(5)
+    for _ in range(300):
+        mean, cov = tk.predict(mean, cov)
+        prior = cov.copy()
+        z = np.array([mean[0] + g.normal(0, 3), mean[1] + g.normal(0, 3), 0.4, h])
+        mean, cov = tk.update(mean, cov, z)
+        assert mean[3] == h
+    for ax, X in _dare_axes(h):
+        if ax != 2:       # the aspect axis (Q/R ~ 1e-8) needs ~2e4 steps; covered by the fixed-point test
+            np.testing.assert_allclose(prior[np.ix_([ax, ax + 4], [ax, ax + 4])], X, rtol=1e-10)
+
+
+def test_dare_solution_is_a_fixed_point_of_update_then_predict():
+    h = 150.0
+    P = np.zeros((8, 8))
+    for ax, X in _dare_axes(h):
+        P[np.ix_([ax, ax + 4], [ax, ax + 4])] = X
+    mean = np.array([100.0, 200.0, 0.4, h, 0, 0, 0, 0])
+    m2, c2 = tk.update(mean, P, np.array([101.0, 199.0, 0.4, h]))
+    m3, c3 = tk.predict(m2, c2)
+    assert m3[3] == h
+    np.testing.assert_allclose(c3, P, rtol=1e-12, atol=1e-12 * np.abs(P).max())
+    for ax, X in _dare_axes(h):
+        blk = c3[np.ix_([ax, ax + 4], [ax, ax + 4])]
+        assert np.max(np.abs(blk - X) / np.abs(X)) < 1e-11
+
+
+def _brute(cost):
+    n, m = cost.shape
+    best, arg = math.inf, None
+    for perm in itertools.permutations(range(m), n):
+        c = sum(cost[i, perm[i]] for i in range(n))
+        if c < best - 1e-12:
+            best, arg = c, perm
+    return best, arg
+
+
+@pytest.mark.parametrize("n,m", [(1, 1), (2, 2), (3, 5), (5, 5), (4, 7), (6, 8), (8, 8)])
+def test_hungarian_matches_brute_force(n, m):
+    g = np.random.default_rng(n * 10 + m)
+    for _ in range(5):
+        cost = g.uniform(0, 1, (n, m))
+        col = tk.hungarian(cost)
+        best, arg = _brute(cost)
+        assert sum(cost[i, col[i]] for i in range(n)) == pytest.approx(best, abs=1e-12)
+        assert tuple(col) == arg       # continuous costs: the optimum is unique
+        assert len(set(col.tolist())) == n
+
+
+def test_hungarian_matches_scipy_large():
+    g = np.random.default_rng(9)
+    for n, m in [(200, 200), (50, 120)]:
+        cost = g.uniform(0, 1, (n, m))
+        col = tk.hungarian(cost)
+        r, c = scipy.optimize.linear_sum_assignment(cost)
+        assert cost[np.arange(n), col].sum() == pytest.approx(cost[r, c].sum(), abs=1e-9)
+
+
+def test_hungarian_ties_prefer_low_columns():
+    assert list(tk.hungarian(np.zeros((4, 4)))) == [0, 1, 2, 3]
+    assert list(tk.hungarian(np.full((2, 5), 1e5))) == [0, 1]
+
+
+def test_assign_transposes_when_more_tracks():
+    cost = np.array([[0.9, 0.1], [0.2, 0.8], [0.05, 0.95]])
+    assert tk.assign(cost) == [(0, 1), (2, 0)]
+
+
+def det_row(box, emb, conf=0.9):
+    r = np.zeros(518)
+    r[:4] = box
+    r[4] = conf
+    r[6:] = emb / np.linalg.norm(emb)
+    return r
+
+
+def test_lifecycle_birth_lost_and_removal():
+    g = np.random.default_rng(4)
+    e1, e2 = g.standard_normal(512), g.standard_normal(512)
+    T = tk.Tracker()
+    out = T.step(np.stack([det_row([100, 100, 140, 220], e1), det_row([500, 300, 560, 450], e2)]))
+    assert [(i, s) for i, s, _ in out] == [(1, tk.TRACKED), (2, tk.TRACKED)]
+    out = T.step(np.stack([det_row([101, 101, 141, 221], e1)]))
+    assert [(i, s) for i, s, _ in out] == [(1, tk.TRACKED), (2, tk.LOST)]
+    for f in range(29):
+        out = T.step(np.stack([det_row([101, 101, 141, 221], e1)]))
+    assert [(i, s) for i, s, _ in out] == [(1, tk.TRACKED), (2, tk.LOST)]   # lost for 30 frames: kept
+    out = T.step(np.stack([det_row([101, 101, 141, 221], e1)]))
+    assert [(i, s) for i, s, _ in out] == [(1, tk.TRACKED)]                 # 31 > 30: removed
+
+
+def test_cost_and_gate_rejections_give_births():
+    g = np.random.default_rng(6)
+    e1 = g.standard_normal(512)
+    T = tk.Tracker()
+    T.step(np.stack([det_row([100, 100, 140, 220], e1)]))
+    # same place, unrelated appearance: cosine cost ~1 > 0.7 -> rejected, new id
+    out = T.step(np.stack([det_row([100, 100, 140, 220], g.standard_normal(512))]))
+    assert [(i, s) for i, s, _ in out] == [(1, tk.LOST), (2, tk.TRACKED)]
+    # same appearance as id 1, far away: gated -> rejected, new id
+    out = T.step(np.stack([det_row([900, 600, 940, 720], e1)]))
+    assert [i for i, s, _ in out if s == tk.TRACKED] == [3]
+    assert T.last["d2"][0, 0] > tk.GATE_CHI2
+
+
+def test_planted_objects_keep_their_ids():
+    """Every detected planted object stays with one track id for the whole clip."""
+    r, nw, nh, px, py = net.letterbox_geometry(1920, 1080, 1088, 608)
+    clip = synth.PlantedClip(3, 8, 40, 1088, 608, pp.anchors(), pp.STRIDES, r, px, py)
+    T = tk.Tracker()
+    owner = {}
+    for t in range(40):
+        dets, embs, truth = clip.frame(t)
+        rows = pp.postprocess_frame(dets, embs, r, px, py)["rows"]
+        T.step(rows)
+        for (o, cx, cy, w, h) in truth:
+            d = np.hypot((rows[:, 0] + rows[:, 2]) / 2 - cx, (rows[:, 1] + rows[:, 3]) / 2 - cy)
+            j = int(np.argmin(d))
+            if d[j] > 1e-3:
+                continue              # suppressed by an overlapping object in NMS
+            tid = T.last["det_track"][j]
+            assert owner.setdefault(o, tid) == tid, "identity switch"
+    assert len(owner) == 8
