@@ -1,0 +1,189 @@
+/*
+ * libjde: JDE detect-and-track on one GB300 (sm_103a), C ABI.
+ *
+ * The operation follows the tracking-by-detection pipeline of
+ * "Faster object tracking pipeline for real time tracking" (Soni, Shah, Vyas):
+ * a Joint Detection and Embedding network (Sec. 3.1: DarkNet-53 backbone, FPN,
+ * predictions from three layers, YOLOv3-style detection) turns a batch of
+ * frames into per-frame detection rows of 518 values (Appendix A, first item:
+ * 4 location values, object confidence, class score, 512-d embedding), which
+ * are filtered by confidence, non-max suppressed (Appendix A, items 2-3) and
+ * then associated to tracks per video stream with a Kalman filter, cosine
+ * cost, motion gating, Hungarian assignment and a track lifecycle (Sec. 3
+ * "Location Estimation" / "Association", Appendix A items 4-9).
+ *
+ * Conventions for every call:
+ *  - Every call returns a jde_status; nothing throws, exits or traps.  On an
+ *    error the handle keeps a message for jde_last_error().
+ *  - "device" pointers are CUDA global-memory pointers on the handle's device;
+ *    "host" pointers are ordinary (preferably pinned) host memory.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *    with device outputs are asynchronous on that stream; calls with host
+ *    outputs synchronise it before returning.
+ *  - The caller owns every buffer it passes; the library owns the weights,
+ *    activations and per-stream tracker state inside the handle.
+ *  - One handle is used by one host thread at a time.
+ */
+#ifndef JDE_H
+#define JDE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct jde_handle jde_handle;
+
+typedef enum {
+  JDE_OK = 0,
+  JDE_ERR_INVALID_ARG = 1, /* a size, pointer or option is out of range */
+  JDE_ERR_OOM = 2,         /* device allocation failed */
+  JDE_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+  JDE_ERR_CAPACITY = 4,    /* an output or state buffer is too small; counts hold the true sizes */
+  JDE_ERR_ADMISSION = 5,   /* a stream slot cannot be granted within the HBM budget */
+  JDE_ERR_TIMEOUT = 6,     /* a device-side bounded wait gave up (kernel error word) */
+  JDE_ERR_NOT_FOUND = 7,   /* unknown stream id or tensor id */
+  JDE_ERR_WEIGHTS = 8,     /* weights blob malformed or does not match the layer table */
+  JDE_ERR_UNSUPPORTED = 9  /* option not built into this library */
+} jde_status;
+
+typedef enum { JDE_FP32 = 0, JDE_BF16 = 1 } jde_precision;
+
+/* Track states reported by jde_track_step (Appendix A: active / lost). */
+enum { JDE_TRACK_TRACKED = 1, JDE_TRACK_LOST = 2 };
+
+/* Values a detection row carries (Appendix A: [n, num_detections, 518]). */
+#define JDE_ROW 518
+#define JDE_EMB 512
+#define JDE_NUM_LAYERS 78
+
+typedef struct {
+  int precision;        /* jde_precision of the convolutions */
+  int max_batch;        /* most frames per jde_detect_batch / jde_forward call */
+  int max_in_w;         /* largest model input width  (multiple of 32) */
+  int max_in_h;         /* largest model input height (multiple of 32) */
+  int max_src_w;        /* largest source frame width  (for host->device staging) */
+  int max_src_h;        /* largest source frame height */
+  int max_cand;         /* K_max: candidates kept per frame after the confidence filter, <= 4096 */
+  float conf_thresh;    /* keep conf >= conf_thresh (Appendix A item 2), default 0.5 */
+  float nms_iou;        /* suppress IoU > nms_iou (Appendix A item 3), default 0.4 */
+  float assign_thresh;  /* reject assigned pairs with cost > assign_thresh (item 7), default 0.7 */
+  double gate_chi2;     /* gate squared Mahalanobis distance > gate_chi2 (item 6), default 9.487729036781154 */
+  int lost_max_frames;  /* remove tracks lost for more frames (item 9), default 30 */
+  float emb_momentum;   /* gallery update e <- norm(m e + (1-m) d), default 0.9 */
+  int max_streams;      /* tracker state slots (video streams), default 64 */
+  int max_tracks;       /* tracks per stream, default 1024 */
+  int max_track_dets;   /* detections per frame entering the tracker, default 1024 */
+  int device;           /* CUDA device ordinal */
+} jde_config;
+
+/* One layer of the network as this library builds it (for the weights blob). */
+typedef struct {
+  int cin, cout, k, stride;
+  int has_bn;        /* 1: BN statistics follow the weights in the blob, 0: a bias follows */
+  int res_nblocks;   /* block count of the residual stage if the conv closes a residual branch, else 0 */
+} jde_layer_desc;
+
+/* Detection output of jde_detect_batch / jde_postprocess for n frames.
+ * rows[f][i][0..517] = x1, y1, x2, y2 (source-frame pixels), conf, cls, unit embedding[512]
+ * in kept order (confidence descending, canonical anchor index ascending).
+ * count[f] is the number of kept detections of frame f (it may exceed `cap`,
+ * in which case only `cap` rows were written).  anchor_index (optional) holds
+ * the canonical anchor index of each row: off_s + (a H_s + y) W_s + x with the
+ * heads ordered by stride 32, 16, 8. */
+typedef struct {
+  float* rows;            /* [n][cap][518] */
+  int32_t* count;         /* [n] */
+  int32_t* anchor_index;  /* [n][cap] or NULL */
+  int cap;
+  int on_device;          /* 1: all pointers are device pointers, 0: host pointers */
+} jde_dets;
+
+/* Track output of jde_track_step for n streams: the tracks alive after the
+ * step, in track order (creation order).  box is the Kalman state mean as
+ * x1, y1, x2, y2 in source-frame pixels; det is the row of the frame's
+ * detection assigned to the track this step, or -1. */
+typedef struct {
+  int64_t* id;      /* [n][cap] */
+  float* box;       /* [n][cap][4] */
+  int32_t* state;   /* [n][cap] JDE_TRACK_* */
+  int32_t* det;     /* [n][cap] */
+  int32_t* count;   /* [n] */
+  int cap;
+  int on_device;
+} jde_tracks;
+
+/* Fill *cfg with the defaults listed above (precision BF16, max_batch 16, 1088x608 from 1920x1080). */
+void jde_default_config(jde_config* cfg);
+
+/* Copy the layer table (JDE_NUM_LAYERS entries, weights-blob order) into out[0..cap).
+ * Returns the number of layers.  Pure host code; needs no GPU. */
+int jde_layer_table(jde_layer_desc* out, int cap);
+
+/* Create a handle on cfg->device.  `weights` (host, nbytes) is a blob:
+ *   "JDEW", u32 version = 1, u32 n_layers, u32 0, then per layer
+ *   u32 cin, cout, k, stride, flags (1 = BN, 2 = bias), 0, 0, 0 and f32
+ *   W[cout][cin][k][k] followed by gamma, beta, mean, var [cout] (BN, eps 1e-5)
+ *   or bias[cout].
+ * The blob is copied; BN is folded and weights are packed on the device.
+ * Errors: JDE_ERR_WEIGHTS if the blob does not match jde_layer_table,
+ * JDE_ERR_OOM, JDE_ERR_CUDA, JDE_ERR_INVALID_ARG. */
+jde_status jde_create(const jde_config* cfg, const void* weights, size_t nbytes, jde_handle** out);
+
+/* Release everything the handle owns.  jde_destroy(NULL) is a no-op. */
+void jde_destroy(jde_handle* h);
+
+/* Message of the last failed call on h (or of the last failed jde_create when h is NULL). */
+const char* jde_last_error(jde_handle* h);
+
+/* Letterbox + network forward (Sec. 3.1) for n frames of src_w x src_h uint8
+ * RGB (HWC, rows tightly packed, frames contiguous) into the handle's head
+ * tensors at model input in_w x in_h.  `frames` is a device pointer when
+ * on_device, else host memory copied inside the call on `stream`.
+ * Letterbox: r = min(in_w/src_w, in_h/src_h), resized size floor(src r + 0.5),
+ * centred, bilinear with half-pixel centres, /255, pad value 0.5. */
+jde_status jde_forward(jde_handle* h, const uint8_t* frames, int n, int src_w, int src_h,
+                       int in_w, int in_h, int on_device, void* stream);
+
+/* Decode, confidence filter, NMS and embedding gather/L2-normalise (Sec. 3.2,
+ * Appendix A items 1-3) for n frames.  heads[0..2] are the detection maps of
+ * strides 32, 16, 8 ([n][H_s][W_s][24] f32, channels 6a..6a+5 = tx, ty, tw, th,
+ * t_obj, t_cls of anchor a), heads[3..5] the embedding maps
+ * ([n][H_s][W_s][512] f32), all device pointers; NULL heads means the
+ * handle's own heads from the last jde_forward.  Boxes are mapped back to
+ * src_w x src_h frame pixels. */
+jde_status jde_postprocess(jde_handle* h, const float* const* heads, int n, int in_w, int in_h,
+                           int src_w, int src_h, jde_dets* out, void* stream);
+
+/* jde_forward followed by jde_postprocess on the handle's heads. */
+jde_status jde_detect_batch(jde_handle* h, const uint8_t* frames, int n, int src_w, int src_h,
+                            int in_w, int in_h, int on_device, jde_dets* out, void* stream);
+
+/* One tracker step (Appendix A items 4-9) for n streams: stream_ids[i] (host
+ * array, distinct ids in [0, max_streams)) consumes frame i of `dets` (device
+ * rows as written by jde_postprocess).  Tracker state stays on the device. */
+jde_status jde_track_step(jde_handle* h, int n, const int32_t* stream_ids, const jde_dets* dets,
+                          jde_tracks* out, void* stream);
+
+/* Forget all tracks of a stream and restart its ids at 1 (asynchronous on stream). */
+jde_status jde_stream_reset(jde_handle* h, int stream_id, void* stream);
+
+/* Copy an internal tensor to `dst` (device pointer, dst_bytes capacity) for
+ * inspection: id 0..77 = output of conv layer id (after its fused epilogue:
+ * bias, leaky-ReLU, residual add), 100 = letterboxed input, 101 = stem im2col
+ * rows (BF16 only).  dims receives {n, h, w, c} of the unpadded tensor, *dtype
+ * 0 = f32, 1 = bf16; the copy is the unpadded tensor in NHWC order.  dst NULL
+ * only reports dims and dtype. */
+jde_status jde_get_tensor(jde_handle* h, int id, void* dst, size_t dst_bytes, int* dims, int* dtype,
+                          void* stream);
+
+/* Device error word accumulated by the kernels (bit 0: bounded wait timed out,
+ * bit 1: capacity overflow); reading it synchronises `stream` and clears it. */
+jde_status jde_kernel_errors(jde_handle* h, int* word, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JDE_H */

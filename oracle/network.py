@@ -145,7 +145,8 @@ def forward(x: np.ndarray, layers, keep_all: bool = False):
     ``(dets, embs, acts)`` where ``dets[s]`` is the ``[N, H_s, W_s, 24]``
     detection map and ``embs[s]`` the ``[N, H_s, W_s, 512]`` embedding map for
     strides 32, 16, 8, and ``acts`` the output of every conv in layer order
-    when ``keep_all`` (else empty).
+    when ``keep_all`` (else empty); for a conv that closes a residual branch
+    the recorded output is the block output ``x + branch``.
     """
     specs = layer_specs()
     if len(layers) != len(specs):
@@ -156,12 +157,14 @@ def forward(x: np.ndarray, layers, keep_all: bool = False):
     it = iter(layers)
     acts = []
 
-    def conv(inp, linear=False):
+    def conv(inp, linear=False, res=None):
         L = next(it)
         w, b = fold_bn(L)
         y = conv2d(inp, w, b, L["stride"])
         if not linear:
             y = leaky(y)
+        if res is not None:
+            y = res + y
         if keep_all:
             acts.append(y)
         return y
@@ -171,7 +174,7 @@ def forward(x: np.ndarray, layers, keep_all: bool = False):
     for c, nb in STAGES:
         x = conv(x)
         for _ in range(nb):
-            x = x + conv(conv(x))
+            x = conv(conv(x), res=x)
         feats[c] = x
     skips = {512: feats[512], 256: feats[256]}
     dets, embs = [], []

@@ -1,0 +1,401 @@
+// BF16 implicit-GEMM convolution on the 5th-generation tensor cores (tcgen05).
+//
+// GEMM view: D[M = pixels][N = out channels] = sum_k A[m][k] B[n][k], K = (tap, ci).
+// One CTA computes a 128 x BN tile with the f32 accumulator in TMEM:
+//   * warp 0 / lane 0 streams A and B k-blocks (BKC channels of one tap) into a
+//     STAGES-deep shared-memory ring with TMA (cp.async.bulk.tensor), 128- or
+//     64-byte swizzled, completion tracked by mbarriers;
+//   * warp 1 / lane 0 issues tcgen05.mma (M=128, N=BN, K=16) per k-block and
+//     frees the ring slot with tcgen05.commit;
+//   * all four warps then read the accumulator rows (TMEM lane = tile row)
+//     with tcgen05.ld and run the fused epilogue: + bias (BN folded),
+//     leaky-ReLU, + residual, bf16/f32 store, optional 2x2 upsample write into
+//     a concat slice.
+// Activation addressing (implicit im2col) needs no gather:
+//   * stride 1 ("flat"): activations keep a 1-pixel zero halo, so for tap
+//     (ky, kx) the A rows of output pixels m0..m0+127 (flattened over the
+//     padded image) are input rows m0 + (ky-1)*Wp + (kx-1): one 2-D TMA box.
+//     Rows that fall on the halo are computed and discarded.
+//   * stride 2 ("patch"): the padded input is split into its four
+//     (row parity, column parity) sub-lattices, each described by its own 4-D
+//     tensor map; tap (ky, kx) of a TH x TW output patch is a dense box of
+//     sub-lattice (ky&1, kx&1) at offset (ky>>1, kx>>1).
+// Every wait is bounded; on a timeout the CTA flags the error word, skips
+// its stores, releases TMEM and exits.
+#include <stdio.h>
+
+#include "internal.h"
+
+namespace {
+
+struct TcArgs {
+  int mode, k, cin_blocks, kt_total;
+  int M_total, Hp, Wp;
+  int TW, TH, tiles_x, tiles_y, n_tiles;
+  ConvSpec c;
+};
+
+template <int BN, int BKC, int STAGES>
+struct TcCfg {
+  static constexpr int A_BYTES = 128 * BKC * 2;
+  static constexpr int B_BYTES = BN * BKC * 2;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+  static constexpr uint32_t LAYOUT = BKC == 64 ? 2u : 4u;     // SW128 : SW64
+  static constexpr uint32_t SBO = 8 * BKC * 2;                 // bytes per 8-row group
+  static constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
+};
+
+__device__ __forceinline__ void store_chunk(const ConvSpec& c, int n, int y, int x, int ch0, int nvalid,
+                                            const float (&v)[32]) {
+  const int reps = c.upsample ? 4 : 1;
+  for (int q = 0; q < reps; ++q) {
+    const int yy = c.upsample ? 2 * y + (q >> 1) : y;
+    const int xx = c.upsample ? 2 * x + (q & 1) : x;
+    const size_t off = tview_off(c.out, n, yy, xx) + ch0;
+    if (c.out.dtype == 1) {
+      __nv_bfloat16* o = static_cast<__nv_bfloat16*>(c.out.ptr) + off;
+      if (nvalid == 32) {
+        uint32_t packed[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+          packed[j] = *reinterpret_cast<uint32_t*>(&h2);
+        }
+        uint4* o4 = reinterpret_cast<uint4*>(o);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          o4[j] = make_uint4(packed[4 * j], packed[4 * j + 1], packed[4 * j + 2], packed[4 * j + 3]);
+      } else {
+        for (int j = 0; j < nvalid; ++j) o[j] = __float2bfloat16_rn(v[j]);
+      }
+    } else {
+      float* o = static_cast<float*>(c.out.ptr) + off;
+      if ((nvalid & 3) == 0) {
+        float4* o4 = reinterpret_cast<float4*>(o);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (4 * j < nvalid) o4[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+      } else {
+        for (int j = 0; j < nvalid; ++j) o[j] = v[j];
+      }
+    }
+  }
+}
+
+template <int BN, int BKC, int STAGES>
+__global__ void __launch_bounds__(128, 1) conv_tc_kernel(const __grid_constant__ TcPlan plan, const TcArgs a) {
+  using Cfg = TcCfg<BN, BKC, STAGES>;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ int s_abort;
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * Cfg::A_BYTES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * Cfg::B_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* done = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const ConvSpec& c = a.c;
+
+  // tile coordinates: consecutive CTAs share the activation tile (n fastest)
+  const int n_tile = blockIdx.x % a.n_tiles;
+  const int m_tile = blockIdx.x / a.n_tiles;
+  const int n0 = n_tile * BN;
+  int m0 = 0, img = 0, oy0 = 0, ox0 = 0;
+  if (a.mode == 0) {
+    m0 = m_tile * 128;
+  } else {
+    const int per_img = a.tiles_x * a.tiles_y;
+    img = m_tile / per_img;
+    const int r = m_tile % per_img;
+    oy0 = (r / a.tiles_x) * a.TH;
+    ox0 = (r % a.tiles_x) * a.TW;
+  }
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    fence_barrier_init();
+    s_abort = 0;
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, Cfg::TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    for (int i = 0; i < 4; ++i)
+      if (a.mode == 1 || i == 0) tma_prefetch(&plan.a[i]);
+    tma_prefetch(&plan.b);
+    for (int kt = 0; kt < a.kt_total; ++kt) {
+      const int s = kt % STAGES;
+      const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
+      if (kt >= STAGES && !mbar_wait(&empty[s], ph ^ 1u)) {
+        flag_error(c.err, KERR_TIMEOUT);
+        atomicExch(&s_abort, 1);
+        break;
+      }
+      const int tap = kt / a.cin_blocks, cb = kt % a.cin_blocks;
+      const int ky = tap / a.k, kx = tap % a.k;
+      mbar_expect_tx(&full[s], Cfg::STAGE_BYTES);
+      uint8_t* dA = sA + s * Cfg::A_BYTES;
+      if (a.mode == 0) {
+        const int shift = a.k == 3 ? (ky - 1) * a.Wp + (kx - 1) : 0;
+        tma_load_2d(dA, &plan.a[0], &full[s], cb * BKC, m0 + shift);
+      } else {
+        tma_load_4d(dA, &plan.a[(ky & 1) * 2 + (kx & 1)], &full[s], cb * BKC, ox0 + (kx >> 1), oy0 + (ky >> 1),
+                    img);
+      }
+      tma_load_2d(sB + s * Cfg::B_BYTES, &plan.b, &full[s], kt * BKC, n0);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    constexpr uint32_t idesc = idesc_bf16(128, BN);
+    for (int kt = 0; kt < a.kt_total; ++kt) {
+      const int s = kt % STAGES;
+      const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
+      if (!mbar_wait(&full[s], ph)) {
+        flag_error(c.err, KERR_TIMEOUT);
+        atomicExch(&s_abort, 1);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t a_base = smem_u32(sA + s * Cfg::A_BYTES);
+      const uint32_t b_base = smem_u32(sB + s * Cfg::B_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < BKC / 16; ++kk) {
+        const uint64_t ad = smem_desc(a_base + kk * 32, Cfg::SBO, Cfg::LAYOUT);
+        const uint64_t bd = smem_desc(b_base + kk * 32, Cfg::SBO, Cfg::LAYOUT);
+        umma_bf16(tmem, ad, bd, idesc, (kt | kk) != 0 ? 1u : 0u);
+      }
+      umma_commit(&empty[s]);
+    }
+    umma_commit(done);
+  }
+  __syncwarp();
+
+  // ---------------- epilogue: TMEM -> registers -> global
+  const bool ok = mbar_wait(done, 0);
+  if (!ok) flag_error(c.err, KERR_TIMEOUT);
+  tc_fence_after();
+  const int row = warp * 32 + lane;
+  int n = 0, y = 0, x = 0;
+  bool valid;
+  if (a.mode == 0) {
+    const int m = m0 + row;
+    const int plane = a.Hp * a.Wp;
+    n = m / plane;
+    const int r = m % plane;
+    y = r / a.Wp - 1;
+    x = r % a.Wp - 1;
+    valid = m < a.M_total && y >= 0 && y < c.Ho && x >= 0 && x < c.Wo;
+  } else {
+    n = img;
+    y = oy0 + row / a.TW;
+    x = ox0 + row % a.TW;
+    valid = y < c.Ho && x < c.Wo;
+  }
+  if (!ok || *((volatile int*)&s_abort)) valid = false;
+
+#pragma unroll 1
+  for (int c0 = 0; c0 < BN; c0 += 32) {
+    uint32_t r[32];
+    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+    tmem_ld_wait();
+    const int ch0 = n0 + c0;
+    if (valid && ch0 < c.cout) {
+      const int nvalid = min(32, c.cout - ch0);
+      float v[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        float t = __uint_as_float(r[j]) + c.bias[ch0 + j];
+        v[j] = c.act ? leaky01(t) : t;
+      }
+      if (c.res.ptr) {
+        const __nv_bfloat16* rp = static_cast<const __nv_bfloat16*>(c.res.ptr) + tview_off(c.res, n, y, x) + ch0;
+        if (nvalid == 32) {
+          const uint4* r4 = reinterpret_cast<const uint4*>(rp);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            uint4 q = r4[j];
+            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162*>(&w[e]);
+              float2 f = __bfloat1622float2(h2);
+              v[8 * j + 2 * e] += f.x;
+              v[8 * j + 2 * e + 1] += f.y;
+            }
+          }
+        } else {
+          for (int j = 0; j < nvalid; ++j) v[j] += __bfloat162float(rp[j]);
+        }
+      }
+      store_chunk(c, n, y, x, ch0, nvalid, v);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, Cfg::TMEM_COLS);
+}
+
+// ----------------------------------------------------------------------------- host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+bool encode(CUtensorMap* m, int rank, void* base, const cuuint64_t* dims, const cuuint64_t* strides_bytes,
+            const cuuint32_t* box, int bkc) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, base, dims, strides_bytes, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, bkc == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int BN, int BKC, int STAGES>
+cudaError_t launch_cfg(const TcPlan& p, const TcArgs& a, cudaStream_t st) {
+  using Cfg = TcCfg<BN, BKC, STAGES>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<BN, BKC, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Cfg::SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  conv_tc_kernel<BN, BKC, STAGES><<<p.m_tiles * p.n_tiles, 128, Cfg::SMEM, st>>>(p, a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int conv_tc_pick_bn(int cout) {
+  if (cout <= 32) return 32;
+  if (cout <= 64) return 64;
+  return 128;
+}
+
+bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const __nv_bfloat16* w, int cout_pad, int bn, char* msg,
+                  size_t msg_len) {
+  plan = TcPlan();
+  plan.spec = c;
+  const int bkc = (c.cin % 64 == 0) ? 64 : (c.cin % 32 == 0 ? 32 : 0);
+  if (!bkc || c.in.dtype != 1 || c.in.pad != 1 || !(c.k == 1 || c.k == 3) || !(c.stride == 1 || c.stride == 2) ||
+      (c.stride == 2 && c.k != 3) || (bn != 32 && bn != 64 && bn != 128 && bn != 256) || cout_pad % bn) {
+    snprintf(msg, msg_len, "tensor-core conv: unsupported shape cin=%d k=%d s=%d bn=%d", c.cin, c.k, c.stride, bn);
+    return false;
+  }
+  plan.bn = bn;
+  plan.bkc = bkc;
+  plan.cin_blocks = c.cin / bkc;
+  plan.kt_total = c.k * c.k * plan.cin_blocks;
+  plan.n_tiles = cout_pad / bn;
+  const int K = c.k * c.k * c.cin;
+  const int Hp = c.in.h + 2, Wp = c.in.w + 2;
+  plan.Hp = Hp;
+  plan.Wp = Wp;
+  void* base = c.in.ptr;
+  bool ok = true;
+  if (c.stride == 1) {
+    plan.mode = 0;
+    plan.M_total = c.in.n * Hp * Wp;
+    plan.m_tiles = (plan.M_total + 127) / 128;
+    cuuint64_t dims[2] = {(cuuint64_t)c.cin, (cuuint64_t)plan.M_total};
+    cuuint64_t strides[1] = {(cuuint64_t)c.in.pixstride * 2};
+    cuuint32_t box[2] = {(cuuint32_t)bkc, 128};
+    ok &= encode(&plan.a[0], 2, base, dims, strides, box, bkc);
+  } else {
+    plan.mode = 1;
+    if ((c.in.h & 1) || (c.in.w & 1)) {
+      snprintf(msg, msg_len, "tensor-core conv: stride-2 input must have even size");
+      return false;
+    }
+    // output patch shape: 128 pixels, widest tile that keeps the waste lowest
+    int best_tw = 128, best_cost = 1 << 30;
+    for (int tw = 8; tw <= 128; tw *= 2) {
+      const int th = 128 / tw;
+      const int cost = ((c.Wo + tw - 1) / tw) * tw * ((c.Ho + th - 1) / th) * th;
+      if (cost < best_cost) best_cost = cost, best_tw = tw;
+    }
+    plan.TW = best_tw;
+    plan.TH = 128 / best_tw;
+    plan.tiles_x = (c.Wo + plan.TW - 1) / plan.TW;
+    plan.tiles_y = (c.Ho + plan.TH - 1) / plan.TH;
+    plan.m_tiles = c.in.n * plan.tiles_x * plan.tiles_y;
+    for (int py = 0; py < 2; ++py)
+      for (int px = 0; px < 2; ++px) {
+        void* pb = static_cast<__nv_bfloat16*>(base) + ((size_t)py * Wp + px) * c.in.pixstride;
+        cuuint64_t dims[4] = {(cuuint64_t)c.cin, (cuuint64_t)(Wp / 2), (cuuint64_t)(Hp / 2), (cuuint64_t)c.in.n};
+        cuuint64_t strides[3] = {(cuuint64_t)2 * c.in.pixstride * 2, (cuuint64_t)2 * Wp * c.in.pixstride * 2,
+                                 (cuuint64_t)Hp * Wp * c.in.pixstride * 2};
+        cuuint32_t box[4] = {(cuuint32_t)bkc, (cuuint32_t)plan.TW, (cuuint32_t)plan.TH, 1};
+        ok &= encode(&plan.a[py * 2 + px], 4, pb, dims, strides, box, bkc);
+      }
+  }
+  {
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)cout_pad};
+    cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+    cuuint32_t box[2] = {(cuuint32_t)bkc, (cuuint32_t)bn};
+    ok &= encode(&plan.b, 2, const_cast<__nv_bfloat16*>(w), dims, strides, box, bkc);
+  }
+  if (!ok) {
+    snprintf(msg, msg_len, "cuTensorMapEncodeTiled failed (cin=%d k=%d s=%d)", c.cin, c.k, c.stride);
+    return false;
+  }
+  return true;
+}
+
+cudaError_t conv_tc_launch(const TcPlan& p, cudaStream_t st) {
+  TcArgs a;
+  a.mode = p.mode;
+  a.k = p.spec.k;
+  a.cin_blocks = p.cin_blocks;
+  a.kt_total = p.kt_total;
+  a.M_total = p.M_total;
+  a.Hp = p.Hp;
+  a.Wp = p.Wp;
+  a.TW = p.TW;
+  a.TH = p.TH;
+  a.tiles_x = p.tiles_x;
+  a.tiles_y = p.tiles_y;
+  a.n_tiles = p.n_tiles;
+  a.c = p.spec;
+  if (p.bkc == 64) {
+    switch (p.bn) {
+      case 32: return launch_cfg<32, 64, 4>(p, a, st);
+      case 64: return launch_cfg<64, 64, 4>(p, a, st);
+      case 128: return launch_cfg<128, 64, 3>(p, a, st);
+      case 256: return launch_cfg<256, 64, 3>(p, a, st);
+    }
+  } else {
+    switch (p.bn) {
+      case 32: return launch_cfg<32, 32, 4>(p, a, st);
+      case 64: return launch_cfg<64, 32, 4>(p, a, st);
+      case 128: return launch_cfg<128, 32, 4>(p, a, st);
+      case 256: return launch_cfg<256, 32, 4>(p, a, st);
+    }
+  }
+  return cudaErrorInvalidValue;
+}

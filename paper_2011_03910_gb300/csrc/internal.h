@@ -1,0 +1,83 @@
+// Internal interfaces between the translation units of libjde.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+// One convolution launch: out = act(conv(in, W) + bias) (+ res), optionally
+// written 2x2-replicated (nearest upsample) into a concat slice.
+struct ConvSpec {
+  int k, stride, cin, cout;
+  TView in, out, res;   // res.ptr == nullptr: no residual
+  int Ho, Wo;           // conv output size (before any upsample)
+  int act;              // 1: leaky-ReLU(0.1), 0: linear
+  int upsample;         // 1: write each output pixel to a 2x2 block of `out`
+  const float* bias;    // [cout_pad] f32
+  int* err;
+};
+
+// SIMT f32 path: weights [K_pad16][cout_pad64] f32, K = (ky*k + kx)*cin + ci.
+void conv_simt_launch(const ConvSpec& c, const float* w_kn, int cout_pad64, cudaStream_t st);
+
+// tcgen05 bf16 path.  Weights [cout_pad][K] bf16 (K-major), K = (ky*k + kx)*cin + ci.
+struct TcPlan {
+  alignas(64) CUtensorMap a[4];  // activations: flat 2-D map, or 4 stride-2 phase maps
+  alignas(64) CUtensorMap b;     // weights
+  int mode;                      // 0 flat (stride 1 over the padded pixel array), 1 patch (stride 2)
+  int bn, bkc;
+  int kt_total, cin_blocks;
+  int m_tiles, n_tiles;
+  int M_total, Hp, Wp;
+  int TW, TH, tiles_x, tiles_y;
+  ConvSpec spec;
+};
+// Fill plan (tensor maps and grid) for a conv whose input is a padded bf16
+// view and whose weights are w ([cout_pad][K] bf16).  Returns false with a
+// message if the shape is not supported by the tensor-core path.
+bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const __nv_bfloat16* w, int cout_pad, int bn, char* msg,
+                  size_t msg_len);
+cudaError_t conv_tc_launch(const TcPlan& plan, cudaStream_t st);
+int conv_tc_pick_bn(int cout);
+
+// Letterbox geometry tables (per output column / row): source index pair and weight.
+struct LbAxis {
+  int i0, i1;
+  float f;
+  int inside;   // 1 inside the resized image, 0 in the letterbox padding
+};
+void letterbox_tables_launch(LbAxis* xs, LbAxis* ys, int src_w, int src_h, int dst_w, int dst_h, double r,
+                             int nw, int nh, int px, int py, cudaStream_t st);
+void letterbox_f32_launch(const uint8_t* frames, int n, int src_w, int src_h, const LbAxis* xs, const LbAxis* ys,
+                          TView out, cudaStream_t st);
+void letterbox_bf16x4_launch(const uint8_t* frames, int n, int src_w, int src_h, const LbAxis* xs,
+                             const LbAxis* ys, TView out, cudaStream_t st);
+void stem_im2col_launch(TView lb4, __nv_bfloat16* rows, cudaStream_t st);
+
+// Post-processing.
+struct HeadGeom {
+  int n;
+  int gh[3], gw[3];      // grid per head (strides 32, 16, 8)
+  int off[4];            // canonical index offsets, off[3] = anchors per frame
+  float anchor_w[12], anchor_h[12];
+  int stride[3];
+  float ratio, pad_x, pad_y;
+};
+struct PostBufs {
+  uint64_t* cand_keys;   // [n][cand_cap]
+  int* cand_count;       // [n]
+  int cand_cap;
+  uint64_t* sorted;      // [n][kmax]
+  int* n_sorted;         // [n]
+  float4* boxes;         // [n][kmax] letterbox xyxy
+  float* conf;           // [n][kmax]
+  float* cls;            // [n][kmax]
+  unsigned long long* mask;  // [n][kmax][kmax/64]
+  int* keep_idx;         // [n][kmax] positions in sorted order
+  int* n_keep;           // [n]
+  int kmax;
+};
+void post_launch(const float* const* heads, const HeadGeom& g, float conf_thresh, float nms_iou, PostBufs& b,
+                 float* rows, int32_t* count, int32_t* anchor_index, int cap, int* err, cudaStream_t st);

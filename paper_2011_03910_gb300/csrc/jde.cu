@@ -1,0 +1,858 @@
+// libjde C ABI: handle, layer table, weights, forward orchestration, post-processing glue.
+//
+// Network (Sec. 3.1 names DarkNet-53 + FPN + three prediction layers; the
+// layer table itself is not printed, this is the reading used throughout):
+//   stem 3x3 3->32; five stride-2 3x3 downsamples (64, 128, 256, 512, 1024)
+//   each followed by 1/2/8/8/4 residual blocks (1x1 c->c/2, 3x3 c/2->c, add);
+//   per scale (stride 32, 16, 8; mid 512, 256, 128): 1x1 mid, 3x3 2mid,
+//   1x1 mid, 3x3 2mid, 1x1 mid -> F; detection 3x3 mid->2mid + linear 1x1
+//   2mid->24; embedding linear 3x3 mid->512; lateral 1x1 mid->mid/2 upsampled
+//   2x into channels [0, mid/2) of the next scale's concat, whose remaining
+//   channels hold the backbone skip (C4 / C3).  BN is folded (eps 1e-5),
+//   leaky-ReLU slope 0.1 after every conv except the two linear heads.
+// Memory: every activation is NHWC with a 1-pixel zero halo, one buffer per
+// layer output (no reuse: the whole pyramid of a max-size batch stays
+// resident, a few GB of HBM), allocated per model-input resolution.  The
+// backbone skips are written straight into their concat slices and the
+// laterals' upsample is fused into their epilogue, so no concat copy runs.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/jde.h"
+#include "internal.h"
+#include "track.h"
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct LayerDef {
+  int cin, cout, k, stride, has_bn, res_nb;
+};
+
+std::vector<LayerDef> build_layers() {
+  std::vector<LayerDef> L;
+  L.push_back({3, 32, 3, 1, 1, 0});
+  const int stage_c[5] = {64, 128, 256, 512, 1024};
+  const int stage_n[5] = {1, 2, 8, 8, 4};
+  for (int s = 0; s < 5; ++s) {
+    const int c = stage_c[s];
+    L.push_back({c / 2, c, 3, 2, 1, 0});
+    for (int b = 0; b < stage_n[s]; ++b) {
+      L.push_back({c, c / 2, 1, 1, 1, 0});
+      L.push_back({c / 2, c, 3, 1, 1, stage_n[s]});
+    }
+  }
+  const int head_cin[3] = {1024, 768, 384}, head_mid[3] = {512, 256, 128};
+  for (int h = 0; h < 3; ++h) {
+    const int ci = head_cin[h], m = head_mid[h];
+    L.push_back({ci, m, 1, 1, 1, 0});
+    L.push_back({m, 2 * m, 3, 1, 1, 0});
+    L.push_back({2 * m, m, 1, 1, 1, 0});
+    L.push_back({m, 2 * m, 3, 1, 1, 0});
+    L.push_back({2 * m, m, 1, 1, 1, 0});
+    L.push_back({m, 2 * m, 3, 1, 1, 0});   // det 3x3
+    L.push_back({2 * m, 24, 1, 1, 0, 0});  // det 1x1 (linear)
+    L.push_back({m, 512, 3, 1, 0, 0});     // emb 3x3 (linear)
+    if (h < 2) L.push_back({m, m / 2, 1, 1, 1, 0});  // lateral
+  }
+  return L;
+}
+
+const std::vector<LayerDef>& layers() {
+  static const std::vector<LayerDef> L = build_layers();
+  return L;
+}
+
+int align_up(int v, int a) { return (v + a - 1) / a * a; }
+
+// Weights folded and packed for both precisions' kernels.
+struct LayerW {
+  float* w_kn = nullptr;           // f32 [K_pad16][cout_pad64]
+  __nv_bfloat16* w_nk = nullptr;   // bf16 [cout_pad_tc][K_tc]
+  float* bias = nullptr;           // f32 [bias_len]
+  int cout_pad64 = 0, cout_pad_tc = 0, bn = 0, k_tc = 0;
+};
+
+// Where each conv reads and writes (tensor ids below, -1 = none).
+struct LayerIO {
+  int in, out, res;
+  int out_slice;   // channel offset inside `out` (concat slices)
+  int upsample;
+  int act;
+  int head;        // output is a head tensor (f32, unpadded): 0..2 det, 3..5 emb, -1 otherwise
+};
+
+// Tensor ids: 0..77 = output of layer l, 78 = cat16, 79 = cat8, 80 = letterbox, 81 = stem im2col rows.
+enum { T_CAT16 = 78, T_CAT8 = 79, T_LB = 80, T_IM2COL = 81, T_COUNT = 82 };
+
+struct TensorDesc {
+  int h, w, c;     // unpadded size at the given input resolution (per frame)
+  int pad;
+  int f32;         // 1: f32 storage
+  int alias;       // >= 0: lives inside tensor `alias` at channel offset `alias_off`
+  int alias_off;
+};
+
+struct ResBuffers {
+  int in_w = 0, in_h = 0;
+  std::vector<TensorDesc> td;
+  std::vector<void*> mem;          // owned allocations (per tensor id, null for aliases)
+  std::vector<size_t> bytes;
+};
+
+struct Plan {
+  int n = 0;
+  std::vector<ConvSpec> specs;     // per layer
+  std::vector<TcPlan> tc;          // per layer (BF16)
+};
+
+}  // namespace
+
+struct jde_handle {
+  jde_config cfg;
+  std::string err;
+  int* d_err = nullptr;
+  std::vector<LayerW> w;
+  std::vector<LayerIO> io;
+  std::map<std::pair<int, int>, ResBuffers> res;
+  std::map<std::tuple<int, int, int>, Plan> plans;
+  ResBuffers* cur = nullptr;
+  int cur_n = 0, cur_src_w = 0, cur_src_h = 0;
+  // letterbox
+  LbAxis* lb_x = nullptr;
+  LbAxis* lb_y = nullptr;
+  int lb_key[4] = {0, 0, 0, 0};
+  uint8_t* frames_dev = nullptr;
+  size_t frames_cap = 0;
+  // post-processing
+  PostBufs pb{};
+  int pb_n = 0;
+  float* rows_stage = nullptr;
+  int32_t* count_stage = nullptr;
+  int32_t* aidx_stage = nullptr;
+  size_t rows_stage_cap = 0;
+  TrackState trk{};
+};
+
+namespace {
+
+jde_status fail(jde_handle* h, jde_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (h)
+    h->err = buf;
+  else
+    g_create_error = buf;
+  return s;
+}
+
+#define CUDA_OR(h, call)                                                                        \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess) return fail((h), JDE_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+bool dmalloc(void** p, size_t bytes) {
+  if (cudaMalloc(p, bytes ? bytes : 16) != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
+// ----------------------------------------------------------------------------- network wiring
+std::vector<LayerIO> build_io() {
+  const auto& L = layers();
+  std::vector<LayerIO> io(L.size());
+  int l = 0;
+  auto set = [&](int in, int res, int act) {
+    io[l] = {in, l, res, 0, 0, act, -1};
+    return l++;
+  };
+  int x = set(T_LB, -1, 1);  // stem (input: letterbox or its im2col rows)
+  const int stage_n[5] = {1, 2, 8, 8, 4};
+  int c3 = -1, c4 = -1;
+  for (int s = 0; s < 5; ++s) {
+    x = set(x, -1, 1);
+    for (int b = 0; b < stage_n[s]; ++b) {
+      const int t = set(x, -1, 1);
+      x = set(t, x, 1);
+    }
+    if (s == 2) c3 = x;
+    if (s == 3) c4 = x;
+  }
+  // backbone skips live inside the concat buffers
+  io[c3].out = T_CAT8;
+  io[c3].out_slice = 128;
+  io[c4].out = T_CAT16;
+  io[c4].out_slice = 256;
+  const int c5 = x;
+  int in = c5;
+  for (int h = 0; h < 3; ++h) {
+    int f = in;
+    for (int j = 0; j < 5; ++j) f = set(f, -1, 1);
+    const int d3 = set(f, -1, 1);
+    const int d1 = set(d3, -1, 0);
+    io[d1].head = h;
+    const int e = set(f, -1, 0);
+    io[e].head = 3 + h;
+    if (h < 2) {
+      const int lat = set(f, -1, 1);
+      io[lat].out = h == 0 ? T_CAT16 : T_CAT8;
+      io[lat].out_slice = 0;
+      io[lat].upsample = 1;
+      in = h == 0 ? T_CAT16 : T_CAT8;
+    }
+  }
+  return io;
+}
+
+// Resolve a tensor id to (storage id, channel offset); layer outputs may alias a concat slice.
+void tensor_desc_table(const jde_handle* h, int in_w, int in_h, std::vector<TensorDesc>& td) {
+  const auto& L = layers();
+  td.assign(T_COUNT, TensorDesc{0, 0, 0, 1, 0, -1, 0});
+  const bool bf16 = h->cfg.precision == JDE_BF16;
+  // spatial size of every layer output follows the input chain
+  std::vector<int> oh(L.size()), ow(L.size());
+  auto in_hw = [&](int tid, int& hh, int& ww) {
+    if (tid == T_LB) {
+      hh = in_h;
+      ww = in_w;
+    } else if (tid == T_CAT16) {
+      hh = in_h / 16;
+      ww = in_w / 16;
+    } else if (tid == T_CAT8) {
+      hh = in_h / 8;
+      ww = in_w / 8;
+    } else {
+      hh = oh[tid];
+      ww = ow[tid];
+    }
+  };
+  for (size_t l = 0; l < L.size(); ++l) {
+    int hh, ww;
+    in_hw(h->io[l].in, hh, ww);
+    oh[l] = (hh + 2 * (L[l].k / 2) - L[l].k) / L[l].stride + 1;
+    ow[l] = (ww + 2 * (L[l].k / 2) - L[l].k) / L[l].stride + 1;
+    TensorDesc d{oh[l], ow[l], L[l].cout, 1, (!bf16 || h->io[l].head >= 0) ? 1 : 0, -1, 0};
+    if (h->io[l].head >= 0) d.pad = 0;
+    if (h->io[l].out != (int)l) {
+      d.alias = h->io[l].out;
+      d.alias_off = h->io[l].out_slice;
+      if (h->io[l].upsample) {
+        d.h *= 2;
+        d.w *= 2;
+      }
+    }
+    td[l] = d;
+  }
+  td[T_CAT16] = TensorDesc{in_h / 16, in_w / 16, 768, 1, bf16 ? 0 : 1, -1, 0};
+  td[T_CAT8] = TensorDesc{in_h / 8, in_w / 8, 384, 1, bf16 ? 0 : 1, -1, 0};
+  td[T_LB] = TensorDesc{in_h, in_w, bf16 ? 4 : 3, 1, bf16 ? 0 : 1, -1, 0};
+  td[T_IM2COL] = TensorDesc{in_h, in_w, 32, 1, 0, -1, 0};
+}
+
+size_t tensor_bytes(const TensorDesc& d, int n) {
+  const size_t el = d.f32 ? 4 : 2;
+  return (size_t)n * (d.h + 2 * d.pad) * (d.w + 2 * d.pad) * d.c * el;
+}
+
+jde_status get_res(jde_handle* h, int in_w, int in_h, ResBuffers** out) {
+  auto key = std::make_pair(in_w, in_h);
+  auto it = h->res.find(key);
+  if (it != h->res.end()) {
+    *out = &it->second;
+    return JDE_OK;
+  }
+  ResBuffers rb;
+  rb.in_w = in_w;
+  rb.in_h = in_h;
+  tensor_desc_table(h, in_w, in_h, rb.td);
+  rb.mem.assign(T_COUNT, nullptr);
+  rb.bytes.assign(T_COUNT, 0);
+  const int n = h->cfg.max_batch;
+  const bool bf16 = h->cfg.precision == JDE_BF16;
+  for (int t = 0; t < T_COUNT; ++t) {
+    if (rb.td[t].alias >= 0) continue;
+    if (t == T_IM2COL && !bf16) continue;
+    const size_t b = tensor_bytes(rb.td[t], n);
+    if (!dmalloc(&rb.mem[t], b)) {
+      for (void* p : rb.mem)
+        if (p) cudaFree(p);
+      return fail(h, JDE_ERR_OOM, "allocating %zu bytes for tensor %d at %dx%d", b, t, in_w, in_h);
+    }
+    rb.bytes[t] = b;
+    // the zero halo is never written again
+    if (cudaMemset(rb.mem[t], 0, b) != cudaSuccess) return fail(h, JDE_ERR_CUDA, "memset of activation buffer");
+  }
+  auto res = h->res.emplace(key, std::move(rb));
+  *out = &res.first->second;
+  return JDE_OK;
+}
+
+TView view_of(const ResBuffers& rb, int tid, int n) {
+  const TensorDesc& d = rb.td[tid];
+  TView v;
+  if (d.alias >= 0) {
+    const TensorDesc& p = rb.td[d.alias];
+    const size_t el = p.f32 ? 4 : 2;
+    v.ptr = static_cast<char*>(rb.mem[d.alias]) + (size_t)d.alias_off * el;
+    v.n = n;
+    v.h = d.h;
+    v.w = d.w;
+    v.c = d.c;
+    v.pad = p.pad;
+    v.pixstride = p.c;
+    v.dtype = p.f32 ? 0 : 1;
+  } else {
+    v.ptr = rb.mem[tid];
+    v.n = n;
+    v.h = d.h;
+    v.w = d.w;
+    v.c = d.c;
+    v.pad = d.pad;
+    v.pixstride = d.c;
+    v.dtype = d.f32 ? 0 : 1;
+  }
+  if (tid == T_LB && d.c == 4) v.c = 3;   // bf16 letterbox stores RGB + one zero channel
+  return v;
+}
+
+jde_status get_plan(jde_handle* h, ResBuffers* rb, int n, Plan** out) {
+  auto key = std::make_tuple(rb->in_w, rb->in_h, n);
+  auto it = h->plans.find(key);
+  if (it != h->plans.end()) {
+    *out = &it->second;
+    return JDE_OK;
+  }
+  const auto& L = layers();
+  Plan p;
+  p.n = n;
+  p.specs.resize(L.size());
+  const bool bf16 = h->cfg.precision == JDE_BF16;
+  if (bf16) p.tc.resize(L.size());
+  for (size_t l = 0; l < L.size(); ++l) {
+    const LayerIO& io = h->io[l];
+    ConvSpec c;
+    memset(&c, 0, sizeof(c));
+    c.k = L[l].k;
+    c.stride = L[l].stride;
+    c.cin = L[l].cin;
+    c.cout = L[l].cout;
+    c.in = view_of(*rb, io.in, n);
+    c.out = view_of(*rb, (int)l, n);
+    c.res.ptr = nullptr;
+    if (io.res >= 0) c.res = view_of(*rb, io.res, n);
+    c.Ho = rb->td[l].h / (io.upsample ? 2 : 1);
+    c.Wo = rb->td[l].w / (io.upsample ? 2 : 1);
+    c.act = io.act;
+    c.upsample = io.upsample;
+    c.bias = h->w[l].bias;
+    c.err = h->d_err;
+    if (bf16 && l == 0) {
+      // the stem runs as a 1x1 conv over its im2col rows (27 values padded to 32)
+      TView r;
+      r.ptr = rb->mem[T_IM2COL];
+      r.n = n;
+      r.h = rb->in_h;
+      r.w = rb->in_w;
+      r.c = 32;
+      r.pad = 1;
+      r.pixstride = 32;
+      r.dtype = 1;
+      c.in = r;
+      c.k = 1;
+      c.cin = 32;
+    }
+    p.specs[l] = c;
+    if (bf16) {
+      char msg[256];
+      if (!conv_tc_plan(p.tc[l], c, h->w[l].w_nk, h->w[l].cout_pad_tc, h->w[l].bn, msg, sizeof(msg)))
+        return fail(h, JDE_ERR_UNSUPPORTED, "layer %zu: %s", l, msg);
+    }
+  }
+  auto res = h->plans.emplace(key, std::move(p));
+  *out = &res.first->second;
+  return JDE_OK;
+}
+
+// ----------------------------------------------------------------------------- weights
+__global__ void pack_kernel(const float* W, const float* gamma, const float* beta, const float* mean,
+                            const float* var, const float* bias_in, int cin, int cout, int k, int K, int kpad16,
+                            int cp64, float* w_kn, int cptc, int ktc, __nv_bfloat16* w_nk, float* bias_out,
+                            int bias_len) {
+  // one thread per (k index, output channel) of the largest padded layout
+  const int rows = kpad16 > ktc ? kpad16 : ktc;
+  const int cols = cp64 > cptc ? cp64 : cptc;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)rows * cols) return;
+  const int kk = (int)(idx / cols), co = (int)(idx % cols);
+  double scale = 1.0;
+  if (co < cout && gamma) scale = (double)gamma[co] / sqrt((double)var[co] + 1e-5);
+  double v = 0.0;
+  if (co < cout && kk < K) {
+    const int tap = kk / cin, ci = kk % cin;
+    const int ky = tap / k, kx = tap % k;
+    v = (double)W[(((size_t)co * cin + ci) * k + ky) * k + kx] * scale;
+  }
+  if (w_kn && kk < kpad16 && co < cp64) w_kn[(size_t)kk * cp64 + co] = (float)v;
+  if (w_nk && kk < ktc && co < cptc) w_nk[(size_t)co * ktc + kk] = __float2bfloat16_rn((float)v);
+  if (kk == 0 && co < bias_len) {
+    double b = 0.0;
+    if (co < cout) b = gamma ? (double)beta[co] - (double)mean[co] * scale : (double)bias_in[co];
+    bias_out[co] = (float)b;
+  }
+}
+
+jde_status load_weights(jde_handle* h, const void* blob, size_t nbytes) {
+  const auto& L = layers();
+  const uint8_t* p = static_cast<const uint8_t*>(blob);
+  if (!blob || nbytes < 16 || memcmp(p, "JDEW", 4) != 0) return fail(h, JDE_ERR_WEIGHTS, "bad weights magic");
+  uint32_t hdr[3];
+  memcpy(hdr, p + 4, 12);
+  if (hdr[0] != 1) return fail(h, JDE_ERR_WEIGHTS, "weights version %u != 1", hdr[0]);
+  if (hdr[1] != L.size()) return fail(h, JDE_ERR_WEIGHTS, "weights have %u layers, expected %zu", hdr[1], L.size());
+  std::vector<size_t> offs(L.size());
+  size_t off = 16;
+  for (size_t l = 0; l < L.size(); ++l) {
+    if (off + 32 > nbytes) return fail(h, JDE_ERR_WEIGHTS, "weights truncated at layer %zu", l);
+    uint32_t lh[8];
+    memcpy(lh, p + off, 32);
+    const uint32_t want_flags = L[l].has_bn ? 1u : 2u;
+    if ((int)lh[0] != L[l].cin || (int)lh[1] != L[l].cout || (int)lh[2] != L[l].k || (int)lh[3] != L[l].stride ||
+        lh[4] != want_flags)
+      return fail(h, JDE_ERR_WEIGHTS, "layer %zu header (%u,%u,%u,%u,%u) does not match the layer table", l, lh[0],
+                  lh[1], lh[2], lh[3], lh[4]);
+    offs[l] = off + 32;
+    off += 32 + 4ull * L[l].cout * L[l].cin * L[l].k * L[l].k + 4ull * L[l].cout * (L[l].has_bn ? 4 : 1);
+    if (off > nbytes) return fail(h, JDE_ERR_WEIGHTS, "weights truncated in layer %zu", l);
+  }
+  if (off != nbytes) return fail(h, JDE_ERR_WEIGHTS, "weights blob has %zu trailing bytes", nbytes - off);
+  void* dblob = nullptr;
+  if (!dmalloc(&dblob, nbytes)) return fail(h, JDE_ERR_OOM, "weights staging (%zu bytes)", nbytes);
+  CUDA_OR(h, cudaMemcpy(dblob, blob, nbytes, cudaMemcpyHostToDevice));
+  const bool bf16 = h->cfg.precision == JDE_BF16;
+  h->w.resize(L.size());
+  for (size_t l = 0; l < L.size(); ++l) {
+    LayerW& lw = h->w[l];
+    const int K = L[l].k * L[l].k * L[l].cin;
+    const int kpad16 = align_up(K, 16);
+    lw.cout_pad64 = align_up(L[l].cout, 64);
+    lw.bn = conv_tc_pick_bn(L[l].cout);
+    lw.cout_pad_tc = align_up(L[l].cout, lw.bn);
+    lw.k_tc = l == 0 ? 32 : K;
+    const int bias_len = (lw.cout_pad64 > lw.cout_pad_tc ? lw.cout_pad64 : lw.cout_pad_tc) + 256;
+    bool ok = dmalloc((void**)&lw.bias, sizeof(float) * bias_len);
+    if (bf16)
+      ok = ok && dmalloc((void**)&lw.w_nk, sizeof(__nv_bfloat16) * (size_t)lw.cout_pad_tc * lw.k_tc);
+    else
+      ok = ok && dmalloc((void**)&lw.w_kn, sizeof(float) * (size_t)kpad16 * lw.cout_pad64);
+    if (!ok) {
+      cudaFree(dblob);
+      return fail(h, JDE_ERR_OOM, "weights of layer %zu", l);
+    }
+    cudaMemset(lw.bias, 0, sizeof(float) * bias_len);
+    const float* base = reinterpret_cast<const float*>(static_cast<uint8_t*>(dblob) + offs[l]);
+    const size_t nw = (size_t)L[l].cout * L[l].cin * L[l].k * L[l].k;
+    const float* W = base;
+    const float *gamma = nullptr, *beta = nullptr, *mean = nullptr, *var = nullptr, *bias = nullptr;
+    if (L[l].has_bn) {
+      gamma = W + nw;
+      beta = gamma + L[l].cout;
+      mean = beta + L[l].cout;
+      var = mean + L[l].cout;
+    } else {
+      bias = W + nw;
+    }
+    const int rows = bf16 ? lw.k_tc : kpad16;
+    const int cols = bf16 ? lw.cout_pad_tc : lw.cout_pad64;
+    const long long total = (long long)rows * cols;
+    pack_kernel<<<(unsigned)((total + 255) / 256), 256>>>(
+        W, gamma, beta, mean, var, bias, L[l].cin, L[l].cout, L[l].k, K, bf16 ? 0 : kpad16, bf16 ? 0 : lw.cout_pad64,
+        lw.w_kn, bf16 ? lw.cout_pad_tc : 0, bf16 ? lw.k_tc : 0, lw.w_nk, lw.bias, bias_len);
+  }
+  cudaError_t e = cudaDeviceSynchronize();
+  cudaFree(dblob);
+  if (e != cudaSuccess) return fail(h, JDE_ERR_CUDA, "packing weights: %s", cudaGetErrorString(e));
+  return JDE_OK;
+}
+
+// ----------------------------------------------------------------------------- helpers
+void geometry(int src_w, int src_h, int in_w, int in_h, double& r, int& nw, int& nh, int& px, int& py) {
+  r = fmin((double)in_w / src_w, (double)in_h / src_h);
+  nw = (int)floor(src_w * r + 0.5);
+  nh = (int)floor(src_h * r + 0.5);
+  px = (in_w - nw) / 2;
+  py = (in_h - nh) / 2;
+}
+
+jde_status ensure_post(jde_handle* h, int n) {
+  if (h->pb_n >= n && h->pb.cand_keys) return JDE_OK;
+  PostBufs& b = h->pb;
+  void* ptrs[] = {b.cand_keys, b.cand_count, b.sorted, b.n_sorted, b.boxes, b.conf, b.cls, b.mask, b.keep_idx,
+                  b.n_keep};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  const int kmax = h->cfg.max_cand;
+  const int anchors = 4 * ((h->cfg.max_in_w / 32) * (h->cfg.max_in_h / 32) + (h->cfg.max_in_w / 16) * (h->cfg.max_in_h / 16) +
+                           (h->cfg.max_in_w / 8) * (h->cfg.max_in_h / 8));
+  b.cand_cap = anchors;
+  b.kmax = kmax;
+  bool ok = dmalloc((void**)&b.cand_keys, sizeof(uint64_t) * (size_t)n * anchors) &&
+            dmalloc((void**)&b.cand_count, sizeof(int) * n) &&
+            dmalloc((void**)&b.sorted, sizeof(uint64_t) * (size_t)n * kmax) &&
+            dmalloc((void**)&b.n_sorted, sizeof(int) * n) && dmalloc((void**)&b.boxes, sizeof(float4) * (size_t)n * kmax) &&
+            dmalloc((void**)&b.conf, sizeof(float) * (size_t)n * kmax) &&
+            dmalloc((void**)&b.cls, sizeof(float) * (size_t)n * kmax) &&
+            dmalloc((void**)&b.mask, sizeof(unsigned long long) * (size_t)n * kmax * (kmax / 64)) &&
+            dmalloc((void**)&b.keep_idx, sizeof(int) * (size_t)n * kmax) && dmalloc((void**)&b.n_keep, sizeof(int) * n);
+  if (!ok) return fail(h, JDE_ERR_OOM, "post-processing buffers for %d frames", n);
+  h->pb_n = n;
+  return JDE_OK;
+}
+
+__global__ void gather_view_kernel(TView v, void* dst, int el) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = (long long)v.n * v.h * v.w * v.c;
+  if (idx >= total) return;
+  const int c = (int)(idx % v.c);
+  long long p = idx / v.c;
+  const int x = (int)(p % v.w);
+  p /= v.w;
+  const int y = (int)(p % v.h);
+  const int n = (int)(p / v.h);
+  const size_t o = tview_off(v, n, y, x) + c;
+  if (el == 4)
+    static_cast<float*>(dst)[idx] = static_cast<const float*>(v.ptr)[o];
+  else
+    static_cast<__nv_bfloat16*>(dst)[idx] = static_cast<const __nv_bfloat16*>(v.ptr)[o];
+}
+
+}  // namespace
+
+// ============================================================================= C ABI
+extern "C" {
+
+void jde_default_config(jde_config* c) {
+  if (!c) return;
+  memset(c, 0, sizeof(*c));
+  c->precision = JDE_BF16;
+  c->max_batch = 16;
+  c->max_in_w = 1088;
+  c->max_in_h = 608;
+  c->max_src_w = 1920;
+  c->max_src_h = 1080;
+  c->max_cand = 4096;
+  c->conf_thresh = 0.5f;
+  c->nms_iou = 0.4f;
+  c->assign_thresh = 0.7f;
+  c->gate_chi2 = 9.487729036781154;
+  c->lost_max_frames = 30;
+  c->emb_momentum = 0.9f;
+  c->max_streams = 64;
+  c->max_tracks = 1024;
+  c->max_track_dets = 1024;
+  c->device = 0;
+}
+
+int jde_layer_table(jde_layer_desc* out, int cap) {
+  const auto& L = layers();
+  for (int i = 0; i < (int)L.size() && i < cap && out; ++i)
+    out[i] = jde_layer_desc{L[i].cin, L[i].cout, L[i].k, L[i].stride, L[i].has_bn, L[i].res_nb};
+  return (int)L.size();
+}
+
+const char* jde_last_error(jde_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+void jde_destroy(jde_handle* h) {
+  if (!h) return;
+  cudaSetDevice(h->cfg.device);
+  cudaDeviceSynchronize();
+  for (auto& lw : h->w) {
+    cudaFree(lw.w_kn);
+    cudaFree(lw.w_nk);
+    cudaFree(lw.bias);
+  }
+  for (auto& kv : h->res)
+    for (void* p : kv.second.mem)
+      if (p) cudaFree(p);
+  PostBufs& b = h->pb;
+  void* ptrs[] = {b.cand_keys, b.cand_count, b.sorted, b.n_sorted, b.boxes, b.conf, b.cls, b.mask, b.keep_idx,
+                  b.n_keep, h->lb_x, h->lb_y, h->frames_dev, h->rows_stage, h->count_stage, h->aidx_stage, h->d_err};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  track_free(h->trk);
+  delete h;
+}
+
+jde_status jde_create(const jde_config* cfg, const void* weights, size_t nbytes, jde_handle** out) {
+  if (!out) return fail(nullptr, JDE_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!cfg) return fail(nullptr, JDE_ERR_INVALID_ARG, "cfg is NULL");
+  const jde_config& c = *cfg;
+  if (c.precision != JDE_FP32 && c.precision != JDE_BF16)
+    return fail(nullptr, JDE_ERR_UNSUPPORTED, "precision %d not supported", c.precision);
+  if (c.max_batch < 1 || c.max_in_w < 32 || c.max_in_h < 32 || c.max_in_w % 32 || c.max_in_h % 32 ||
+      c.max_src_w < 1 || c.max_src_h < 1 || c.max_cand < 64 || c.max_cand > 4096 || c.max_cand % 64 ||
+      c.max_streams < 1 || c.max_tracks < 1 || c.max_track_dets < 1 || c.max_track_dets > 4096 ||
+      c.max_tracks > 4096)
+    return fail(nullptr, JDE_ERR_INVALID_ARG, "config out of range");
+  if (cudaSetDevice(c.device) != cudaSuccess) return fail(nullptr, JDE_ERR_CUDA, "cudaSetDevice(%d)", c.device);
+  jde_handle* h = new jde_handle();
+  h->cfg = c;
+  h->io = build_io();
+  jde_status s = JDE_OK;
+  if (!dmalloc((void**)&h->d_err, sizeof(int))) s = fail(h, JDE_ERR_OOM, "error word");
+  if (s == JDE_OK) cudaMemset(h->d_err, 0, sizeof(int));
+  if (s == JDE_OK) s = load_weights(h, weights, nbytes);
+  if (s == JDE_OK && !(dmalloc((void**)&h->lb_x, sizeof(LbAxis) * c.max_in_w) &&
+                       dmalloc((void**)&h->lb_y, sizeof(LbAxis) * c.max_in_h)))
+    s = fail(h, JDE_ERR_OOM, "letterbox tables");
+  if (s == JDE_OK && track_alloc(h->trk, c) != 0) s = fail(h, JDE_ERR_OOM, "tracker state");
+  if (s != JDE_OK) {
+    g_create_error = h->err;
+    jde_destroy(h);
+    return s;
+  }
+  *out = h;
+  return JDE_OK;
+}
+
+jde_status jde_forward(jde_handle* h, const uint8_t* frames, int n, int src_w, int src_h, int in_w, int in_h,
+                       int on_device, void* stream) {
+  if (!h) return fail(nullptr, JDE_ERR_INVALID_ARG, "handle is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!frames || n < 1 || n > h->cfg.max_batch || in_w % 32 || in_h % 32 || in_w < 32 || in_h < 32 ||
+      in_w > h->cfg.max_in_w || in_h > h->cfg.max_in_h || src_w < 1 || src_h < 1)
+    return fail(h, JDE_ERR_INVALID_ARG, "jde_forward: bad arguments (n=%d in=%dx%d src=%dx%d)", n, in_w, in_h, src_w,
+                src_h);
+  const size_t fbytes = (size_t)n * src_w * src_h * 3;
+  if (!on_device) {
+    if (fbytes > h->frames_cap) {
+      cudaFree(h->frames_dev);
+      h->frames_dev = nullptr;
+      if (!dmalloc((void**)&h->frames_dev, fbytes)) return fail(h, JDE_ERR_OOM, "frame staging");
+      h->frames_cap = fbytes;
+    }
+    CUDA_OR(h, cudaMemcpyAsync(h->frames_dev, frames, fbytes, cudaMemcpyHostToDevice, st));
+    frames = h->frames_dev;
+  }
+  ResBuffers* rb;
+  jde_status s = get_res(h, in_w, in_h, &rb);
+  if (s != JDE_OK) return s;
+  Plan* plan;
+  s = get_plan(h, rb, n, &plan);
+  if (s != JDE_OK) return s;
+  const int key[4] = {src_w, src_h, in_w, in_h};
+  if (memcmp(key, h->lb_key, sizeof(key)) != 0) {
+    double r;
+    int nw, nh, px, py;
+    geometry(src_w, src_h, in_w, in_h, r, nw, nh, px, py);
+    letterbox_tables_launch(h->lb_x, h->lb_y, src_w, src_h, in_w, in_h, r, nw, nh, px, py, st);
+    memcpy(h->lb_key, key, sizeof(key));
+  }
+  const TView lb = view_of(*rb, T_LB, n);
+  const bool bf16 = h->cfg.precision == JDE_BF16;
+  if (bf16) {
+    letterbox_bf16x4_launch(frames, n, src_w, src_h, h->lb_x, h->lb_y, lb, st);
+    stem_im2col_launch(lb, static_cast<__nv_bfloat16*>(rb->mem[T_IM2COL]), st);
+  } else {
+    letterbox_f32_launch(frames, n, src_w, src_h, h->lb_x, h->lb_y, lb, st);
+  }
+  const auto& L = layers();
+  for (size_t l = 0; l < L.size(); ++l) {
+    if (bf16) {
+      cudaError_t e = conv_tc_launch(plan->tc[l], st);
+      if (e != cudaSuccess) return fail(h, JDE_ERR_CUDA, "conv layer %zu: %s", l, cudaGetErrorString(e));
+    } else {
+      conv_simt_launch(plan->specs[l], h->w[l].w_kn, h->w[l].cout_pad64, st);
+    }
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(h, JDE_ERR_CUDA, "forward launch: %s", cudaGetErrorString(e));
+  h->cur = rb;
+  h->cur_n = n;
+  h->cur_src_w = src_w;
+  h->cur_src_h = src_h;
+  return JDE_OK;
+}
+
+jde_status jde_postprocess(jde_handle* h, const float* const* heads, int n, int in_w, int in_h, int src_w, int src_h,
+                           jde_dets* out, void* stream) {
+  if (!h) return fail(nullptr, JDE_ERR_INVALID_ARG, "handle is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!out || !out->rows || !out->count || out->cap < 1 || n < 1 || n > h->cfg.max_batch || in_w % 32 ||
+      in_h % 32 || in_w > h->cfg.max_in_w || in_h > h->cfg.max_in_h || in_w < 32 || in_h < 32 || src_w < 1 ||
+      src_h < 1)
+    return fail(h, JDE_ERR_INVALID_ARG, "jde_postprocess: bad arguments");
+  const float* hp[6];
+  if (heads) {
+    for (int i = 0; i < 6; ++i) {
+      if (!heads[i]) return fail(h, JDE_ERR_INVALID_ARG, "jde_postprocess: head %d is NULL", i);
+      hp[i] = heads[i];
+    }
+  } else {
+    if (!h->cur || h->cur->in_w != in_w || h->cur->in_h != in_h || h->cur_n < n)
+      return fail(h, JDE_ERR_INVALID_ARG, "jde_postprocess: no forward result at %dx%d for %d frames", in_w, in_h, n);
+    const auto& L = layers();
+    for (size_t l = 0; l < L.size(); ++l)
+      if (h->io[l].head >= 0) hp[h->io[l].head] = static_cast<const float*>(h->cur->mem[l]);
+  }
+  jde_status s = ensure_post(h, n);
+  if (s != JDE_OK) return s;
+  HeadGeom g;
+  memset(&g, 0, sizeof(g));
+  g.n = n;
+  const int strides[3] = {32, 16, 8};
+  const float base[3] = {128.f, 32.f, 8.f};
+  g.off[0] = 0;
+  for (int i = 0; i < 3; ++i) {
+    g.stride[i] = strides[i];
+    g.gh[i] = in_h / strides[i];
+    g.gw[i] = in_w / strides[i];
+    g.off[i + 1] = g.off[i] + 4 * g.gh[i] * g.gw[i];
+    for (int a = 0; a < 4; ++a) {
+      const double w = base[i] * pow(sqrt(2.0), a);
+      g.anchor_w[i * 4 + a] = (float)w;
+      g.anchor_h[i * 4 + a] = (float)(3.0 * w);
+    }
+  }
+  double r;
+  int nw, nh, px, py;
+  geometry(src_w, src_h, in_w, in_h, r, nw, nh, px, py);
+  g.ratio = (float)r;
+  g.pad_x = (float)px;
+  g.pad_y = (float)py;
+  float* rows = out->rows;
+  int32_t* count = out->count;
+  int32_t* aidx = out->anchor_index;
+  const size_t need = (size_t)n * out->cap;
+  if (!out->on_device) {
+    if (need > h->rows_stage_cap) {
+      cudaFree(h->rows_stage);
+      cudaFree(h->count_stage);
+      cudaFree(h->aidx_stage);
+      h->rows_stage = nullptr;
+      h->count_stage = nullptr;
+      h->aidx_stage = nullptr;
+      if (!(dmalloc((void**)&h->rows_stage, sizeof(float) * 518 * need) &&
+            dmalloc((void**)&h->count_stage, sizeof(int32_t) * h->cfg.max_batch) &&
+            dmalloc((void**)&h->aidx_stage, sizeof(int32_t) * need)))
+        return fail(h, JDE_ERR_OOM, "detection staging");
+      h->rows_stage_cap = need;
+    }
+    rows = h->rows_stage;
+    count = h->count_stage;
+    aidx = out->anchor_index ? h->aidx_stage : nullptr;
+  }
+  post_launch(hp, g, h->cfg.conf_thresh, h->cfg.nms_iou, h->pb, rows, count, aidx, out->cap, h->d_err, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(h, JDE_ERR_CUDA, "post-processing launch: %s", cudaGetErrorString(e));
+  if (!out->on_device) {
+    CUDA_OR(h, cudaMemcpyAsync(out->count, count, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
+    CUDA_OR(h, cudaStreamSynchronize(st));
+    int maxc = 0;
+    for (int i = 0; i < n; ++i) maxc = out->count[i] > maxc ? out->count[i] : maxc;
+    const int rows_copy = maxc < out->cap ? maxc : out->cap;
+    for (int i = 0; i < n && rows_copy > 0; ++i) {
+      const int ci = out->count[i] < out->cap ? out->count[i] : out->cap;
+      if (ci <= 0) continue;
+      CUDA_OR(h, cudaMemcpyAsync(out->rows + (size_t)i * out->cap * 518, rows + (size_t)i * out->cap * 518,
+                                 sizeof(float) * 518 * ci, cudaMemcpyDeviceToHost, st));
+      if (out->anchor_index)
+        CUDA_OR(h, cudaMemcpyAsync(out->anchor_index + (size_t)i * out->cap, aidx + (size_t)i * out->cap,
+                                   sizeof(int32_t) * ci, cudaMemcpyDeviceToHost, st));
+    }
+    CUDA_OR(h, cudaStreamSynchronize(st));
+    if (maxc > out->cap) return fail(h, JDE_ERR_CAPACITY, "a frame kept %d detections, cap is %d", maxc, out->cap);
+  }
+  return JDE_OK;
+}
+
+jde_status jde_detect_batch(jde_handle* h, const uint8_t* frames, int n, int src_w, int src_h, int in_w, int in_h,
+                            int on_device, jde_dets* out, void* stream) {
+  jde_status s = jde_forward(h, frames, n, src_w, src_h, in_w, in_h, on_device, stream);
+  if (s != JDE_OK) return s;
+  return jde_postprocess(h, nullptr, n, in_w, in_h, src_w, src_h, out, stream);
+}
+
+jde_status jde_get_tensor(jde_handle* h, int id, void* dst, size_t dst_bytes, int* dims, int* dtype, void* stream) {
+  if (!h) return fail(nullptr, JDE_ERR_INVALID_ARG, "handle is NULL");
+  if (!h->cur) return fail(h, JDE_ERR_NOT_FOUND, "no forward has run");
+  int tid;
+  if (id >= 0 && id < JDE_NUM_LAYERS)
+    tid = id;
+  else if (id == 100)
+    tid = T_LB;
+  else if (id == 101 && h->cfg.precision == JDE_BF16)
+    tid = T_IM2COL;
+  else
+    return fail(h, JDE_ERR_NOT_FOUND, "unknown tensor id %d", id);
+  TView v = view_of(*h->cur, tid, h->cur_n);
+  if (tid == T_IM2COL) {   // raw rows over the padded domain
+    v.ptr = h->cur->mem[T_IM2COL];
+    v.h = h->cur->in_h + 2;
+    v.w = h->cur->in_w + 2;
+    v.c = 32;
+    v.pad = 0;
+    v.pixstride = 32;
+    v.dtype = 1;
+  }
+  if (dims) {
+    dims[0] = v.n;
+    dims[1] = v.h;
+    dims[2] = v.w;
+    dims[3] = v.c;
+  }
+  if (dtype) *dtype = v.dtype;
+  if (!dst) return JDE_OK;
+  const int el = v.dtype ? 2 : 4;
+  const long long total = (long long)v.n * v.h * v.w * v.c;
+  if ((size_t)total * el > dst_bytes) return fail(h, JDE_ERR_CAPACITY, "jde_get_tensor: dst too small");
+  gather_view_kernel<<<(unsigned)((total + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(v, dst, el);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(h, JDE_ERR_CUDA, "gather: %s", cudaGetErrorString(e));
+  return JDE_OK;
+}
+
+jde_status jde_kernel_errors(jde_handle* h, int* word, void* stream) {
+  if (!h || !word) return fail(h, JDE_ERR_INVALID_ARG, "jde_kernel_errors: NULL argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CUDA_OR(h, cudaMemcpyAsync(word, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CUDA_OR(h, cudaStreamSynchronize(st));
+  CUDA_OR(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
+  return JDE_OK;
+}
+
+jde_status jde_track_step(jde_handle* h, int n, const int32_t* stream_ids, const jde_dets* dets, jde_tracks* out,
+                          void* stream) {
+  if (!h) return fail(nullptr, JDE_ERR_INVALID_ARG, "handle is NULL");
+  char msg[256] = {0};
+  const int r = track_step(h->trk, h->cfg, n, stream_ids, dets, out, h->d_err, static_cast<cudaStream_t>(stream), msg,
+                           sizeof(msg));
+  if (r != JDE_OK) return fail(h, (jde_status)r, "jde_track_step: %s", msg);
+  return JDE_OK;
+}
+
+jde_status jde_stream_reset(jde_handle* h, int stream_id, void* stream) {
+  if (!h) return fail(nullptr, JDE_ERR_INVALID_ARG, "handle is NULL");
+  if (stream_id < 0 || stream_id >= h->cfg.max_streams)
+    return fail(h, JDE_ERR_NOT_FOUND, "stream id %d out of range", stream_id);
+  if (track_reset(h->trk, stream_id, static_cast<cudaStream_t>(stream)) != 0)
+    return fail(h, JDE_ERR_CUDA, "stream reset failed");
+  return JDE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,155 @@
+// Letterbox resize of uint8 RGB frames to the network input, and the stem's im2col rows.
+//
+// Geometry (the paper only states FullHD input, Sec. 5.1): r = min(dst_w/src_w,
+// dst_h/src_h); the image is resized to floor(src r + 0.5) on each axis,
+// centred (pad = floor((dst - new)/2) on the left/top), sampled bilinearly with
+// half-pixel centres src = (dst + 0.5)/r - 0.5 clamped to the image, scaled by
+// 1/255; the padding holds 0.5.  The per-column and per-row sample positions
+// are computed once in double precision; the per-pixel blend is f32.
+#include "internal.h"
+
+namespace {
+
+__global__ void tables_kernel(LbAxis* xs, LbAxis* ys, int src_w, int src_h, int dst_w, int dst_h, double r, int nw,
+                              int nh, int px, int py) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < dst_w) {
+    LbAxis a = {0, 0, 0.f, 0};
+    const int d = i - px;
+    if (d >= 0 && d < nw) {
+      double s = (d + 0.5) / r - 0.5;
+      s = fmin(fmax(s, 0.0), (double)(src_w - 1));
+      const int i0 = (int)floor(s);
+      a.i0 = i0;
+      a.i1 = min(i0 + 1, src_w - 1);
+      a.f = (float)(s - i0);
+      a.inside = 1;
+    }
+    xs[i] = a;
+  }
+  if (i < dst_h) {
+    LbAxis a = {0, 0, 0.f, 0};
+    const int d = i - py;
+    if (d >= 0 && d < nh) {
+      double s = (d + 0.5) / r - 0.5;
+      s = fmin(fmax(s, 0.0), (double)(src_h - 1));
+      const int i0 = (int)floor(s);
+      a.i0 = i0;
+      a.i1 = min(i0 + 1, src_h - 1);
+      a.f = (float)(s - i0);
+      a.inside = 1;
+    }
+    ys[i] = a;
+  }
+}
+
+__device__ __forceinline__ void sample(const uint8_t* img, int src_w, const LbAxis& ax, const LbAxis& ay,
+                                       float (&v)[3]) {
+  if (!(ax.inside && ay.inside)) {
+    v[0] = v[1] = v[2] = 0.5f;
+    return;
+  }
+  const uint8_t* r0 = img + (size_t)ay.i0 * src_w * 3;
+  const uint8_t* r1 = img + (size_t)ay.i1 * src_w * 3;
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) {
+    const float p00 = r0[ax.i0 * 3 + ch], p01 = r0[ax.i1 * 3 + ch];
+    const float p10 = r1[ax.i0 * 3 + ch], p11 = r1[ax.i1 * 3 + ch];
+    const float top = p00 * (1.f - ax.f) + p01 * ax.f;
+    const float bot = p10 * (1.f - ax.f) + p11 * ax.f;
+    v[ch] = (top * (1.f - ay.f) + bot * ay.f) / 255.f;
+  }
+}
+
+// f32, 3 channels, into the interior of a haloed view
+__global__ void letterbox_f32_kernel(const uint8_t* frames, int n, int src_w, int src_h, const LbAxis* xs,
+                                     const LbAxis* ys, TView out) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = (long long)n * out.h * out.w;
+  if (idx >= total) return;
+  const int x = (int)(idx % out.w);
+  const int y = (int)((idx / out.w) % out.h);
+  const int f = (int)(idx / ((long long)out.w * out.h));
+  float v[3];
+  sample(frames + (size_t)f * src_w * src_h * 3, src_w, xs[x], ys[y], v);
+  float* o = static_cast<float*>(out.ptr) + tview_off(out, f, y, x);
+  o[0] = v[0];
+  o[1] = v[1];
+  o[2] = v[2];
+}
+
+// bf16, 4 channels (RGB, 0), 8 bytes per pixel, into the interior of a haloed view
+__global__ void letterbox_bf16x4_kernel(const uint8_t* frames, int n, int src_w, int src_h, const LbAxis* xs,
+                                        const LbAxis* ys, TView out) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = (long long)n * out.h * out.w;
+  if (idx >= total) return;
+  const int x = (int)(idx % out.w);
+  const int y = (int)((idx / out.w) % out.h);
+  const int f = (int)(idx / ((long long)out.w * out.h));
+  float v[3];
+  sample(frames + (size_t)f * src_w * src_h * 3, src_w, xs[x], ys[y], v);
+  __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
+  __nv_bfloat162 b = __floats2bfloat162_rn(v[2], 0.f);
+  uint2 q = make_uint2(*reinterpret_cast<uint32_t*>(&a), *reinterpret_cast<uint32_t*>(&b));
+  *reinterpret_cast<uint2*>(static_cast<__nv_bfloat16*>(out.ptr) + tview_off(out, f, y, x)) = q;
+}
+
+// Stem im2col: one 32-value bf16 row per pixel of the padded output domain,
+// value (ky*3 + kx)*3 + c = lb[n, y + ky - 1, x + kx - 1, c] (0 outside the
+// image, i.e. the conv's zero padding), values 27..31 = 0.  Halo rows are left
+// untouched (they are zero and their outputs are discarded).
+__global__ void stem_im2col_kernel(TView lb, __nv_bfloat16* rows) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = (long long)lb.n * lb.h * lb.w;
+  if (idx >= total) return;
+  const int x = (int)(idx % lb.w);
+  const int y = (int)((idx / lb.w) % lb.h);
+  const int f = (int)(idx / ((long long)lb.w * lb.h));
+  const __nv_bfloat16* src = static_cast<const __nv_bfloat16*>(lb.ptr);
+  __nv_bfloat16 v[32];
+#pragma unroll
+  for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+    for (int kx = 0; kx < 3; ++kx) {
+      // the halo of lb is zero, so (y + ky - 1, x + kx - 1) is always addressable
+      const uint2 q = *reinterpret_cast<const uint2*>(src + tview_off(lb, f, y + ky - 1, x + kx - 1));
+      const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&q);
+      const int t = (ky * 3 + kx) * 3;
+      v[t] = e[0];
+      v[t + 1] = e[1];
+      v[t + 2] = e[2];
+    }
+#pragma unroll
+  for (int j = 27; j < 32; ++j) v[j] = __float2bfloat16_rn(0.f);
+  const size_t row = ((size_t)f * (lb.h + 2) + y + 1) * (lb.w + 2) + x + 1;
+  uint4* o = reinterpret_cast<uint4*>(rows + row * 32);
+  const uint4* s4 = reinterpret_cast<const uint4*>(v);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) o[j] = s4[j];
+}
+
+}  // namespace
+
+void letterbox_tables_launch(LbAxis* xs, LbAxis* ys, int src_w, int src_h, int dst_w, int dst_h, double r, int nw,
+                             int nh, int px, int py, cudaStream_t st) {
+  const int n = dst_w > dst_h ? dst_w : dst_h;
+  tables_kernel<<<(n + 255) / 256, 256, 0, st>>>(xs, ys, src_w, src_h, dst_w, dst_h, r, nw, nh, px, py);
+}
+
+void letterbox_f32_launch(const uint8_t* frames, int n, int src_w, int src_h, const LbAxis* xs, const LbAxis* ys,
+                          TView out, cudaStream_t st) {
+  const long long total = (long long)n * out.h * out.w;
+  letterbox_f32_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(frames, n, src_w, src_h, xs, ys, out);
+}
+
+void letterbox_bf16x4_launch(const uint8_t* frames, int n, int src_w, int src_h, const LbAxis* xs,
+                             const LbAxis* ys, TView out, cudaStream_t st) {
+  const long long total = (long long)n * out.h * out.w;
+  letterbox_bf16x4_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(frames, n, src_w, src_h, xs, ys, out);
+}
+
+void stem_im2col_launch(TView lb4, __nv_bfloat16* rows, cudaStream_t st) {
+  const long long total = (long long)lb4.n * lb4.h * lb4.w;
+  stem_im2col_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(lb4, rows);
+}

@@ -1,0 +1,696 @@
+// Tracker step on the device (Sec. 3 "Location Estimation" / "Association",
+// Appendix A items 4-9), for several video streams per launch.
+//
+//   prep   : Kalman predict of every active/lost track (x <- F x,
+//            P <- F P F^T + Q, Q from the pre-prediction height), then the
+//            innovation covariance S = H P H^T + R (R from the predicted
+//            height) and its Cholesky factor for gating and update;
+//   cost   : C[k][j] = 1 - <e_k, d_j> (f32 dot of unit embeddings), replaced by
+//            the "infinite" 1e5 when the squared Mahalanobis distance
+//            |L^-1 (z_j - H x_k)|^2 exceeds the chi-square gate;
+//   assign : shortest-augmenting-path Hungarian in f64 (one warp per stream;
+//            rows = the smaller side, tracks in creation order, detections in
+//            kept order; columns scanned ascending, first minimum wins), pairs
+//            costing more than the threshold rejected, Kalman update
+//            (K = P H^T S^-1, x += K y, P -= K S K^T) and gallery update of
+//            the assigned tracks, lost/removal bookkeeping, births in
+//            detection order, output.
+// Noise model: constant velocity on (cx, cy, a = w/h, h), dt = 1, sigma_p =
+// 1/20 and sigma_v = 1/160 of the height (the paper names the Kalman filter
+// but not its model).
+// Track data never moves: each stream has a pool of slots, an `order` list
+// (slot of the k-th track in creation order) and a free-slot stack.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "common.cuh"
+#include "track.h"
+
+namespace {
+
+constexpr double SP = 1.0 / 20.0;
+constexpr double SV = 1.0 / 160.0;
+constexpr double INF_COST = 1e5;
+constexpr int MAXB = 64;
+
+struct Slots {
+  int stream[MAXB];
+};
+
+struct StepArgs {
+  TrackState t;
+  const float* rows;      // [n][cap][518]
+  const int32_t* count;   // [n]
+  int cap;
+  int n;
+  double gate;
+  float assign_thresh;
+  int lost_max;
+  float momentum;
+  int* err;
+  // outputs
+  long long* o_id;
+  float* o_box;
+  int32_t* o_state;
+  int32_t* o_det;
+  int32_t* o_count;
+  int o_cap;
+};
+
+__device__ __forceinline__ int det_count(const StepArgs& a, int b) {
+  const int c = a.count[b];
+  const int d = c < a.cap ? c : a.cap;
+  return d < a.t.max_dets ? d : a.t.max_dets;
+}
+
+__device__ void measurement(const float* row, double (&z)[4]) {
+  const double x1 = row[0], y1 = row[1], x2 = row[2], y2 = row[3];
+  const double w = x2 - x1, h = y2 - y1;
+  z[0] = x1 + w / 2;
+  z[1] = y1 + h / 2;
+  z[2] = w / h;
+  z[3] = h;
+}
+
+__global__ void reset_kernel(TrackState t, int s) {
+  const int T = t.max_tracks;
+  for (int k = threadIdx.x; k < T; k += blockDim.x) {
+    t.free_stack[(size_t)s * T + k] = T - 1 - k;
+    t.order[(size_t)s * T + k] = -1;
+  }
+  if (threadIdx.x == 0) {
+    t.n_tracks[s] = 0;
+    t.next_id[s] = 1;
+    t.free_top[s] = T;
+  }
+}
+
+// ---------------------------------------------------------------- predict + gating factors
+__global__ void prep_kernel(StepArgs a, Slots sl) {
+  const int b = blockIdx.y;
+  const int s = sl.stream[b];
+  const int T = a.t.max_tracks;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= a.t.n_tracks[s]) return;
+  const int slot = a.t.order[(size_t)s * T + k];
+  double* m = a.t.mean + ((size_t)s * T + slot) * 8;
+  double* P = a.t.cov + ((size_t)s * T + slot) * 64;
+  double mm[8], p[64], tmp[64];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) mm[i] = m[i];
+#pragma unroll
+  for (int i = 0; i < 64; ++i) p[i] = P[i];
+  const double h = mm[3];
+  // x <- F x
+#pragma unroll
+  for (int i = 0; i < 4; ++i) mm[i] = mm[i] + mm[i + 4];
+  // P <- (F P) F^T + Q
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) tmp[i * 8 + j] = i < 4 ? p[i * 8 + j] + p[(i + 4) * 8 + j] : p[i * 8 + j];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) p[i * 8 + j] = j < 4 ? tmp[i * 8 + j] + tmp[i * 8 + j + 4] : tmp[i * 8 + j];
+  const double qp = (SP * h) * (SP * h), qv = (SV * h) * (SV * h);
+  p[0] += qp;
+  p[9] += qp;
+  p[18] += 1e-2 * 1e-2;
+  p[27] += qp;
+  p[36] += qv;
+  p[45] += qv;
+  p[54] += 1e-5 * 1e-5;
+  p[63] += qv;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) m[i] = mm[i];
+#pragma unroll
+  for (int i = 0; i < 64; ++i) P[i] = p[i];
+  // S = H P H^T + R, Cholesky S = L L^T
+  const double hp = mm[3];
+  const double rp = (SP * hp) * (SP * hp);
+  double S[16];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) S[i * 4 + j] = p[i * 8 + j];
+  S[0] += rp;
+  S[5] += rp;
+  S[10] += 1e-1 * 1e-1;
+  S[15] += rp;
+  double L[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) L[i] = 0.0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    double sj = S[j * 4 + j];
+#pragma unroll
+    for (int q = 0; q < j; ++q) sj -= L[j * 4 + q] * L[j * 4 + q];
+    L[j * 4 + j] = sqrt(sj);
+#pragma unroll
+    for (int i = j + 1; i < 4; ++i) {
+      double v = S[i * 4 + j];
+#pragma unroll
+      for (int q = 0; q < j; ++q) v -= L[i * 4 + q] * L[j * 4 + q];
+      L[i * 4 + j] = v / L[j * 4 + j];
+    }
+  }
+  double* gl = a.t.gate_l + ((size_t)b * T + slot) * 16;
+  double* gz = a.t.gate_z + ((size_t)b * T + slot) * 4;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) gl[i] = L[i];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) gz[i] = mm[i];
+}
+
+// ---------------------------------------------------------------- cost + gate
+// 32 tracks x 32 detections per CTA, 256 threads: thread (tx, ty) owns det tx, tracks 4ty..4ty+3.
+__global__ void cost_kernel(StepArgs a, Slots sl) {
+  const int b = blockIdx.z;
+  const int s = sl.stream[b];
+  const int T = a.t.max_tracks;
+  const int nt = a.t.n_tracks[s];
+  const int D = det_count(a, b);
+  const int k0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+  if (k0 >= nt || j0 >= D) return;
+  __shared__ float Es[32][33];
+  __shared__ float Ds[32][33];
+  __shared__ int slot_s[32];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  if (threadIdx.x < 32) slot_s[threadIdx.x] = k0 + threadIdx.x < nt ? a.t.order[(size_t)s * T + k0 + threadIdx.x] : -1;
+  __syncthreads();
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  const float* rows = a.rows + (size_t)b * a.cap * 518;
+  for (int c0 = 0; c0 < 512; c0 += 32) {
+    for (int e = threadIdx.x; e < 32 * 32; e += 256) {
+      const int r = e >> 5, cc = e & 31;
+      const int sl2 = slot_s[r];
+      Es[r][cc] = sl2 >= 0 ? a.t.emb[((size_t)s * T + sl2) * 512 + c0 + cc] : 0.f;
+      Ds[r][cc] = j0 + r < D ? rows[(size_t)(j0 + r) * 518 + 6 + c0 + cc] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int cc = 0; cc < 32; ++cc) {
+      const float dv = Ds[tx][cc];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = fmaf(Es[ty * 4 + q][cc], dv, acc[q]);
+    }
+    __syncthreads();
+  }
+  const int j = j0 + tx;
+  if (j >= D) return;
+  double z[4];
+  measurement(rows + (size_t)j * 518, z);
+  const bool trans = nt > D;
+  const int M = trans ? nt : D;
+  double* A = a.t.cost + (size_t)b * T * a.t.max_dets;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int k = k0 + ty * 4 + q;
+    if (k >= nt) break;
+    const int slot = slot_s[ty * 4 + q];
+    const double* L = a.t.gate_l + ((size_t)b * T + slot) * 16;
+    const double* zh = a.t.gate_z + ((size_t)b * T + slot) * 4;
+    double w[4], d2 = 0.0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      double v = z[i] - zh[i];
+#pragma unroll
+      for (int c = 0; c < i; ++c) v -= L[i * 4 + c] * w[c];
+      w[i] = v / L[i * 4 + i];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) d2 += w[i] * w[i];
+    double cost = (double)(1.f - acc[q]);
+    if (d2 > a.gate) cost = INF_COST;
+    if (trans)
+      A[(size_t)j * M + k] = cost;
+    else
+      A[(size_t)k * M + j] = cost;
+  }
+}
+
+// ---------------------------------------------------------------- assignment, update, lifecycle
+__device__ __forceinline__ void argmin_warp(double& v, int& j) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, v, off);
+    const int oj = __shfl_xor_sync(0xffffffffu, j, off);
+    if (ov < v || (ov == v && oj < j)) {
+      v = ov;
+      j = oj;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) assign_kernel(StepArgs a, Slots sl) {
+  extern __shared__ uint8_t smem[];
+  const int b = blockIdx.x;
+  const int s = sl.stream[b];
+  const int T = a.t.max_tracks;
+  const int Dmax = a.t.max_dets;
+  const int nt = a.t.n_tracks[s];
+  const int D = det_count(a, b);
+  const bool trans = nt > D;
+  const int R = trans ? D : nt;   // rows
+  const int M = trans ? nt : D;   // cols
+  const int MM = T > Dmax ? T : Dmax;
+  double* u = reinterpret_cast<double*>(smem);
+  double* v = u + (MM + 1);
+  double* minv = v + (MM + 1);
+  int* p = reinterpret_cast<int*>(minv + (MM + 1));
+  int* way = p + (MM + 1);
+  int* trk_det = way + (MM + 1);     // [T] by order index
+  int* det_trk = trk_det + T;        // [Dmax]
+  int* new_order = det_trk + Dmax;   // [T]
+  uint8_t* used = reinterpret_cast<uint8_t*>(new_order + T);
+  __shared__ int s_fail, s_nnew, s_births;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double* A = a.t.cost + (size_t)b * T * Dmax;
+  const float* rows = a.rows + (size_t)b * a.cap * 518;
+  for (int k = tid; k < T; k += blockDim.x) trk_det[k] = -1;
+  for (int j = tid; j < Dmax; j += blockDim.x) det_trk[j] = -1;
+  if (tid == 0) s_fail = 0;
+  __syncthreads();
+
+  if (warp == 0 && R > 0) {
+    for (int j = lane; j <= M; j += 32) {
+      v[j] = 0.0;
+      p[j] = 0;
+      way[j] = 0;
+    }
+    for (int i = lane; i <= R; i += 32) u[i] = 0.0;
+    __syncwarp();
+    for (int i = 1; i <= R && !s_fail; ++i) {
+      if (lane == 0) p[0] = i;
+      for (int j = lane; j <= M; j += 32) {
+        minv[j] = INFINITY;
+        used[j] = 0;
+      }
+      __syncwarp();
+      int j0 = 0;
+      for (int iter = 0; iter <= M; ++iter) {
+        if (lane == 0) used[j0] = 1;
+        __syncwarp();
+        const int i0 = p[j0];
+        const double ui0 = u[i0];
+        const double* arow = A + (size_t)(i0 - 1) * M;
+        double best = INFINITY;
+        int bestj = 0x7fffffff;
+        for (int j = lane + 1; j <= M; j += 32) {
+          if (!used[j]) {
+            const double cur = (arow[j - 1] - ui0) - v[j];
+            if (cur < minv[j]) {
+              minv[j] = cur;
+              way[j] = j0;
+            }
+            if (minv[j] < best) {
+              best = minv[j];
+              bestj = j;
+            }
+          }
+        }
+        argmin_warp(best, bestj);
+        if (bestj == 0x7fffffff) {   // no finite free column: cost matrix holds NaN
+          if (lane == 0) s_fail = 1;
+          break;
+        }
+        const double delta = best;
+        for (int j = lane; j <= M; j += 32) {
+          if (used[j]) {
+            u[p[j]] += delta;
+            v[j] -= delta;
+          } else {
+            minv[j] -= delta;
+          }
+        }
+        __syncwarp();
+        j0 = bestj;
+        if (p[j0] == 0) break;
+      }
+      __syncwarp();
+      if (lane == 0 && !s_fail) {
+        int jj = j0;
+        for (int guard = 0; guard <= M && jj; ++guard) {
+          const int j1 = way[jj];
+          p[jj] = p[j1];
+          jj = j1;
+        }
+      }
+      __syncwarp();
+    }
+    // pairs, rejected when the (gated) cost is above the threshold
+    for (int j = lane + 1; j <= M; j += 32) {
+      if (!p[j] || s_fail) continue;
+      const int r = p[j] - 1, c = j - 1;
+      const double cost = A[(size_t)r * M + c];
+      if (cost > (double)a.assign_thresh || cost >= INF_COST) continue;
+      const int k = trans ? c : r, d = trans ? r : c;
+      trk_det[k] = d;
+      det_trk[d] = k;
+    }
+  }
+  __syncthreads();
+  if (s_fail) flag_error(a.err, KERR_TIMEOUT);
+
+  // Kalman update of assigned tracks, lost bookkeeping (one thread per track)
+  for (int k = tid; k < nt; k += blockDim.x) {
+    const int slot = a.t.order[(size_t)s * T + k];
+    const size_t ts = (size_t)s * T + slot;
+    const int d = trk_det[k];
+    if (d >= 0) {
+      double z[4];
+      measurement(rows + (size_t)d * 518, z);
+      double* m = a.t.mean + ts * 8;
+      double* P = a.t.cov + ts * 64;
+      const double* L = a.t.gate_l + ((size_t)b * T + slot) * 16;
+      const double hp = m[3];
+      const double rp = (SP * hp) * (SP * hp);
+      double S[16];
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) S[i * 4 + j] = P[i * 8 + j];
+      S[0] += rp;
+      S[5] += rp;
+      S[10] += 1e-1 * 1e-1;
+      S[15] += rp;
+      // K row i solves (L L^T) k = (P H^T)[i]
+      double K[32];
+      for (int i = 0; i < 8; ++i) {
+        double t[4];
+        for (int r = 0; r < 4; ++r) {
+          double vv = P[i * 8 + r];
+          for (int c = 0; c < r; ++c) vv -= L[r * 4 + c] * t[c];
+          t[r] = vv / L[r * 4 + r];
+        }
+        for (int r = 3; r >= 0; --r) {
+          double vv = t[r];
+          for (int c = r + 1; c < 4; ++c) vv -= L[c * 4 + r] * K[i * 4 + c];
+          K[i * 4 + r] = vv / L[r * 4 + r];
+        }
+      }
+      double y[4];
+      for (int r = 0; r < 4; ++r) y[r] = z[r] - m[r];
+      for (int i = 0; i < 8; ++i) {
+        double acc = 0.0;
+        for (int r = 0; r < 4; ++r) acc += K[i * 4 + r] * y[r];
+        m[i] += acc;
+      }
+      double KS[32];
+      for (int i = 0; i < 8; ++i)
+        for (int c = 0; c < 4; ++c) {
+          double acc = 0.0;
+          for (int r = 0; r < 4; ++r) acc += K[i * 4 + r] * S[r * 4 + c];
+          KS[i * 4 + c] = acc;
+        }
+      for (int i = 0; i < 8; ++i)
+        for (int j = 0; j < 8; ++j) {
+          double acc = 0.0;
+          for (int c = 0; c < 4; ++c) acc += KS[i * 4 + c] * K[j * 4 + c];
+          P[i * 8 + j] -= acc;
+        }
+      a.t.state[ts] = JDE_TRACK_TRACKED;
+      a.t.since[ts] = 0;
+      a.t.last_det[ts] = d;
+    } else {
+      a.t.state[ts] = JDE_TRACK_LOST;
+      a.t.since[ts] += 1;
+      a.t.last_det[ts] = -1;
+    }
+  }
+  __syncthreads();
+  // gallery update of assigned tracks (one warp per track): e <- normalise(m e + (1 - m) d)
+  for (int k = warp; k < nt; k += blockDim.x / 32) {
+    const int d = trk_det[k];
+    if (d < 0) continue;
+    const int slot = a.t.order[(size_t)s * T + k];
+    float* e = a.t.emb + ((size_t)s * T + slot) * 512;
+    const float* dv = rows + (size_t)d * 518 + 6;
+    float vals[16], ss = 0.f;
+    for (int q = 0; q < 16; ++q) {
+      const int c = q * 32 + lane;
+      vals[q] = a.momentum * e[c] + (1.f - a.momentum) * dv[c];
+      ss += vals[q] * vals[q];
+    }
+    for (int off = 16; off > 0; off >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, off);
+    const float inv = ss > 0.f ? 1.f / sqrtf(ss) : 0.f;
+    for (int q = 0; q < 16; ++q) e[q * 32 + lane] = vals[q] * inv;
+  }
+  __syncthreads();
+  // removal, order compaction and births (serial bookkeeping on one thread; O(T + D) integer work)
+  if (tid == 0) {
+    int nn = 0;
+    int top = a.t.free_top[s];
+    for (int k = 0; k < nt; ++k) {
+      const int slot = a.t.order[(size_t)s * T + k];
+      const size_t ts = (size_t)s * T + slot;
+      if (a.t.state[ts] == JDE_TRACK_LOST && a.t.since[ts] > a.lost_max) {
+        a.t.free_stack[(size_t)s * T + top++] = slot;
+        continue;
+      }
+      new_order[nn++] = slot;
+    }
+    int births = 0;
+    long long nid = a.t.next_id[s];
+    for (int j = 0; j < D; ++j) {
+      if (det_trk[j] >= 0) continue;
+      if (top == 0 || nn >= T) {
+        flag_error(a.err, KERR_CAPACITY);
+        break;
+      }
+      const int slot = a.t.free_stack[(size_t)s * T + --top];
+      const size_t ts = (size_t)s * T + slot;
+      a.t.id[ts] = nid++;
+      a.t.state[ts] = JDE_TRACK_TRACKED;
+      a.t.since[ts] = 0;
+      a.t.last_det[ts] = j;
+      det_trk[j] = -2 - slot;   // marks the birth slot for the parallel init below
+      new_order[nn++] = slot;
+      ++births;
+    }
+    a.t.next_id[s] = nid;
+    a.t.free_top[s] = top;
+    s_nnew = nn;
+    s_births = births;
+  }
+  __syncthreads();
+  const int nn = s_nnew;
+  for (int k = tid; k < nn; k += blockDim.x) a.t.order[(size_t)s * T + k] = new_order[k];
+  // initialise born tracks: x = (z, 0), P0 from the measured height, gallery = detection embedding
+  for (int j = tid; j < D; j += blockDim.x) {
+    if (det_trk[j] > -2) continue;
+    const int slot = -2 - det_trk[j];
+    const size_t ts = (size_t)s * T + slot;
+    double z[4];
+    measurement(rows + (size_t)j * 518, z);
+    double* m = a.t.mean + ts * 8;
+    double* P = a.t.cov + ts * 64;
+    for (int i = 0; i < 4; ++i) {
+      m[i] = z[i];
+      m[i + 4] = 0.0;
+    }
+    for (int i = 0; i < 64; ++i) P[i] = 0.0;
+    const double h = z[3];
+    const double sp2 = (2 * SP * h) * (2 * SP * h), sv2 = (10 * SV * h) * (10 * SV * h);
+    P[0] = sp2;
+    P[9] = sp2;
+    P[18] = 1e-2 * 1e-2;
+    P[27] = sp2;
+    P[36] = sv2;
+    P[45] = sv2;
+    P[54] = 1e-5 * 1e-5;
+    P[63] = sv2;
+  }
+  for (int j = warp; j < D; j += blockDim.x / 32) {
+    if (det_trk[j] > -2) continue;
+    const int slot = -2 - det_trk[j];
+    float* e = a.t.emb + ((size_t)s * T + slot) * 512;
+    const float* dv = rows + (size_t)j * 518 + 6;
+    for (int q = 0; q < 16; ++q) e[q * 32 + lane] = dv[q * 32 + lane];
+  }
+  if (tid == 0) a.t.n_tracks[s] = nn;
+  __syncthreads();
+  // output in track order
+  if (tid == 0) a.o_count[b] = nn;
+  for (int k = tid; k < nn && k < a.o_cap; k += blockDim.x) {
+    const int slot = new_order[k];
+    const size_t ts = (size_t)s * T + slot;
+    const double* m = a.t.mean + ts * 8;
+    const size_t o = (size_t)b * a.o_cap + k;
+    const double w = m[2] * m[3];
+    a.o_id[o] = a.t.id[ts];
+    a.o_box[o * 4 + 0] = (float)(m[0] - w / 2);
+    a.o_box[o * 4 + 1] = (float)(m[1] - m[3] / 2);
+    a.o_box[o * 4 + 2] = (float)(m[0] + w / 2);
+    a.o_box[o * 4 + 3] = (float)(m[1] + m[3] / 2);
+    a.o_state[o] = a.t.state[ts];
+    if (a.o_det) a.o_det[o] = a.t.last_det[ts];
+  }
+}
+
+size_t assign_smem(const TrackState& t) {
+  const int MM = t.max_tracks > t.max_dets ? t.max_tracks : t.max_dets;
+  return sizeof(double) * 3 * (MM + 1) + sizeof(int) * 2 * (MM + 1) + sizeof(int) * (2 * t.max_tracks + t.max_dets) +
+         (MM + 1) + 16;
+}
+
+bool dalloc(void** p, size_t bytes) {
+  if (cudaMalloc(p, bytes ? bytes : 16) != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+int track_alloc(TrackState& t, const jde_config& cfg) {
+  t.max_streams = cfg.max_streams;
+  t.max_tracks = cfg.max_tracks;
+  t.max_dets = cfg.max_track_dets;
+  t.max_batch = cfg.max_batch < MAXB ? cfg.max_batch : MAXB;
+  const size_t S = t.max_streams, T = t.max_tracks, B = t.max_batch, D = t.max_dets;
+  bool ok = dalloc((void**)&t.n_tracks, sizeof(int) * S) && dalloc((void**)&t.next_id, sizeof(long long) * S) &&
+            dalloc((void**)&t.order, sizeof(int) * S * T) && dalloc((void**)&t.free_stack, sizeof(int) * S * T) &&
+            dalloc((void**)&t.free_top, sizeof(int) * S) && dalloc((void**)&t.id, sizeof(long long) * S * T) &&
+            dalloc((void**)&t.state, sizeof(int) * S * T) && dalloc((void**)&t.since, sizeof(int) * S * T) &&
+            dalloc((void**)&t.mean, sizeof(double) * S * T * 8) && dalloc((void**)&t.cov, sizeof(double) * S * T * 64) &&
+            dalloc((void**)&t.emb, sizeof(float) * S * T * 512) && dalloc((void**)&t.last_det, sizeof(int) * S * T) &&
+            dalloc((void**)&t.gate_l, sizeof(double) * B * T * 16) && dalloc((void**)&t.gate_z, sizeof(double) * B * T * 4) &&
+            dalloc((void**)&t.cost, sizeof(double) * B * T * D) && dalloc((void**)&t.slot_stream, sizeof(int) * B);
+  if (!ok) return 1;
+  if (cudaFuncSetAttribute(assign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)assign_smem(t)) !=
+      cudaSuccess)
+    return 1;
+  for (int s = 0; s < t.max_streams; ++s) reset_kernel<<<1, 256>>>(t, s);
+  return cudaDeviceSynchronize() == cudaSuccess ? 0 : 1;
+}
+
+void track_free(TrackState& t) {
+  void* ptrs[] = {t.n_tracks, t.next_id, t.order, t.free_stack, t.free_top, t.id, t.state, t.since, t.mean, t.cov,
+                  t.emb, t.last_det, t.gate_l, t.gate_z, t.cost, t.slot_stream, t.rows_stage, t.count_stage,
+                  t.o_id, t.o_box, t.o_state, t.o_det, t.o_count};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  t = TrackState();
+}
+
+int track_reset(TrackState& t, int s, cudaStream_t st) {
+  reset_kernel<<<1, 256, 0, st>>>(t, s);
+  return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+int track_step(TrackState& t, const jde_config& cfg, int n, const int32_t* stream_ids, const jde_dets* dets,
+               jde_tracks* out, int* err, cudaStream_t st, char* msg, size_t msg_len) {
+  if (n < 1 || n > t.max_batch || !stream_ids || !dets || !out || !dets->rows || !dets->count || dets->cap < 1 ||
+      !out->id || !out->box || !out->state || !out->count || out->cap < 1) {
+    snprintf(msg, msg_len, "bad arguments (n=%d, at most %d streams per call)", n, t.max_batch);
+    return JDE_ERR_INVALID_ARG;
+  }
+  Slots sl;
+  for (int i = 0; i < n; ++i) {
+    if (stream_ids[i] < 0 || stream_ids[i] >= t.max_streams) {
+      snprintf(msg, msg_len, "stream id %d out of range", stream_ids[i]);
+      return JDE_ERR_NOT_FOUND;
+    }
+    for (int j = 0; j < i; ++j)
+      if (stream_ids[j] == stream_ids[i]) {
+        snprintf(msg, msg_len, "stream id %d appears twice in one call", stream_ids[i]);
+        return JDE_ERR_INVALID_ARG;
+      }
+    sl.stream[i] = stream_ids[i];
+  }
+  const float* rows = dets->rows;
+  const int32_t* count = dets->count;
+  if (!dets->on_device) {
+    const size_t need = (size_t)t.max_batch * dets->cap * 518;
+    static size_t have = 0;
+    if (!t.rows_stage || need > have) {
+      cudaFree(t.rows_stage);
+      cudaFree(t.count_stage);
+      if (!dalloc((void**)&t.rows_stage, sizeof(float) * need) ||
+          !dalloc((void**)&t.count_stage, sizeof(int32_t) * t.max_batch)) {
+        snprintf(msg, msg_len, "detection staging");
+        return JDE_ERR_OOM;
+      }
+      have = need;
+    }
+    if (cudaMemcpyAsync(t.rows_stage, dets->rows, sizeof(float) * (size_t)n * dets->cap * 518, cudaMemcpyHostToDevice,
+                        st) != cudaSuccess ||
+        cudaMemcpyAsync(t.count_stage, dets->count, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      snprintf(msg, msg_len, "staging copy failed");
+      return JDE_ERR_CUDA;
+    }
+    rows = t.rows_stage;
+    count = t.count_stage;
+  }
+  StepArgs a;
+  a.t = t;
+  a.rows = rows;
+  a.count = count;
+  a.cap = dets->cap;
+  a.n = n;
+  a.gate = cfg.gate_chi2;
+  a.assign_thresh = cfg.assign_thresh;
+  a.lost_max = cfg.lost_max_frames;
+  a.momentum = cfg.emb_momentum;
+  a.err = err;
+  a.o_cap = out->cap;
+  if (out->on_device) {
+    a.o_id = reinterpret_cast<long long*>(out->id);
+    a.o_box = out->box;
+    a.o_state = out->state;
+    a.o_det = out->det;
+    a.o_count = out->count;
+  } else {
+    if (!t.o_id || out->cap > t.o_cap) {
+      void* ptrs[] = {t.o_id, t.o_box, t.o_state, t.o_det, t.o_count};
+      for (void* p : ptrs)
+        if (p) cudaFree(p);
+      const size_t c = (size_t)t.max_batch * out->cap;
+      if (!(dalloc((void**)&t.o_id, sizeof(long long) * c) && dalloc((void**)&t.o_box, sizeof(float) * 4 * c) &&
+            dalloc((void**)&t.o_state, sizeof(int32_t) * c) && dalloc((void**)&t.o_det, sizeof(int32_t) * c) &&
+            dalloc((void**)&t.o_count, sizeof(int32_t) * t.max_batch))) {
+        snprintf(msg, msg_len, "track output staging");
+        return JDE_ERR_OOM;
+      }
+      t.o_cap = out->cap;
+      a.t = t;
+    }
+    a.o_id = t.o_id;
+    a.o_box = t.o_box;
+    a.o_state = t.o_state;
+    a.o_det = t.o_det;
+    a.o_count = t.o_count;
+  }
+  dim3 gp((t.max_tracks + 127) / 128, n);
+  prep_kernel<<<gp, 128, 0, st>>>(a, sl);
+  dim3 gc((t.max_tracks + 31) / 32, (t.max_dets + 31) / 32, n);
+  cost_kernel<<<gc, 256, 0, st>>>(a, sl);
+  assign_kernel<<<n, 256, assign_smem(t), st>>>(a, sl);
+  if (cudaGetLastError() != cudaSuccess) {
+    snprintf(msg, msg_len, "tracker launch failed");
+    return JDE_ERR_CUDA;
+  }
+  if (!out->on_device) {
+    const size_t c = (size_t)n * out->cap;
+    bool ok = cudaMemcpyAsync(out->count, a.o_count, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+              cudaMemcpyAsync(out->id, a.o_id, sizeof(long long) * c, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+              cudaMemcpyAsync(out->box, a.o_box, sizeof(float) * 4 * c, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+              cudaMemcpyAsync(out->state, a.o_state, sizeof(int32_t) * c, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+              (!out->det ||
+               cudaMemcpyAsync(out->det, a.o_det, sizeof(int32_t) * c, cudaMemcpyDeviceToHost, st) == cudaSuccess) &&
+              cudaStreamSynchronize(st) == cudaSuccess;
+    if (!ok) {
+      snprintf(msg, msg_len, "track output copy failed");
+      return JDE_ERR_CUDA;
+    }
+    for (int i = 0; i < n; ++i)
+      if (out->count[i] > out->cap) {
+        snprintf(msg, msg_len, "stream %d has %d tracks, cap is %d", stream_ids[i], out->count[i], out->cap);
+        return JDE_ERR_CAPACITY;
+      }
+  }
+  return JDE_OK;
+}

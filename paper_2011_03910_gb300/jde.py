@@ -1,0 +1,190 @@
+"""Thin ctypes binding of libjde (include/jde.h): same names, argument marshalling only.
+
+Every computation happens in the CUDA library.  Device memory is passed as
+raw pointers; ``torch`` tensors are accepted wherever a pointer is expected
+(their ``data_ptr()`` is used), host numpy arrays where host memory is
+expected.  Importing this module loads ``libjde.so`` and fails loudly if it
+has not been built (``python -m paper_2011_03910_gb300._build``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libjde.so")
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"libjde.so is not built ({_LIB_PATH}); run python -m paper_2011_03910_gb300._build")
+lib = C.CDLL(_LIB_PATH)
+
+JDE_OK = 0
+JDE_FP32, JDE_BF16 = 0, 1
+JDE_TRACK_TRACKED, JDE_TRACK_LOST = 1, 2
+JDE_ROW, JDE_EMB, JDE_NUM_LAYERS = 518, 512, 78
+STATUS = {0: "JDE_OK", 1: "JDE_ERR_INVALID_ARG", 2: "JDE_ERR_OOM", 3: "JDE_ERR_CUDA", 4: "JDE_ERR_CAPACITY",
+          5: "JDE_ERR_ADMISSION", 6: "JDE_ERR_TIMEOUT", 7: "JDE_ERR_NOT_FOUND", 8: "JDE_ERR_WEIGHTS",
+          9: "JDE_ERR_UNSUPPORTED"}
+
+
+class jde_config(C.Structure):
+    _fields_ = [("precision", C.c_int), ("max_batch", C.c_int), ("max_in_w", C.c_int), ("max_in_h", C.c_int),
+                ("max_src_w", C.c_int), ("max_src_h", C.c_int), ("max_cand", C.c_int), ("conf_thresh", C.c_float),
+                ("nms_iou", C.c_float), ("assign_thresh", C.c_float), ("gate_chi2", C.c_double),
+                ("lost_max_frames", C.c_int), ("emb_momentum", C.c_float), ("max_streams", C.c_int),
+                ("max_tracks", C.c_int), ("max_track_dets", C.c_int), ("device", C.c_int)]
+
+
+class jde_layer_desc(C.Structure):
+    _fields_ = [("cin", C.c_int), ("cout", C.c_int), ("k", C.c_int), ("stride", C.c_int), ("has_bn", C.c_int),
+                ("res_nblocks", C.c_int)]
+
+
+class jde_dets(C.Structure):
+    _fields_ = [("rows", C.c_void_p), ("count", C.c_void_p), ("anchor_index", C.c_void_p), ("cap", C.c_int),
+                ("on_device", C.c_int)]
+
+
+class jde_tracks(C.Structure):
+    _fields_ = [("id", C.c_void_p), ("box", C.c_void_p), ("state", C.c_void_p), ("det", C.c_void_p),
+                ("count", C.c_void_p), ("cap", C.c_int), ("on_device", C.c_int)]
+
+
+_P = C.c_void_p
+_sig = {
+    "jde_default_config": (None, [C.POINTER(jde_config)]),
+    "jde_layer_table": (C.c_int, [C.POINTER(jde_layer_desc), C.c_int]),
+    "jde_create": (C.c_int, [C.POINTER(jde_config), _P, C.c_size_t, C.POINTER(_P)]),
+    "jde_destroy": (None, [_P]),
+    "jde_last_error": (C.c_char_p, [_P]),
+    "jde_forward": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _P]),
+    "jde_postprocess": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(jde_dets), _P]),
+    "jde_detect_batch": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                   C.POINTER(jde_dets), _P]),
+    "jde_track_step": (C.c_int, [_P, C.c_int, _P, C.POINTER(jde_dets), C.POINTER(jde_tracks), _P]),
+    "jde_stream_reset": (C.c_int, [_P, C.c_int, _P]),
+    "jde_get_tensor": (C.c_int, [_P, C.c_int, _P, C.c_size_t, C.POINTER(C.c_int), C.POINTER(C.c_int), _P]),
+    "jde_kernel_errors": (C.c_int, [_P, C.POINTER(C.c_int), _P]),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_sig)
+
+
+class JdeError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def ptr(x) -> int | None:
+    """Raw address of a torch tensor, numpy array, int or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def stream_ptr(s) -> int | None:
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(h, status):
+    if status != JDE_OK:
+        raise JdeError(status, lib.jde_last_error(h).decode(errors="replace"))
+
+
+def jde_default_config() -> jde_config:
+    cfg = jde_config()
+    lib.jde_default_config(C.byref(cfg))
+    return cfg
+
+
+def jde_layer_table():
+    """List of (cin, cout, k, stride, has_bn, res_nblocks) in weights-blob order."""
+    n = lib.jde_layer_table(None, 0)
+    arr = (jde_layer_desc * n)()
+    lib.jde_layer_table(arr, n)
+    return [(d.cin, d.cout, d.k, d.stride, bool(d.has_bn), d.res_nblocks) for d in arr]
+
+
+def jde_create(cfg: jde_config, blob: bytes):
+    h = _P()
+    buf = C.create_string_buffer(blob, len(blob))
+    _check(None, lib.jde_create(C.byref(cfg), buf, len(blob), C.byref(h)))
+    return h
+
+
+def jde_destroy(h) -> None:
+    lib.jde_destroy(h)
+
+
+def jde_last_error(h=None) -> str:
+    return lib.jde_last_error(h).decode(errors="replace")
+
+
+def jde_forward(h, frames, n, src_w, src_h, in_w, in_h, on_device=True, stream=None):
+    _check(h, lib.jde_forward(h, ptr(frames), n, src_w, src_h, in_w, in_h, int(on_device), stream_ptr(stream)))
+
+
+def make_dets(rows, count, anchor_index=None, cap=None, on_device=True) -> jde_dets:
+    d = jde_dets()
+    d.rows, d.count, d.anchor_index = ptr(rows), ptr(count), ptr(anchor_index)
+    d.cap = int(cap if cap is not None else rows.shape[1])
+    d.on_device = int(on_device)
+    return d
+
+
+def make_tracks(ids, box, state, det, count, cap=None, on_device=True) -> jde_tracks:
+    t = jde_tracks()
+    t.id, t.box, t.state, t.det, t.count = ptr(ids), ptr(box), ptr(state), ptr(det), ptr(count)
+    t.cap = int(cap if cap is not None else ids.shape[1])
+    t.on_device = int(on_device)
+    return t
+
+
+def jde_postprocess(h, heads, n, in_w, in_h, src_w, src_h, dets: jde_dets, stream=None):
+    arr = None
+    if heads is not None:
+        arr = (_P * 6)(*[ptr(x) for x in heads])
+    _check(h, lib.jde_postprocess(h, arr, n, in_w, in_h, src_w, src_h, C.byref(dets), stream_ptr(stream)))
+
+
+def jde_detect_batch(h, frames, n, src_w, src_h, in_w, in_h, dets: jde_dets, on_device=True, stream=None):
+    _check(h, lib.jde_detect_batch(h, ptr(frames), n, src_w, src_h, in_w, in_h, int(on_device), C.byref(dets),
+                                   stream_ptr(stream)))
+
+
+def jde_track_step(h, stream_ids, dets: jde_dets, tracks: jde_tracks, stream=None):
+    ids = np.ascontiguousarray(stream_ids, dtype=np.int32)
+    _check(h, lib.jde_track_step(h, len(ids), ids.ctypes.data, C.byref(dets), C.byref(tracks), stream_ptr(stream)))
+
+
+def jde_stream_reset(h, stream_id, stream=None):
+    _check(h, lib.jde_stream_reset(h, stream_id, stream_ptr(stream)))
+
+
+def jde_get_tensor(h, tid, dst=None, dst_bytes=0, stream=None):
+    """Returns ((n, h, w, c), dtype) and copies into dst (device) when given."""
+    dims = (C.c_int * 4)()
+    dt = C.c_int()
+    _check(h, lib.jde_get_tensor(h, tid, ptr(dst), dst_bytes, dims, C.byref(dt), stream_ptr(stream)))
+    return tuple(dims), dt.value
+
+
+def jde_kernel_errors(h, stream=None) -> int:
+    w = C.c_int()
+    _check(h, lib.jde_kernel_errors(h, C.byref(w), stream_ptr(stream)))
+    return w.value

@@ -179,8 +179,10 @@ def random_heads(seed: int, batch: int, grids, tobj_mean: float = -2.0, tobj_std
 class PlantedClip:
     """Objects planted on constant-velocity paths into JDE head tensors.
 
-    Object ``o`` has a fixed size (w, h) in frame pixels and moves on a straight
-    line that stays inside the frame for the whole clip; each frame its centre
+    Object ``o`` has a fixed size (w, h) in frame pixels (h ~ U(80, 320),
+    w/h ~ U(0.35, 0.5)) and moves at a constant velocity of at most
+    ``max_speed`` px/frame per axis on a path that stays inside the frame for
+    the whole clip; each frame its centre
     gets N(0, ``jitter``) px noise, and it is hidden with probability ``occl``.
     Each object carries a unit identity vector ``u_o``; its cell in the
     embedding map holds ``u_o + n`` with ``n`` an isotropic Gaussian vector of
@@ -201,7 +203,8 @@ class PlantedClip:
     """
 
     def __init__(self, seed, n_objects, n_frames, in_w, in_h, anchors, strides, ratio, pad_x, pad_y,
-                 src_w=SRC_W, src_h=SRC_H, occl=0.1, jitter=2.0, emb_noise=0.1, emb_noise_per_dim=False):
+                 src_w=SRC_W, src_h=SRC_H, occl=0.1, jitter=2.0, emb_noise=0.1, emb_noise_per_dim=False,
+                 max_speed=3.0):
         self.seed, self.n, self.T = seed, n_objects, n_frames
         self.in_w, self.in_h = in_w, in_h
         self.anchors, self.strides = anchors, strides
@@ -212,12 +215,14 @@ class PlantedClip:
         h = g.uniform(80.0, 320.0, n_objects)
         w = h * g.uniform(0.35, 0.5, n_objects)
         self.size = np.stack([w, h], 1)
-        lo_x, hi_x = w / 2 + 4, src_w - w / 2 - 4
-        lo_y, hi_y = h / 2 + 4, src_h - h / 2 - 4
-        p0 = np.stack([g.uniform(lo_x, hi_x), g.uniform(lo_y, hi_y)], 1)
-        p1 = np.stack([g.uniform(lo_x, hi_x), g.uniform(lo_y, hi_y)], 1)
-        self.start = p0
-        self.vel = (p1 - p0) / max(n_frames - 1, 1)
+        # velocity up to max_speed px/frame per axis; the start is drawn so the whole path stays inside
+        self.vel = g.uniform(-max_speed, max_speed, (n_objects, 2))
+        span = self.vel * max(n_frames - 1, 1)
+        lo_x = w / 2 + 4 + np.maximum(0, -span[:, 0])
+        hi_x = src_w - w / 2 - 4 - np.maximum(0, span[:, 0])
+        lo_y = h / 2 + 4 + np.maximum(0, -span[:, 1])
+        hi_y = src_h - h / 2 - 4 - np.maximum(0, span[:, 1])
+        self.start = np.stack([g.uniform(lo_x, hi_x), g.uniform(lo_y, hi_y)], 1)
         ident = g.standard_normal((n_objects, 512))
         self.ident = ident / np.linalg.norm(ident, axis=1, keepdims=True)
         # isotropic noise with E|n| = emb_noise (per-dim sigma emb_noise/sqrt(512)),

@@ -1,0 +1,101 @@
+"""Helpers shared by the GPU parity tests: handles, forward runs, head/row extraction, tie detection."""
+from __future__ import annotations
+
+import functools
+
+import numpy as np
+import torch
+
+import synth
+from oracle import network as net
+from oracle import postprocess as pp
+
+
+@functools.lru_cache(maxsize=None)
+def blob() -> bytes:
+    return synth.weights_blob(net.layer_specs())
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_layers():
+    return synth.parse_blob(blob())
+
+
+def jde():
+    from paper_2011_03910_gb300 import _build
+    _build.build()
+    from paper_2011_03910_gb300 import jde as j
+    return j
+
+
+def make_handle(precision, max_batch=2, in_w=320, in_h=192, src_w=1920, src_h=1080, **kw):
+    j = jde()
+    cfg = j.jde_default_config()
+    cfg.precision = precision
+    cfg.max_batch = max_batch
+    cfg.max_in_w, cfg.max_in_h = in_w, in_h
+    cfg.max_src_w, cfg.max_src_h = src_w, src_h
+    for k, v in kw.items():
+        setattr(cfg, k, v)
+    return j.jde_create(cfg, blob())
+
+
+HEAD_LAYERS = [58, 67, 76, 59, 68, 77]     # det 1x1 of strides 32/16/8, then emb 3x3 of strides 32/16/8
+
+
+def get_tensor(h, tid):
+    j = jde()
+    dims, dt = j.jde_get_tensor(h, tid)
+    t = torch.empty(dims, dtype=torch.float32 if dt == 0 else torch.bfloat16, device="cuda")
+    j.jde_get_tensor(h, tid, t, t.numel() * t.element_size(), torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    return t.float().cpu().numpy().astype(np.float64)
+
+
+def forward(h, frames: np.ndarray, in_w, in_h):
+    j = jde()
+    f = torch.from_numpy(np.ascontiguousarray(frames)).cuda()
+    n, sh, sw, _ = frames.shape
+    j.jde_forward(h, f, n, sw, sh, in_w, in_h, True, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    assert j.jde_kernel_errors(h) == 0
+    return [get_tensor(h, l) for l in HEAD_LAYERS]
+
+
+def rel_maxabs(g, o):
+    return float(np.max(np.abs(g - o)) / np.max(np.abs(o)))
+
+
+def heads_to_device(dets, embs):
+    """Per-head numpy arrays [n, H, W, C] -> contiguous float32 CUDA tensors (det32, det16, det8, emb32, emb16, emb8)."""
+    return [torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda() for x in list(dets) + list(embs)]
+
+
+def postprocess(h, heads_dev, n, in_w, in_h, src_w, src_h, cap=4096):
+    j = jde()
+    rows = torch.zeros((n, cap, 518), dtype=torch.float32, device="cuda")
+    count = torch.zeros(n, dtype=torch.int32, device="cuda")
+    aidx = torch.full((n, cap), -1, dtype=torch.int32, device="cuda")
+    d = j.make_dets(rows, count, aidx, cap=cap)
+    j.jde_postprocess(h, heads_dev, n, in_w, in_h, src_w, src_h, d, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    assert j.jde_kernel_errors(h) == 0
+    return rows, count, aidx, d
+
+
+def nms_tie_frame(out, thr=pp.NMS_IOU, conf_band=1e-6, iou_band=1e-6):
+    """True when a decision of the oracle's frame lies within the tie band: two candidates
+    whose confidences differ by less than conf_band (relative) with IoU above threshold,
+    or a candidate pair whose IoU is within iou_band (relative) of the threshold."""
+    b = out["cand_boxes"]
+    c = out["cand_conf"]
+    n = len(b)
+    for i in range(n):
+        if i + 1 < n:
+            ious = pp.iou_many(b[i], b[i + 1:])
+            if np.any(np.abs(ious - thr) <= iou_band * thr):
+                return True
+            close = np.abs(c[i + 1:] - c[i]) <= conf_band * c[i]
+            if np.any(close & (ious > thr * (1 - iou_band))):
+                return True
+    return False
