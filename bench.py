@@ -1,0 +1,409 @@
+#!/usr/bin/env python
+"""Throughput of the JDE detect-and-track step on one GB300 (and N replicas).
+
+One step = the whole hot path over one batch: letterbox of B FullHD uint8
+frames to 1088x608, the 78-conv JDE network (BF16 tcgen05 implicit GEMM),
+decode + confidence filter + NMS + embedding L2 for every frame, and one
+tracker step (Kalman, cosine cost, gating, Hungarian, lifecycle) for each of
+the B video streams.  Frames are uniform random uint8 (stand-in for the
+FullHD MOT16 sequences of the paper's speed study, Sec. 5.1).  Random weights
+cannot detect anything in noise, so the post-processing and tracker consume
+head tensors with 50 planted objects per stream (constant-velocity paths),
+swapped in after the forward: the forward does its full work, the tracker gets
+a realistic, checkable load.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+of the same pipeline on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+SRC_W, SRC_H = 1920, 1080
+IN_W, IN_H = 1088, 608
+STRIDES = (32, 16, 8)
+METRIC = "JDE FPS at 1088x608: BF16/FP8 batched vs FP32 plain on one GB300; p99 latency"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--batch", type=int, default=16)
+    p.add_argument("--objects", type=int, default=50)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-fp32", action="store_true")
+    p.add_argument("--soak", type=int, default=40, help="untimed steps while the clock sampler starts")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------- helpers
+def conv_flops(table, in_w, in_h):
+    """2*M*N*K summed over the layer table (spatial sizes follow the DarkNet-53 + FPN chain)."""
+    sizes = [(in_h, in_w)]
+    h, w = in_h, in_w
+    for nb in (1, 2, 8, 8, 4):
+        h, w = (h + 1) // 2, (w + 1) // 2
+        sizes += [(h, w)] * (1 + 2 * nb)
+    for i, s in enumerate(STRIDES):
+        sizes += [(in_h // s, in_w // s)] * (9 if i < 2 else 8)
+    return sum(2 * hh * ww * co * ci * k * k for (ci, co, k, _, _, _), (hh, ww) in zip(table, sizes))
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while the GPU is under load."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def planted_clips(n_streams, n_frames, n_obj, anchors, ratio, px, py):
+    import synth
+    return [synth.PlantedClip(100 + s, n_obj, n_frames, IN_W, IN_H, anchors, STRIDES, ratio, px, py)
+            for s in range(n_streams)]
+
+
+def anchor_table():
+    """Anchor (w, h) per head as the library's decode uses them (pedestrian 1:3, sqrt(2) steps)."""
+    return [[(b * 2 ** (i / 2), 3 * b * 2 ** (i / 2)) for i in range(4)] for b in (128.0, 32.0, 8.0)]
+
+
+def letterbox_geometry(src_w, src_h, dst_w, dst_h):
+    import math
+    r = min(dst_w / src_w, dst_h / src_h)
+    nw, nh = int(math.floor(src_w * r + 0.5)), int(math.floor(src_h * r + 0.5))
+    return r, (dst_w - nw) // 2, (dst_h - nh) // 2
+
+
+def build_heads_device(torch, clips, t, device):
+    """Dense planted head tensors for frame t of every stream, built in HBM from the sparse entries."""
+    B = len(clips)
+    grids = [(IN_H // s, IN_W // s) for s in STRIDES]
+    dets = []
+    embs = []
+    for (gh, gw) in grids:
+        d = torch.zeros((B, gh, gw, 24), dtype=torch.float32, device=device)
+        d[..., 4::6] = -6.0
+        dets.append(d)
+        embs.append(torch.zeros((B, gh, gw, 512), dtype=torch.float32, device=device))
+    for b, c in enumerate(clips):
+        det_e, emb_e, _ = c.frame_entries(t)
+        for s in range(3):
+            de = [e for e in det_e if e[0] == s]
+            if de:
+                ys = torch.tensor([e[1] for e in de], device=device)
+                xs = torch.tensor([e[2] for e in de], device=device)
+                ch = torch.tensor([[6 * e[3] + k for k in range(6)] for e in de], device=device)
+                vals = torch.tensor([e[4] for e in de], dtype=torch.float32, device=device)
+                dets[s][b][ys[:, None], xs[:, None], ch] = vals
+            ee = [e for e in emb_e if e[0] == s]
+            if ee:
+                ys = torch.tensor([e[1] for e in ee], device=device)
+                xs = torch.tensor([e[2] for e in ee], device=device)
+                embs[s][b][ys, xs] = torch.from_numpy(np.stack([e[3] for e in ee])).to(device)
+    return dets + embs
+
+
+# ----------------------------------------------------------------------------- reference arm
+def cpu_oracle_frames(n_frames, seed_base=7):
+    """Time the FP64 oracle pipeline (letterbox, network, post-processing, tracker step) on
+    n_frames 1920x1080 frames at 1088x608, one frame per step; returns per-frame seconds."""
+    import synth
+    from oracle import network as net
+    from oracle import postprocess as pp
+    from oracle import tracker as tk
+    layers = synth.parse_blob(synth.weights_blob(net.layer_specs()))
+    r, nw, nh, px, py = net.letterbox_geometry(SRC_W, SRC_H, IN_W, IN_H)
+    clip = synth.PlantedClip(100, 50, max(n_frames, 1), IN_W, IN_H, pp.anchors(), pp.STRIDES, r, px, py)
+    T = tk.Tracker()
+    times = []
+    for i in range(n_frames):
+        frame = synth.frames_uniform(seed_base, 1, SRC_H, SRC_W, first=i)
+        dets_p, embs_p, _ = clip.frame(i)
+        t0 = time.perf_counter()
+        x = net.letterbox(frame, IN_W, IN_H)
+        net.forward(x, layers)
+        out = pp.postprocess_frame(dets_p, embs_p, r, px, py)
+        T.step(out["rows"])
+        times.append(time.perf_counter() - t0)
+    return times
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    steps, warm = args.steps, args.warmup
+    times = cpu_oracle_frames(steps + warm)[warm:]
+    total = sum(times)
+    v = steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "frames/s", "n_gpus": args.gpus,
+        "steps": steps, "warmup": warm, "ms_per_step": 1000 * total / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "JDE FP64 CPU oracle, 1088x608 letterboxed from 1920x1080 uint8, one frame per step"
+                   ", 50 planted objects for post-processing + tracking", "batch": 1, "in": [IN_W, IN_H]},
+        "cpu_baseline": {"value": v, "unit": "frames/s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": f"{steps} frames, one per step"},
+        "e2e": {"value": v, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- our arm
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    import torch
+    import synth
+    from paper_2011_03910_gb300 import _build
+    _build.build()
+    from paper_2011_03910_gb300 import jde
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    B, K, W = args.batch, args.steps, args.warmup
+    table = jde.jde_layer_table()
+    blob = synth.weights_blob(table)
+    cfg = jde.jde_default_config()
+    cfg.precision = jde.JDE_BF16
+    cfg.max_batch = B
+    cfg.max_streams = B
+    cfg.device = local
+    h = jde.jde_create(cfg, blob)
+    st = torch.cuda.current_stream()
+
+    # inputs resident in HBM: 4 distinct batches of frames, planted heads for every step
+    NF = 4
+    frames = [torch.from_numpy(synth.frames_uniform(1000 * (rank + 1) + i, B, SRC_H, SRC_W)).to(dev)
+              for i in range(NF)]
+    ratio, px, py = letterbox_geometry(SRC_W, SRC_H, IN_W, IN_H)
+    soak = args.soak
+    n_heads = W + soak + K
+    clips = planted_clips(B, n_heads, args.objects, anchor_table(), ratio, px, py)
+    heads = [build_heads_device(torch, clips, t, dev) for t in range(n_heads)]
+    cap = 256
+    rows = torch.zeros((B, cap, 518), dtype=torch.float32, device=dev)
+    count = torch.zeros(B, dtype=torch.int32, device=dev)
+    dets = jde.make_dets(rows, count, None, cap=cap)
+    tcap = 256
+    tr = [torch.zeros((B, tcap), dtype=torch.int64, device=dev), torch.zeros((B, tcap, 4), device=dev),
+          torch.zeros((B, tcap), dtype=torch.int32, device=dev), torch.zeros((B, tcap), dtype=torch.int32, device=dev),
+          torch.zeros(B, dtype=torch.int32, device=dev)]
+    tracks = jde.make_tracks(*tr, cap=tcap)
+    streams = list(range(B))
+
+    def step(t):
+        jde.jde_forward(h, frames[t % NF], B, SRC_W, SRC_H, IN_W, IN_H, True, st)
+        jde.jde_postprocess(h, heads[t], B, IN_W, IN_H, SRC_W, SRC_H, dets, st)
+        jde.jde_track_step(h, streams, dets, tracks, st)
+
+    for t in range(W):
+        step(t)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    for t in range(W, W + soak):      # keeps the GPU loaded while the clock sampler starts
+        step(t)
+    torch.cuda.synchronize()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    prof = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = jde.jde_launch_count()
+    evs[0].record(st)
+    for i in range(K):
+        jde.jde_set_profile_events(h, *prof[i])
+        step(W + soak + i)
+        evs[i + 1].record(st)
+    torch.cuda.synchronize()
+    l1 = jde.jde_launch_count()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    jde.jde_set_profile_events(h)
+    assert jde.jde_kernel_errors(h) == 0
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(K)]
+    total_ms = evs[0].elapsed_time(evs[K])
+    conv_ms = sum(p[1].elapsed_time(p[2]) for p in prof)
+    fwd_ms = sum(p[0].elapsed_time(p[2]) for p in prof)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * B * K / (total_ms / 1000.0)
+
+    # roofline of the convolutions (tcgen05 implicit GEMM): algorithmic FLOPs / measured conv time
+    flops_frame = conv_flops(table, IN_W, IN_H)
+    peaks, peak_kind = measured_peaks()
+    achieved = flops_frame * B * K / (conv_ms / 1000.0) / 1e12
+    peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "conv_tc_kernel (78 launches per step, aggregated)",
+                "peak_kind": f"{peak_kind} bf16 sustained"}
+
+    # e2e: host frames in (pinned), tracks out to host, through the same C ABI
+    pinned = [f.cpu().pin_memory() for f in frames]
+    tr_h = [np.zeros((B, tcap), np.int64), np.zeros((B, tcap, 4), np.float32), np.zeros((B, tcap), np.int32),
+            np.zeros((B, tcap), np.int32), np.zeros(B, np.int32)]
+    tracks_h = jde.make_tracks(*tr_h, cap=tcap, on_device=False)
+    h2d = B * SRC_W * SRC_H * 3
+    d2h = sum(x.nbytes for x in tr_h)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(K):
+        t = W + soak + i
+        jde.jde_forward(h, pinned[t % NF], B, SRC_W, SRC_H, IN_W, IN_H, False, st)
+        jde.jde_postprocess(h, heads[t], B, IN_W, IN_H, SRC_W, SRC_H, dets, st)
+        jde.jde_track_step(h, streams, dets, tracks_h, st)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * B * K / e2e_s, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    # plain FP32 batch-1 comparator (no graph): same step, one frame / one stream
+    fp32 = None
+    if not args.no_fp32 and rank == 0:
+        cfg32 = jde.jde_default_config()
+        cfg32.precision = jde.JDE_FP32
+        cfg32.max_batch = 1
+        cfg32.max_streams = 1
+        cfg32.device = local
+        h32 = jde.jde_create(cfg32, blob)
+        rows1 = torch.zeros((1, cap, 518), dtype=torch.float32, device=dev)
+        count1 = torch.zeros(1, dtype=torch.int32, device=dev)
+        dets1 = jde.make_dets(rows1, count1, None, cap=cap)
+        tr1 = [x[:1].clone() for x in tr]
+        tracks1 = jde.make_tracks(*tr1, cap=tcap)
+        n32 = max(5, K // 2)
+
+        def step32(t):
+            jde.jde_forward(h32, frames[t % NF][:1], 1, SRC_W, SRC_H, IN_W, IN_H, True, st)
+            jde.jde_postprocess(h32, [x[:1] for x in heads[t]], 1, IN_W, IN_H, SRC_W, SRC_H, dets1, st)
+            jde.jde_track_step(h32, [0], dets1, tracks1, st)
+
+        for t in range(3):
+            step32(t)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for i in range(n32):
+            step32(3 + i)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms32 = e0.elapsed_time(e1) / n32
+        fp32 = {"fps": 1000.0 / ms32, "ms_per_frame": ms32, "steps": n32, "batch": 1, "graph": False}
+        jde.jde_destroy(h32)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        ts = cpu_oracle_frames(1)
+        cpu = {"value": 1.0 / ts[0], "unit": "frames/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "1 frame 1920x1080 -> 1088x608: FP64 letterbox + network + post-processing + tracker step"}
+
+    if rank == 0:
+        srt = sorted(step_ms)
+        line = {
+            "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": f"JDE BF16, 1920x1080 uint8 -> 1088x608 letterbox, batch {B} ({B} streams), "
+                                   f"{args.objects} planted objects/stream for post-processing + tracking",
+                       "batch": B, "in": [IN_W, IN_H], "src": [SRC_W, SRC_H], "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2: ~5 GB of activations per step, 4 rotating 100 MB frame batches"},
+            "latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
+                           "what": "per batch step (every frame of the batch completes at its end)"},
+            "stages_ms_per_step": {"forward": fwd_ms / K, "convs": conv_ms / K,
+                                   "post_and_track": (total_ms - fwd_ms) / K},
+            "fp32_plain_batch1": fp32,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(l1 - l0),
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    jde.jde_destroy(h)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -183,6 +183,15 @@ jde_status jde_get_tensor(jde_handle* h, int id, void* dst, size_t dst_bytes, in
  * bit 1: capacity overflow); reading it synchronises `stream` and clears it. */
 jde_status jde_kernel_errors(jde_handle* h, int* word, void* stream);
 
+/* Number of kernels libjde has launched in this process (all handles), for launch accounting. */
+unsigned long long jde_launch_count(void);
+
+/* Stage timing: when set (cudaEvent_t values, or NULL to stop), jde_forward
+ * records forward_begin before the letterbox, conv_begin before the first
+ * convolution and conv_end after the last one, on the call's stream.  The
+ * events stay owned by the caller. */
+jde_status jde_set_profile_events(jde_handle* h, void* forward_begin, void* conv_begin, void* conv_end);
+
 #ifdef __cplusplus
 }
 #endif

@@ -9,6 +9,9 @@
 
 #define JDE_DEV __device__ __forceinline__
 
+// Process-wide count of kernels launched by libjde (host side, for launch accounting).
+void jde_count_launch(unsigned n = 1);
+
 // Bits of the per-handle device error word.
 enum : int { KERR_TIMEOUT = 1, KERR_CAPACITY = 2 };
 

@@ -285,6 +285,7 @@ cudaError_t launch_cfg(const TcPlan& p, const TcArgs& a, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
+  jde_count_launch();
   conv_tc_kernel<BN, BKC, STAGES><<<p.m_tiles * p.n_tiles, 128, Cfg::SMEM, st>>>(p, a);
   return cudaGetLastError();
 }

@@ -20,6 +20,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <map>
 #include <string>
 #include <tuple>
@@ -28,6 +29,9 @@
 #include "../../include/jde.h"
 #include "internal.h"
 #include "track.h"
+
+static std::atomic<unsigned long long> g_launches{0};
+void jde_count_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 namespace {
 
@@ -140,6 +144,7 @@ struct jde_handle {
   int32_t* aidx_stage = nullptr;
   size_t rows_stage_cap = 0;
   TrackState trk{};
+  cudaEvent_t prof[3] = {nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -479,6 +484,7 @@ jde_status load_weights(jde_handle* h, const void* blob, size_t nbytes) {
     const int rows = bf16 ? lw.k_tc : kpad16;
     const int cols = bf16 ? lw.cout_pad_tc : lw.cout_pad64;
     const long long total = (long long)rows * cols;
+    jde_count_launch();
     pack_kernel<<<(unsigned)((total + 255) / 256), 256>>>(
         W, gamma, beta, mean, var, bias, L[l].cin, L[l].cout, L[l].k, K, bf16 ? 0 : kpad16, bf16 ? 0 : lw.cout_pad64,
         lw.w_kn, bf16 ? lw.cout_pad_tc : 0, bf16 ? lw.k_tc : 0, lw.w_nk, lw.bias, bias_len);
@@ -665,6 +671,7 @@ jde_status jde_forward(jde_handle* h, const uint8_t* frames, int n, int src_w, i
   }
   const TView lb = view_of(*rb, T_LB, n);
   const bool bf16 = h->cfg.precision == JDE_BF16;
+  if (h->prof[0]) cudaEventRecord(h->prof[0], st);
   if (bf16) {
     letterbox_bf16x4_launch(frames, n, src_w, src_h, h->lb_x, h->lb_y, lb, st);
     stem_im2col_launch(lb, static_cast<__nv_bfloat16*>(rb->mem[T_IM2COL]), st);
@@ -672,6 +679,7 @@ jde_status jde_forward(jde_handle* h, const uint8_t* frames, int n, int src_w, i
     letterbox_f32_launch(frames, n, src_w, src_h, h->lb_x, h->lb_y, lb, st);
   }
   const auto& L = layers();
+  if (h->prof[1]) cudaEventRecord(h->prof[1], st);
   for (size_t l = 0; l < L.size(); ++l) {
     if (bf16) {
       cudaError_t e = conv_tc_launch(plan->tc[l], st);
@@ -680,6 +688,7 @@ jde_status jde_forward(jde_handle* h, const uint8_t* frames, int n, int src_w, i
       conv_simt_launch(plan->specs[l], h->w[l].w_kn, h->w[l].cout_pad64, st);
     }
   }
+  if (h->prof[2]) cudaEventRecord(h->prof[2], st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(h, JDE_ERR_CUDA, "forward launch: %s", cudaGetErrorString(e));
   h->cur = rb;
@@ -821,7 +830,7 @@ jde_status jde_get_tensor(jde_handle* h, int id, void* dst, size_t dst_bytes, in
   const int el = v.dtype ? 2 : 4;
   const long long total = (long long)v.n * v.h * v.w * v.c;
   if ((size_t)total * el > dst_bytes) return fail(h, JDE_ERR_CAPACITY, "jde_get_tensor: dst too small");
-  gather_view_kernel<<<(unsigned)((total + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(v, dst, el);
+  (jde_count_launch(), gather_view_kernel<<<(unsigned)((total + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(v, dst, el));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(h, JDE_ERR_CUDA, "gather: %s", cudaGetErrorString(e));
   return JDE_OK;
@@ -843,6 +852,16 @@ jde_status jde_track_step(jde_handle* h, int n, const int32_t* stream_ids, const
   const int r = track_step(h->trk, h->cfg, n, stream_ids, dets, out, h->d_err, static_cast<cudaStream_t>(stream), msg,
                            sizeof(msg));
   if (r != JDE_OK) return fail(h, (jde_status)r, "jde_track_step: %s", msg);
+  return JDE_OK;
+}
+
+unsigned long long jde_launch_count(void) { return g_launches.load(); }
+
+jde_status jde_set_profile_events(jde_handle* h, void* forward_begin, void* conv_begin, void* conv_end) {
+  if (!h) return fail(nullptr, JDE_ERR_INVALID_ARG, "handle is NULL");
+  h->prof[0] = static_cast<cudaEvent_t>(forward_begin);
+  h->prof[1] = static_cast<cudaEvent_t>(conv_begin);
+  h->prof[2] = static_cast<cudaEvent_t>(conv_end);
   return JDE_OK;
 }
 

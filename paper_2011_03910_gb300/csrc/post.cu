@@ -303,19 +303,25 @@ void post_launch(const float* const* heads, const HeadGeom& g, float conf_thresh
   const int n = g.n;
   cudaMemsetAsync(b.cand_count, 0, sizeof(int) * n, st);
   dim3 gf((g.off[3] + 255) / 256, n);
+  jde_count_launch();
   filter_kernel<<<gf, 256, 0, st>>>(heads[0], heads[1], heads[2], g, conf_thresh, b.cand_keys, b.cand_count,
                                     b.cand_cap);
+  jde_count_launch();
   select_sort_kernel<<<n, 1024, SORT_CAP * sizeof(uint64_t), st>>>(b.cand_keys, b.cand_count, b.cand_cap, b.sorted,
                                                                    b.n_sorted, b.kmax);
   dim3 gp((b.kmax + 127) / 128, n);
+  jde_count_launch();
   prep_kernel<<<gp, 128, 0, st>>>(heads[0], heads[1], heads[2], g, b.sorted, b.n_sorted, b.kmax, b.boxes, b.conf,
                                   b.cls);
   dim3 gm(b.kmax / 64, b.kmax / 64, n);
+  jde_count_launch();
   nms_mask_kernel<<<gm, 64, 0, st>>>(b.boxes, b.n_sorted, b.kmax, nms_iou, b.mask);
   const int wpb = 4;
+  jde_count_launch();
   nms_scan_kernel<<<(n + wpb - 1) / wpb, 32 * wpb, wpb * (b.kmax / 64) * sizeof(unsigned long long), st>>>(
       b.mask, b.n_sorted, b.kmax, b.keep_idx, b.n_keep, n);
   dim3 ge((b.kmax + 3) / 4, n);
+  jde_count_launch();
   emit_kernel<<<ge, 128, 0, st>>>(heads[3], heads[4], heads[5], g, b.sorted, b.boxes, b.conf, b.cls, b.keep_idx,
                                   b.n_keep, b.kmax, rows, count, anchor_index, cap);
 }

@@ -134,22 +134,26 @@ __global__ void stem_im2col_kernel(TView lb, __nv_bfloat16* rows) {
 void letterbox_tables_launch(LbAxis* xs, LbAxis* ys, int src_w, int src_h, int dst_w, int dst_h, double r, int nw,
                              int nh, int px, int py, cudaStream_t st) {
   const int n = dst_w > dst_h ? dst_w : dst_h;
+  jde_count_launch();
   tables_kernel<<<(n + 255) / 256, 256, 0, st>>>(xs, ys, src_w, src_h, dst_w, dst_h, r, nw, nh, px, py);
 }
 
 void letterbox_f32_launch(const uint8_t* frames, int n, int src_w, int src_h, const LbAxis* xs, const LbAxis* ys,
                           TView out, cudaStream_t st) {
   const long long total = (long long)n * out.h * out.w;
+  jde_count_launch();
   letterbox_f32_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(frames, n, src_w, src_h, xs, ys, out);
 }
 
 void letterbox_bf16x4_launch(const uint8_t* frames, int n, int src_w, int src_h, const LbAxis* xs,
                              const LbAxis* ys, TView out, cudaStream_t st) {
   const long long total = (long long)n * out.h * out.w;
+  jde_count_launch();
   letterbox_bf16x4_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(frames, n, src_w, src_h, xs, ys, out);
 }
 
 void stem_im2col_launch(TView lb4, __nv_bfloat16* rows, cudaStream_t st) {
   const long long total = (long long)lb4.n * lb4.h * lb4.w;
+  jde_count_launch();
   stem_im2col_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(lb4, rows);
 }

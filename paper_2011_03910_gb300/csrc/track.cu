@@ -563,7 +563,10 @@ int track_alloc(TrackState& t, const jde_config& cfg) {
   if (cudaFuncSetAttribute(assign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)assign_smem(t)) !=
       cudaSuccess)
     return 1;
-  for (int s = 0; s < t.max_streams; ++s) reset_kernel<<<1, 256>>>(t, s);
+  for (int s = 0; s < t.max_streams; ++s) {
+    jde_count_launch();
+    reset_kernel<<<1, 256>>>(t, s);
+  }
   return cudaDeviceSynchronize() == cudaSuccess ? 0 : 1;
 }
 
@@ -577,6 +580,7 @@ void track_free(TrackState& t) {
 }
 
 int track_reset(TrackState& t, int s, cudaStream_t st) {
+  jde_count_launch();
   reset_kernel<<<1, 256, 0, st>>>(t, s);
   return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
@@ -665,9 +669,12 @@ int track_step(TrackState& t, const jde_config& cfg, int n, const int32_t* strea
     a.o_count = t.o_count;
   }
   dim3 gp((t.max_tracks + 127) / 128, n);
+  jde_count_launch();
   prep_kernel<<<gp, 128, 0, st>>>(a, sl);
   dim3 gc((t.max_tracks + 31) / 32, (t.max_dets + 31) / 32, n);
+  jde_count_launch();
   cost_kernel<<<gc, 256, 0, st>>>(a, sl);
+  jde_count_launch();
   assign_kernel<<<n, 256, assign_smem(t), st>>>(a, sl);
   if (cudaGetLastError() != cudaSuccess) {
     snprintf(msg, msg_len, "tracker launch failed");

@@ -65,6 +65,8 @@ _sig = {
     "jde_stream_reset": (C.c_int, [_P, C.c_int, _P]),
     "jde_get_tensor": (C.c_int, [_P, C.c_int, _P, C.c_size_t, C.POINTER(C.c_int), C.POINTER(C.c_int), _P]),
     "jde_kernel_errors": (C.c_int, [_P, C.POINTER(C.c_int), _P]),
+    "jde_launch_count": (C.c_ulonglong, []),
+    "jde_set_profile_events": (C.c_int, [_P, _P, _P, _P]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(lib, _name)
@@ -188,3 +190,13 @@ def jde_kernel_errors(h, stream=None) -> int:
     w = C.c_int()
     _check(h, lib.jde_kernel_errors(h, C.byref(w), stream_ptr(stream)))
     return w.value
+
+
+def jde_launch_count() -> int:
+    return int(lib.jde_launch_count())
+
+
+def jde_set_profile_events(h, forward_begin=None, conv_begin=None, conv_end=None):
+    """Events are torch.cuda.Event objects (recorded by the library on the call's stream) or None."""
+    ev = [None if e is None else e.cuda_event for e in (forward_begin, conv_begin, conv_end)]
+    _check(h, lib.jde_set_profile_events(h, *ev))

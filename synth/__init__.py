@@ -230,22 +230,18 @@ class PlantedClip:
         self.emb_sigma = emb_noise if emb_noise_per_dim else emb_noise / math.sqrt(512.0)
         self.grids = [(in_h // s, in_w // s) for s in strides]
 
-    def frame(self, t: int):
-        """Head tensors of frame ``t``: ``(dets, embs, truth)``.
+    def frame_entries(self, t: int):
+        """Sparse content of frame ``t``: ``(det_entries, emb_entries, truth)``.
 
-        ``dets[s]`` is ``[H_s, W_s, 24]`` float32, ``embs[s]`` ``[H_s, W_s, 512]``
-        float32, ``truth`` a list of ``(object_id, cx, cy, w, h)`` in frame px of
-        the objects that were planted (visible) in this frame.
+        ``det_entries`` lists ``(head, y, x, anchor, values[6])``, ``emb_entries``
+        lists ``(head, y, x, vector[512])``; every other detection value is 0
+        except the objectness channels (-6) and every other embedding value 0.
+        ``truth`` lists ``(object_id, cx, cy, w, h)`` in frame px of the objects
+        planted in this frame.
         """
         g = _rng(self.seed, t)
-        dets = []
-        for (gh, gw) in self.grids:
-            d = np.zeros((gh, gw, 24), np.float32)
-            d[..., 4::6] = -6.0
-            dets.append(d)
-        embs = [np.zeros((gh, gw, 512), np.float32) for (gh, gw) in self.grids]
         used = set()
-        truth = []
+        det_e, emb_e, truth = [], [], []
         jit = g.normal(0.0, self.jitter, (self.n, 2))
         hide = g.random(self.n) < self.occl
         third = g.random(self.n) < 0.5
@@ -279,14 +275,29 @@ class PlantedClip:
             tx, ty = math.log(fx / (1 - fx)), math.log(fy / (1 - fy))
             for j, (_, b, _, _) in enumerate(slots):
                 aw, ah = self.anchors[s][b]
-                base = 6 * b
-                d = dets[s][gy, gx]
-                d[base + 0], d[base + 1] = tx, ty
-                d[base + 2], d[base + 3] = math.log(lw / aw), math.log(lh / ah)
-                d[base + 4] = 4.0 if j == 0 else 1.0
-                d[base + 5] = 4.0
+                vals = [tx, ty, math.log(lw / aw), math.log(lh / ah), 4.0 if j == 0 else 1.0, 4.0]
+                det_e.append((s, gy, gx, b, vals))
                 used.add((s, b, gy, gx))
             used.add((s, gy, gx))
-            embs[s][gy, gx] = (self.ident[o] + noise[o]).astype(np.float32)
+            emb_e.append((s, gy, gx, (self.ident[o] + noise[o]).astype(np.float32)))
             truth.append((o, cx, cy, w, h))
+        return det_e, emb_e, truth
+
+    def frame(self, t: int):
+        """Dense head tensors of frame ``t``: ``(dets, embs, truth)``.
+
+        ``dets[s]`` is ``[H_s, W_s, 24]`` float32, ``embs[s]`` ``[H_s, W_s, 512]``
+        float32 (the entries of ``frame_entries`` written into the background).
+        """
+        det_e, emb_e, truth = self.frame_entries(t)
+        dets = []
+        for (gh, gw) in self.grids:
+            d = np.zeros((gh, gw, 24), np.float32)
+            d[..., 4::6] = -6.0
+            dets.append(d)
+        embs = [np.zeros((gh, gw, 512), np.float32) for (gh, gw) in self.grids]
+        for s, y, x, b, vals in det_e:
+            dets[s][y, x, 6 * b:6 * b + 6] = vals
+        for s, y, x, vec in emb_e:
+            embs[s][y, x] = vec
         return dets, embs, truth

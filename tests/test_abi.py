@@ -10,7 +10,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "jde.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:jde_status|void|int|const char\s*\*)\s+(jde_\w+)\s*\(", src, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:jde_status|void|int|unsigned long long|const char\s*\*)\s+(jde_\w+)\s*\(", src, flags=re.M)))
 
 
 @pytest.fixture(scope="module")
