@@ -285,6 +285,9 @@ def main():
     torch.cuda.synchronize()
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
     prof = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    for p3 in prof:          # torch creates the CUDA event on its first record; the library re-records it
+        for e in p3:
+            e.record(st)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
