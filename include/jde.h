@@ -192,6 +192,32 @@ unsigned long long jde_launch_count(void);
  * events stay owned by the caller. */
 jde_status jde_set_profile_events(jde_handle* h, void* forward_begin, void* conv_begin, void* conv_end);
 
+/* Post-processing for callers that cannot allocate device memory: code that
+ * runs after a host application has reserved all device memory, a real-time
+ * loop where a cudaMalloc (which can synchronise the device) is not allowed,
+ * or a plugin that receives device pointers but no allocator.  The paper has
+ * no counterpart; this is a deployment variant of jde_postprocess.
+ * Same computation and rows as jde_postprocess with the thresholds passed in
+ * (conf_thresh, nms_iou, max_cand = K_max, a multiple of 64 in [64, 4096]).
+ * It needs no handle and calls no cudaMalloc, cudaFree or allocating library
+ * routine: heads[0..5] (device, layout as in jde_postprocess) and the outputs
+ * (device; out->on_device must be 1) are the caller's, and all scratch comes
+ * from one fixed 32 MiB device array compiled into the library, which every
+ * GPU that loads libjde holds until the process exits.  A call needs about
+ * n * (8 * anchors + max_cand * (36 + max_cand / 8)) bytes of it (anchors =
+ * 4 * (in_w*in_h/1024 + in_w*in_h/256 + in_w*in_h/64)); a larger request
+ * returns JDE_ERR_CAPACITY with the sizes in err_msg (e.g. 16 frames at
+ * 1088x608 fit with max_cand <= 2048).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current: make that first call
+ * before any stream capture.  Every call uses the same array and leaves its
+ * contents behind; two calls that can overlap on the GPU (different streams
+ * or host threads) race, so the caller must serialise them.
+ * err_msg (optional, err_len bytes) receives the reason of a failure. */
+jde_status jde_postprocess_noalloc(const float* const* heads, int n, int in_w, int in_h, int src_w, int src_h,
+                                   float conf_thresh, float nms_iou, int max_cand, jde_dets* out, void* stream,
+                                   char* err_msg, size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -67,6 +67,8 @@ _sig = {
     "jde_kernel_errors": (C.c_int, [_P, C.POINTER(C.c_int), _P]),
     "jde_launch_count": (C.c_ulonglong, []),
     "jde_set_profile_events": (C.c_int, [_P, _P, _P, _P]),
+    "jde_postprocess_noalloc": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float, C.c_float,
+                                          C.c_int, C.POINTER(jde_dets), _P, C.c_char_p, C.c_size_t]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(lib, _name)
@@ -200,3 +202,14 @@ def jde_set_profile_events(h, forward_begin=None, conv_begin=None, conv_end=None
     """Events are torch.cuda.Event objects (recorded by the library on the call's stream) or None."""
     ev = [None if e is None else e.cuda_event for e in (forward_begin, conv_begin, conv_end)]
     _check(h, lib.jde_set_profile_events(h, *ev))
+
+
+def jde_postprocess_noalloc(heads, n, in_w, in_h, src_w, src_h, conf_thresh, nms_iou, max_cand, dets: jde_dets,
+                            stream=None):
+    """Allocation-free post-processing (scratch from the library's fixed device array)."""
+    arr = (_P * 6)(*[ptr(x) for x in heads])
+    msg = C.create_string_buffer(512)
+    st = lib.jde_postprocess_noalloc(arr, n, in_w, in_h, src_w, src_h, conf_thresh, nms_iou, max_cand,
+                                     C.byref(dets), stream_ptr(stream), msg, len(msg))
+    if st != JDE_OK:
+        raise JdeError(st, msg.value.decode(errors="replace"))
