@@ -31,20 +31,43 @@ namespace {
 struct TcArgs {
   int mode, k, cin_blocks, kt_total;
   int M_total, Hp, Wp;
-  int TW, TH, tiles_x, tiles_y, n_tiles;
+  int TW, TH, tiles_x, tiles_y, n_tiles, total_tiles;
+  int tma_out, tma_res;
   ConvSpec c;
 };
+
+// warp 0: TMA producer; warp 1: MMA issuer + TMEM owner; warps 2..9: epilogue in two
+// groups of four, group g draining TMEM accumulator buffer g (tiles alternate).
+constexpr int EPI_WARPS = 8;
+constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;
 
 template <int BN, int BKC, int STAGES>
 struct TcCfg {
   static constexpr int A_BYTES = 128 * BKC * 2;
   static constexpr int B_BYTES = BN * BKC * 2;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
-  static constexpr uint32_t LAYOUT = BKC == 64 ? 2u : 4u;     // SW128 : SW64
+  static constexpr int SWC = BN < 128 ? BN : 128;       // columns staged per epilogue pass
+  static constexpr int PASSES = BN / SWC;
+  static constexpr int SUB = SWC < 64 ? SWC : 64;       // channels per TMA store box (64 or 128-byte rows)
+  static constexpr int NSUB = SWC / SUB;
+  static constexpr int SUB_BYTES = 128 * SUB * 2;
+  static constexpr int C_BYTES = NSUB * SUB_BYTES;      // staging tile of one epilogue group
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 2 * C_BYTES + 1024 /*align*/ + 512 /*barriers*/;
+  static constexpr uint32_t LAYOUT = BKC == 64 ? 2u : 4u;     // SW128 : SW64 (MMA operand tiles)
   static constexpr uint32_t SBO = 8 * BKC * 2;                 // bytes per 8-row group
-  static constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
+  static constexpr uint32_t TMEM_COLS = 2 * BN;                // two accumulator buffers
+  static_assert(SMEM <= 227 * 1024, "shared memory budget");
+  static_assert(TMEM_COLS >= 32 && TMEM_COLS <= 512, "TMEM budget");
 };
+
+// 16-byte unit `unit` of staged row `row` inside a SUB-channel box written by TMA with
+// 128-byte (SUB 64) or 64-byte (SUB 32) swizzle: the unit index is XORed with the
+// address bits 7..9 (resp. 7..8) of the row start.
+template <int SUB>
+__device__ __forceinline__ uint32_t stage_off(int row, int unit) {
+  if (SUB == 64) return (uint32_t)(row * 128 + ((unit ^ (row & 7)) << 4));
+  return (uint32_t)(row * 64 + ((unit ^ ((row >> 1) & 3)) << 4));
+}
 
 __device__ __forceinline__ void store_chunk(const ConvSpec& c, int n, int y, int x, int ch0, int nvalid,
                                             const float (&v)[32]) {
@@ -67,7 +90,9 @@ __device__ __forceinline__ void store_chunk(const ConvSpec& c, int n, int y, int
         for (int j = 0; j < 4; ++j)
           o4[j] = make_uint4(packed[4 * j], packed[4 * j + 1], packed[4 * j + 2], packed[4 * j + 3]);
       } else {
-        for (int j = 0; j < nvalid; ++j) o[j] = __float2bfloat16_rn(v[j]);
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (j < nvalid) o[j] = __float2bfloat16_rn(v[j]);
       }
     } else {
       float* o = static_cast<float*>(c.out.ptr) + off;
@@ -77,173 +102,305 @@ __device__ __forceinline__ void store_chunk(const ConvSpec& c, int n, int y, int
         for (int j = 0; j < 8; ++j)
           if (4 * j < nvalid) o4[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
       } else {
-        for (int j = 0; j < nvalid; ++j) o[j] = v[j];
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (j < nvalid) o[j] = v[j];
       }
     }
   }
 }
 
+struct TileCoord {
+  int n0, m0, img, oy0, ox0;
+};
+
+__device__ __forceinline__ TileCoord tile_coord(const TcArgs& a, int tile, int bn) {
+  TileCoord t;
+  const int n_tile = tile % a.n_tiles;   // consecutive tiles share the activation tile
+  const int m_tile = tile / a.n_tiles;
+  t.n0 = n_tile * bn;
+  t.m0 = 0;
+  t.img = 0;
+  t.oy0 = 0;
+  t.ox0 = 0;
+  if (a.mode == 0) {
+    t.m0 = m_tile * 128;
+  } else {
+    const int per_img = a.tiles_x * a.tiles_y;
+    t.img = m_tile / per_img;
+    const int r = m_tile % per_img;
+    t.oy0 = (r / a.tiles_x) * a.TH;
+    t.ox0 = (r % a.tiles_x) * a.TW;
+  }
+  return t;
+}
+
+__device__ __forceinline__ bool aborted(const int* flag) { return *((volatile const int*)flag) != 0; }
+
+// Persistent CTA (one per SM): tiles blockIdx.x, blockIdx.x + gridDim.x, ...
 template <int BN, int BKC, int STAGES>
-__global__ void __launch_bounds__(128, 1) conv_tc_kernel(const __grid_constant__ TcPlan plan, const TcArgs a) {
+__global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_constant__ TcPlan plan, const TcArgs a) {
   using Cfg = TcCfg<BN, BKC, STAGES>;
   extern __shared__ uint8_t smem_raw[];
   __shared__ int s_abort;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
   uint8_t* sB = smem + STAGES * Cfg::A_BYTES;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * Cfg::B_BYTES);
+  uint8_t* sC = sB + STAGES * Cfg::B_BYTES;              // 2 staging tiles
+  uint64_t* full = reinterpret_cast<uint64_t*>(sC + 2 * Cfg::C_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* done = empty + STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* acc_full = empty + STAGES;   // [2] MMA -> epilogue group
+  uint64_t* acc_empty = acc_full + 2;    // [2] epilogue group -> MMA
+  uint64_t* res_full = acc_empty + 2;    // [2] residual tile landed in staging tile g
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(res_full + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const ConvSpec& c = a.c;
-
-  // tile coordinates: consecutive CTAs share the activation tile (n fastest)
-  const int n_tile = blockIdx.x % a.n_tiles;
-  const int m_tile = blockIdx.x / a.n_tiles;
-  const int n0 = n_tile * BN;
-  int m0 = 0, img = 0, oy0 = 0, ox0 = 0;
-  if (a.mode == 0) {
-    m0 = m_tile * 128;
-  } else {
-    const int per_img = a.tiles_x * a.tiles_y;
-    img = m_tile / per_img;
-    const int r = m_tile % per_img;
-    oy0 = (r / a.tiles_x) * a.TH;
-    ox0 = (r % a.tiles_x) * a.TW;
-  }
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], EPI_WARPS / 2);
+      mbar_init(&res_full[b], 1);
+    }
     fence_barrier_init();
     s_abort = 0;
   }
-  if (warp == 0) tmem_alloc(tmem_slot, Cfg::TMEM_COLS);
+  if (warp == 1) tmem_alloc(tmem_slot, Cfg::TMEM_COLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer
-    for (int i = 0; i < 4; ++i)
-      if (a.mode == 1 || i == 0) tma_prefetch(&plan.a[i]);
-    tma_prefetch(&plan.b);
-    for (int kt = 0; kt < a.kt_total; ++kt) {
-      const int s = kt % STAGES;
-      const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
-      if (kt >= STAGES && !mbar_wait(&empty[s], ph ^ 1u)) {
-        flag_error(c.err, KERR_TIMEOUT);
-        atomicExch(&s_abort, 1);
-        break;
-      }
-      const int tap = kt / a.cin_blocks, cb = kt % a.cin_blocks;
-      const int ky = tap / a.k, kx = tap % a.k;
-      mbar_expect_tx(&full[s], Cfg::STAGE_BYTES);
-      uint8_t* dA = sA + s * Cfg::A_BYTES;
-      if (a.mode == 0) {
-        const int shift = a.k == 3 ? (ky - 1) * a.Wp + (kx - 1) : 0;
-        tma_load_2d(dA, &plan.a[0], &full[s], cb * BKC, m0 + shift);
-      } else {
-        tma_load_4d(dA, &plan.a[(ky & 1) * 2 + (kx & 1)], &full[s], cb * BKC, ox0 + (kx >> 1), oy0 + (ky >> 1),
-                    img);
-      }
-      tma_load_2d(sB + s * Cfg::B_BYTES, &plan.b, &full[s], kt * BKC, n0);
-    }
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer
-    constexpr uint32_t idesc = idesc_bf16(128, BN);
-    for (int kt = 0; kt < a.kt_total; ++kt) {
-      const int s = kt % STAGES;
-      const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
-      if (!mbar_wait(&full[s], ph)) {
-        flag_error(c.err, KERR_TIMEOUT);
-        atomicExch(&s_abort, 1);
-        break;
-      }
-      tc_fence_after();
-      const uint32_t a_base = smem_u32(sA + s * Cfg::A_BYTES);
-      const uint32_t b_base = smem_u32(sB + s * Cfg::B_BYTES);
-#pragma unroll
-      for (int kk = 0; kk < BKC / 16; ++kk) {
-        const uint64_t ad = smem_desc(a_base + kk * 32, Cfg::SBO, Cfg::LAYOUT);
-        const uint64_t bd = smem_desc(b_base + kk * 32, Cfg::SBO, Cfg::LAYOUT);
-        umma_bf16(tmem, ad, bd, idesc, (kt | kk) != 0 ? 1u : 0u);
-      }
-      umma_commit(&empty[s]);
-    }
-    umma_commit(done);
-  }
-  __syncwarp();
-
-  // ---------------- epilogue: TMEM -> registers -> global
-  const bool ok = mbar_wait(done, 0);
-  if (!ok) flag_error(c.err, KERR_TIMEOUT);
-  tc_fence_after();
-  const int row = warp * 32 + lane;
-  int n = 0, y = 0, x = 0;
-  bool valid;
-  if (a.mode == 0) {
-    const int m = m0 + row;
-    const int plane = a.Hp * a.Wp;
-    n = m / plane;
-    const int r = m % plane;
-    y = r / a.Wp - 1;
-    x = r % a.Wp - 1;
-    valid = m < a.M_total && y >= 0 && y < c.Ho && x >= 0 && x < c.Wo;
-  } else {
-    n = img;
-    y = oy0 + row / a.TW;
-    x = ox0 + row % a.TW;
-    valid = y < c.Ho && x < c.Wo;
-  }
-  if (!ok || *((volatile int*)&s_abort)) valid = false;
-
-#pragma unroll 1
-  for (int c0 = 0; c0 < BN; c0 += 32) {
-    uint32_t r[32];
-    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-    tmem_ld_wait();
-    const int ch0 = n0 + c0;
-    if (valid && ch0 < c.cout) {
-      const int nvalid = min(32, c.cout - ch0);
-      float v[32];
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        float t = __uint_as_float(r[j]) + c.bias[ch0 + j];
-        v[j] = c.act ? leaky01(t) : t;
-      }
-      if (c.res.ptr) {
-        const __nv_bfloat16* rp = static_cast<const __nv_bfloat16*>(c.res.ptr) + tview_off(c.res, n, y, x) + ch0;
-        if (nvalid == 32) {
-          const uint4* r4 = reinterpret_cast<const uint4*>(rp);
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            uint4 q = r4[j];
-            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162*>(&w[e]);
-              float2 f = __bfloat1622float2(h2);
-              v[8 * j + 2 * e] += f.x;
-              v[8 * j + 2 * e + 1] += f.y;
-            }
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer
+      for (int i = 0; i < 4; ++i)
+        if (a.mode == 1 || i == 0) tma_prefetch(&plan.a[i]);
+      tma_prefetch(&plan.b);
+      uint32_t it = 0;
+      for (int tile = blockIdx.x; tile < a.total_tiles && !aborted(&s_abort); tile += gridDim.x) {
+        const TileCoord tc = tile_coord(a, tile, BN);
+        for (int kt = 0; kt < a.kt_total; ++kt, ++it) {
+          const uint32_t s = it % STAGES;
+          const uint32_t ph = (it / STAGES) & 1u;
+          if (it >= (uint32_t)STAGES && !mbar_wait(&empty[s], ph ^ 1u)) {
+            flag_error(c.err, KERR_TIMEOUT);
+            atomicExch(&s_abort, 1);
+            break;
           }
-        } else {
-          for (int j = 0; j < nvalid; ++j) v[j] += __bfloat162float(rp[j]);
+          const int tap = kt / a.cin_blocks, cb = kt % a.cin_blocks;
+          const int ky = tap / a.k, kx = tap % a.k;
+          mbar_expect_tx(&full[s], Cfg::STAGE_BYTES);
+          uint8_t* dA = sA + s * Cfg::A_BYTES;
+          if (a.mode == 0) {
+            const int shift = a.k == 3 ? (ky - 1) * a.Wp + (kx - 1) : 0;
+            tma_load_2d(dA, &plan.a[0], &full[s], cb * BKC, tc.m0 + shift);
+          } else {
+            tma_load_4d(dA, &plan.a[(ky & 1) * 2 + (kx & 1)], &full[s], cb * BKC, tc.ox0 + (kx >> 1),
+                        tc.oy0 + (ky >> 1), tc.img);
+          }
+          tma_load_2d(sB + s * Cfg::B_BYTES, &plan.b, &full[s], kt * BKC, tc.n0);
         }
       }
-      store_chunk(c, n, y, x, ch0, nvalid, v);
     }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      constexpr uint32_t idesc = idesc_bf16(128, BN);
+      uint32_t it = 0, local = 0;
+      for (int tile = blockIdx.x; tile < a.total_tiles; tile += gridDim.x, ++local) {
+        const uint32_t buf = local & 1u, use = local >> 1;
+        if (local >= 2 && !mbar_wait(&acc_empty[buf], (use - 1) & 1u)) {
+          flag_error(c.err, KERR_TIMEOUT);
+          atomicExch(&s_abort, 1);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + buf * BN;
+        bool ok = true;
+        for (int kt = 0; kt < a.kt_total; ++kt, ++it) {
+          const uint32_t s = it % STAGES;
+          const uint32_t ph = (it / STAGES) & 1u;
+          if (!mbar_wait(&full[s], ph)) {
+            flag_error(c.err, KERR_TIMEOUT);
+            atomicExch(&s_abort, 1);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_base = smem_u32(sA + s * Cfg::A_BYTES);
+          const uint32_t b_base = smem_u32(sB + s * Cfg::B_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < BKC / 16; ++kk) {
+            const uint64_t ad = smem_desc(a_base + kk * 32, Cfg::SBO, Cfg::LAYOUT);
+            const uint64_t bd = smem_desc(b_base + kk * 32, Cfg::SBO, Cfg::LAYOUT);
+            umma_bf16(d, ad, bd, idesc, (kt | kk) != 0 ? 1u : 0u);
+          }
+          umma_commit(&empty[s]);
+        }
+        umma_commit(&acc_full[buf]);
+        if (!ok) break;
+      }
+    }
+  } else {
+    // ---------------- epilogue: group g = (warp - 2) / 4 takes the tiles whose local index has parity g
+    const int ew = warp - 2;
+    const int g = ew >> 2;
+    const int quarter = warp & 3;           // TMEM lanes a warp may read: 32 * (warp % 4) ...
+    const int row = quarter * 32 + lane;
+    const bool elected = (ew & 3) == 0 && lane == 0;
+    const int bar_id = 1 + g;
+    uint8_t* stg = sC + g * Cfg::C_BYTES;
+    uint32_t res_uses = 0, local = 0;
+    for (int tile = blockIdx.x; tile < a.total_tiles; tile += gridDim.x, ++local) {
+      if ((local & 1u) != (uint32_t)g) continue;
+      const uint32_t buf = (uint32_t)g, use = local >> 1;
+      bool ok = mbar_wait(&acc_full[buf], use & 1u);
+      if (!ok) {
+        flag_error(c.err, KERR_TIMEOUT);
+        atomicExch(&s_abort, 1);
+      }
+      ok = bar_and(ok, bar_id, 128);        // the group's four warps take the same path
+      tc_fence_after();
+      const TileCoord tc = tile_coord(a, tile, BN);
+      int n = 0, y = 0, x = 0;
+      bool valid;
+      if (a.mode == 0) {
+        const int m = tc.m0 + row;
+        const int plane = a.Hp * a.Wp;
+        n = m / plane;
+        const int r = m % plane;
+        y = r / a.Wp - 1;
+        x = r % a.Wp - 1;
+        valid = m < a.M_total && y >= 0 && y < c.Ho && x >= 0 && x < c.Wo;
+      } else {
+        n = tc.img;
+        y = tc.oy0 + row / a.TW;
+        x = tc.ox0 + row % a.TW;
+        valid = y < c.Ho && x < c.Wo;
+      }
+      if (a.tma_out) {
+        // staged: TMEM -> (bias, leaky, + residual) -> bf16 staging tile -> TMA store.
+        // Rows on the halo are written as zeros, which keeps the halo zero.
+        for (int p = 0; p < Cfg::PASSES; ++p) {
+          const bool use_res = a.tma_res && ok;
+          if (elected) {
+            bulk_wait_read0();              // the previous store has finished reading the staging tile
+            if (use_res) {
+              mbar_expect_tx(&res_full[g], Cfg::C_BYTES);
+              for (int j = 0; j < Cfg::NSUB; ++j)
+                tma_load_2d(stg + j * Cfg::SUB_BYTES, &plan.r, &res_full[g], tc.n0 + p * Cfg::SWC + j * Cfg::SUB,
+                            tc.m0);
+            }
+          }
+          named_bar(bar_id, 128);
+          if (use_res) {
+            if (!mbar_wait(&res_full[g], res_uses & 1u)) {
+              flag_error(c.err, KERR_TIMEOUT);
+              atomicExch(&s_abort, 1);
+            }
+            ++res_uses;
+          }
+#pragma unroll 1
+          for (int c0 = 0; c0 < Cfg::SWC; c0 += 32) {
+            uint32_t r[32];
+            tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + buf * BN + (uint32_t)(p * Cfg::SWC + c0), r);
+            tmem_ld_wait();
+            const float4* b4 = reinterpret_cast<const float4*>(c.bias + tc.n0 + p * Cfg::SWC + c0);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int col = c0 + 8 * u;                       // column inside this pass
+              uint8_t* q = stg + (col / Cfg::SUB) * Cfg::SUB_BYTES + stage_off<Cfg::SUB>(row, (col % Cfg::SUB) >> 3);
+              const float4 b0 = b4[2 * u], b1 = b4[2 * u + 1];
+              float t[8] = {__uint_as_float(r[8 * u]) + b0.x,     __uint_as_float(r[8 * u + 1]) + b0.y,
+                            __uint_as_float(r[8 * u + 2]) + b0.z, __uint_as_float(r[8 * u + 3]) + b0.w,
+                            __uint_as_float(r[8 * u + 4]) + b1.x, __uint_as_float(r[8 * u + 5]) + b1.y,
+                            __uint_as_float(r[8 * u + 6]) + b1.z, __uint_as_float(r[8 * u + 7]) + b1.w};
+              if (c.act) {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) t[e] = leaky01(t[e]);
+              }
+              if (use_res) {
+                const uint4 rq = *reinterpret_cast<const uint4*>(q);
+                const uint32_t rv[4] = {rq.x, rq.y, rq.z, rq.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                  const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&rv[e]));
+                  t[2 * e] += f.x;
+                  t[2 * e + 1] += f.y;
+                }
+              }
+              uint32_t pk[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                __nv_bfloat162 h2 = valid ? __floats2bfloat162_rn(t[2 * e], t[2 * e + 1]) : __floats2bfloat162_rn(0.f, 0.f);
+                pk[e] = *reinterpret_cast<uint32_t*>(&h2);
+              }
+              *reinterpret_cast<uint4*>(q) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            }
+          }
+          if (p == Cfg::PASSES - 1) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[buf]);   // accumulator buffer free for the MMA
+          }
+          fence_proxy_async();               // staging writes visible to the TMA store
+          named_bar(bar_id, 128);
+          if (elected && ok && !aborted(&s_abort)) {
+            for (int j = 0; j < Cfg::NSUB; ++j) {
+              const int ch = tc.n0 + p * Cfg::SWC + j * Cfg::SUB;
+              if (a.mode == 0)
+                tma_store_2d(&plan.o, stg + j * Cfg::SUB_BYTES, ch, tc.m0);
+              else
+                tma_store_4d(&plan.o, stg + j * Cfg::SUB_BYTES, ch, tc.ox0 + 1, tc.oy0 + 1, tc.img);
+            }
+            bulk_commit();
+          }
+        }
+      } else {
+        // direct: one pixel row per thread (f32 heads, upsampled laterals)
+        if (!ok || aborted(&s_abort)) valid = false;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+          uint32_t r[32];
+          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + buf * BN + (uint32_t)c0, r);
+          tmem_ld_wait();
+          const int ch0 = tc.n0 + c0;
+          if (valid && ch0 < c.cout) {
+            const int nvalid = min(32, c.cout - ch0);
+            float v[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const float t = __uint_as_float(r[j]) + c.bias[ch0 + j];
+              v[j] = c.act ? leaky01(t) : t;
+            }
+            if (c.res.ptr) {
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                if (j < nvalid)
+                  v[j] += __bfloat162float(
+                      static_cast<const __nv_bfloat16*>(c.res.ptr)[tview_off(c.res, n, y, x) + ch0 + j]);
+            }
+            store_chunk(c, n, y, x, ch0, nvalid, v);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[buf]);
+      }
+      if (!ok) break;
+    }
+    if (elected) bulk_wait0();               // stores done before the CTA (and its smem) goes away
   }
+  __syncwarp();
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, Cfg::TMEM_COLS);
+  if (warp == 1) tmem_dealloc(tmem, Cfg::TMEM_COLS);
 }
 
 // ----------------------------------------------------------------------------- host side
@@ -275,6 +432,16 @@ bool encode(CUtensorMap* m, int rank, void* base, const cuuint64_t* dims, const 
   return r == CUDA_SUCCESS;
 }
 
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+  }
+  return n;
+}
+
 template <int BN, int BKC, int STAGES>
 cudaError_t launch_cfg(const TcPlan& p, const TcArgs& a, cudaStream_t st) {
   using Cfg = TcCfg<BN, BKC, STAGES>;
@@ -285,8 +452,10 @@ cudaError_t launch_cfg(const TcPlan& p, const TcArgs& a, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
+  const int tiles = p.m_tiles * p.n_tiles;
+  const int grid = tiles < sm_count() ? tiles : sm_count();
   jde_count_launch();
-  conv_tc_kernel<BN, BKC, STAGES><<<p.m_tiles * p.n_tiles, 128, Cfg::SMEM, st>>>(p, a);
+  conv_tc_kernel<BN, BKC, STAGES><<<grid, TC_THREADS, Cfg::SMEM, st>>>(p, a);
   return cudaGetLastError();
 }
 
@@ -295,7 +464,8 @@ cudaError_t launch_cfg(const TcPlan& p, const TcArgs& a, cudaStream_t st) {
 int conv_tc_pick_bn(int cout) {
   if (cout <= 32) return 32;
   if (cout <= 64) return 64;
-  return 128;
+  if (cout <= 128) return 128;
+  return 256;
 }
 
 bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const __nv_bfloat16* w, int cout_pad, int bn, char* msg,
@@ -361,6 +531,32 @@ bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const __nv_bfloat16* w, int c
     cuuint32_t box[2] = {(cuuint32_t)bkc, (cuuint32_t)bn};
     ok &= encode(&plan.b, 2, const_cast<__nv_bfloat16*>(w), dims, strides, box, bkc);
   }
+  // TMA-stored epilogue: bf16 padded outputs written in place (no upsample), channel
+  // count a multiple of the store box (64, or 32 for 32-wide tiles)
+  const int sub = bn < 64 ? bn : 64;
+  plan.tma_out = c.out.dtype == 1 && !c.upsample && c.out.pad == 1 && c.cout % sub == 0;
+  plan.tma_res = plan.tma_out && c.res.ptr != nullptr && c.stride == 1 && c.res.dtype == 1 && c.res.pad == 1;
+  if (plan.tma_out) {
+    const int Ho = c.Ho, Wo = c.Wo;
+    if (plan.mode == 0) {
+      cuuint64_t dims[2] = {(cuuint64_t)c.cout, (cuuint64_t)plan.M_total};
+      cuuint64_t strides[1] = {(cuuint64_t)c.out.pixstride * 2};
+      cuuint32_t box[2] = {(cuuint32_t)sub, 128};
+      ok &= encode(&plan.o, 2, c.out.ptr, dims, strides, box, sub);
+    } else {
+      cuuint64_t dims[4] = {(cuuint64_t)c.cout, (cuuint64_t)(Wo + 2), (cuuint64_t)(Ho + 2), (cuuint64_t)c.out.n};
+      cuuint64_t strides[3] = {(cuuint64_t)c.out.pixstride * 2, (cuuint64_t)(Wo + 2) * c.out.pixstride * 2,
+                               (cuuint64_t)(Ho + 2) * (Wo + 2) * c.out.pixstride * 2};
+      cuuint32_t box[4] = {(cuuint32_t)sub, (cuuint32_t)plan.TW, (cuuint32_t)plan.TH, 1};
+      ok &= encode(&plan.o, 4, c.out.ptr, dims, strides, box, sub);
+    }
+  }
+  if (plan.tma_res) {
+    cuuint64_t dims[2] = {(cuuint64_t)c.cout, (cuuint64_t)plan.M_total};
+    cuuint64_t strides[1] = {(cuuint64_t)c.res.pixstride * 2};
+    cuuint32_t box[2] = {(cuuint32_t)sub, 128};
+    ok &= encode(&plan.r, 2, c.res.ptr, dims, strides, box, sub);
+  }
   if (!ok) {
     snprintf(msg, msg_len, "cuTensorMapEncodeTiled failed (cin=%d k=%d s=%d)", c.cin, c.k, c.stride);
     return false;
@@ -382,20 +578,23 @@ cudaError_t conv_tc_launch(const TcPlan& p, cudaStream_t st) {
   a.tiles_x = p.tiles_x;
   a.tiles_y = p.tiles_y;
   a.n_tiles = p.n_tiles;
+  a.total_tiles = p.m_tiles * p.n_tiles;
+  a.tma_out = p.tma_out;
+  a.tma_res = p.tma_res;
   a.c = p.spec;
   if (p.bkc == 64) {
     switch (p.bn) {
-      case 32: return launch_cfg<32, 64, 4>(p, a, st);
-      case 64: return launch_cfg<64, 64, 4>(p, a, st);
-      case 128: return launch_cfg<128, 64, 3>(p, a, st);
+      case 32: return launch_cfg<32, 64, 8>(p, a, st);
+      case 64: return launch_cfg<64, 64, 7>(p, a, st);
+      case 128: return launch_cfg<128, 64, 4>(p, a, st);
       case 256: return launch_cfg<256, 64, 3>(p, a, st);
     }
   } else {
     switch (p.bn) {
-      case 32: return launch_cfg<32, 32, 4>(p, a, st);
-      case 64: return launch_cfg<64, 32, 4>(p, a, st);
-      case 128: return launch_cfg<128, 32, 4>(p, a, st);
-      case 256: return launch_cfg<256, 32, 4>(p, a, st);
+      case 32: return launch_cfg<32, 32, 12>(p, a, st);
+      case 64: return launch_cfg<64, 32, 12>(p, a, st);
+      case 128: return launch_cfg<128, 32, 8>(p, a, st);
+      case 256: return launch_cfg<256, 32, 6>(p, a, st);
     }
   }
   return cudaErrorInvalidValue;

@@ -26,6 +26,9 @@ void conv_simt_launch(const ConvSpec& c, const float* w_kn, int cout_pad64, cuda
 struct TcPlan {
   alignas(64) CUtensorMap a[4];  // activations: flat 2-D map, or 4 stride-2 phase maps
   alignas(64) CUtensorMap b;     // weights
+  alignas(64) CUtensorMap o;     // output (TMA-stored epilogue), valid when tma_out
+  alignas(64) CUtensorMap r;     // residual (TMA-loaded into the staging tile), valid when tma_res
+  int tma_out, tma_res;
   int mode;                      // 0 flat (stride 1 over the padded pixel array), 1 patch (stride 2)
   int bn, bkc;
   int kt_total, cin_blocks;
