@@ -157,6 +157,13 @@ jde_status jde_forward(jde_handle* h, const uint8_t* frames, int n, int src_w, i
 jde_status jde_postprocess(jde_handle* h, const float* const* heads, int n, int in_w, int in_h,
                            int src_w, int src_h, jde_dets* out, void* stream);
 
+/* Head tensors are double-buffered: the k-th jde_forward on a handle writes
+ * set k mod 2 and jde_postprocess(heads = NULL) reads the set of the last
+ * forward.  So the post-processing of batch k, enqueued on a second stream
+ * after an event recorded behind forward k, may run while forward k+1 runs;
+ * forward k+2 overwrites the set of batch k and must be ordered after that
+ * post-processing by the caller (e.g. cudaStreamWaitEvent). */
+
 /* jde_forward followed by jde_postprocess on the handle's heads. */
 jde_status jde_detect_batch(jde_handle* h, const uint8_t* frames, int n, int src_w, int src_h,
                             int in_w, int in_h, int on_device, jde_dets* out, void* stream);

@@ -46,7 +46,7 @@ struct TcCfg {
   static constexpr int A_BYTES = 128 * BKC * 2;
   static constexpr int B_BYTES = BN * BKC * 2;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr int SWC = BN < 128 ? BN : 128;       // columns staged per epilogue pass
+  static constexpr int SWC = BN < 64 ? BN : 64;         // columns staged per epilogue pass
   static constexpr int PASSES = BN / SWC;
   static constexpr int SUB = SWC < 64 ? SWC : 64;       // channels per TMA store box (64 or 128-byte rows)
   static constexpr int NSUB = SWC / SUB;
@@ -584,17 +584,17 @@ cudaError_t conv_tc_launch(const TcPlan& p, cudaStream_t st) {
   a.c = p.spec;
   if (p.bkc == 64) {
     switch (p.bn) {
-      case 32: return launch_cfg<32, 64, 8>(p, a, st);
-      case 64: return launch_cfg<64, 64, 7>(p, a, st);
-      case 128: return launch_cfg<128, 64, 4>(p, a, st);
-      case 256: return launch_cfg<256, 64, 3>(p, a, st);
+      case 32: return launch_cfg<32, 64, 10>(p, a, st);
+      case 64: return launch_cfg<64, 64, 8>(p, a, st);
+      case 128: return launch_cfg<128, 64, 6>(p, a, st);
+      case 256: return launch_cfg<256, 64, 4>(p, a, st);
     }
   } else {
     switch (p.bn) {
-      case 32: return launch_cfg<32, 32, 12>(p, a, st);
-      case 64: return launch_cfg<64, 32, 12>(p, a, st);
-      case 128: return launch_cfg<128, 32, 8>(p, a, st);
-      case 256: return launch_cfg<256, 32, 6>(p, a, st);
+      case 32: return launch_cfg<32, 32, 16>(p, a, st);
+      case 64: return launch_cfg<64, 32, 16>(p, a, st);
+      case 128: return launch_cfg<128, 32, 12>(p, a, st);
+      case 256: return launch_cfg<256, 32, 8>(p, a, st);
     }
   }
   return cudaErrorInvalidValue;

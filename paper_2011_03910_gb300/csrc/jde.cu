@@ -110,6 +110,7 @@ struct ResBuffers {
   std::vector<TensorDesc> td;
   std::vector<void*> mem;          // owned allocations (per tensor id, null for aliases)
   std::vector<size_t> bytes;
+  std::vector<size_t> set_bytes;   // head tensors hold two sets (double buffer); bytes of one set
 };
 
 struct Plan {
@@ -145,6 +146,8 @@ struct jde_handle {
   size_t rows_stage_cap = 0;
   TrackState trk{};
   cudaEvent_t prof[3] = {nullptr, nullptr, nullptr};
+  int head_set = 0;   // head-tensor set the next forward writes
+  int cur_set = 0;    // set written by the last forward
 };
 
 namespace {
@@ -287,12 +290,15 @@ jde_status get_res(jde_handle* h, int in_w, int in_h, ResBuffers** out) {
   tensor_desc_table(h, in_w, in_h, rb.td);
   rb.mem.assign(T_COUNT, nullptr);
   rb.bytes.assign(T_COUNT, 0);
+  rb.set_bytes.assign(T_COUNT, 0);
   const int n = h->cfg.max_batch;
   const bool bf16 = h->cfg.precision == JDE_BF16;
   for (int t = 0; t < T_COUNT; ++t) {
     if (rb.td[t].alias >= 0) continue;
     if (t == T_IM2COL && !bf16) continue;
-    const size_t b = tensor_bytes(rb.td[t], n);
+    const bool head = t < JDE_NUM_LAYERS && h->io[t].head >= 0;
+    rb.set_bytes[t] = tensor_bytes(rb.td[t], n);
+    const size_t b = rb.set_bytes[t] * (head ? 2 : 1);
     if (!dmalloc(&rb.mem[t], b)) {
       for (void* p : rb.mem)
         if (p) cudaFree(p);
@@ -679,6 +685,14 @@ jde_status jde_forward(jde_handle* h, const uint8_t* frames, int n, int src_w, i
     letterbox_f32_launch(frames, n, src_w, src_h, h->lb_x, h->lb_y, lb, st);
   }
   const auto& L = layers();
+  // head tensors are double-buffered: this forward writes set head_set
+  const int set = h->head_set;
+  for (size_t l = 0; l < L.size(); ++l) {
+    if (h->io[l].head < 0) continue;
+    void* p = static_cast<char*>(rb->mem[l]) + (size_t)set * rb->set_bytes[l];
+    plan->specs[l].out.ptr = p;
+    if (bf16) plan->tc[l].spec.out.ptr = p;
+  }
   if (h->prof[1]) cudaEventRecord(h->prof[1], st);
   for (size_t l = 0; l < L.size(); ++l) {
     if (bf16) {
@@ -695,6 +709,8 @@ jde_status jde_forward(jde_handle* h, const uint8_t* frames, int n, int src_w, i
   h->cur_n = n;
   h->cur_src_w = src_w;
   h->cur_src_h = src_h;
+  h->cur_set = set;
+  h->head_set = set ^ 1;
   return JDE_OK;
 }
 
@@ -717,7 +733,9 @@ jde_status jde_postprocess(jde_handle* h, const float* const* heads, int n, int 
       return fail(h, JDE_ERR_INVALID_ARG, "jde_postprocess: no forward result at %dx%d for %d frames", in_w, in_h, n);
     const auto& L = layers();
     for (size_t l = 0; l < L.size(); ++l)
-      if (h->io[l].head >= 0) hp[h->io[l].head] = static_cast<const float*>(h->cur->mem[l]);
+      if (h->io[l].head >= 0)
+        hp[h->io[l].head] = reinterpret_cast<const float*>(static_cast<const char*>(h->cur->mem[l]) +
+                                                            (size_t)h->cur_set * h->cur->set_bytes[l]);
   }
   jde_status s = ensure_post(h, n);
   if (s != JDE_OK) return s;
@@ -810,6 +828,8 @@ jde_status jde_get_tensor(jde_handle* h, int id, void* dst, size_t dst_bytes, in
   else
     return fail(h, JDE_ERR_NOT_FOUND, "unknown tensor id %d", id);
   TView v = view_of(*h->cur, tid, h->cur_n);
+  if (tid < JDE_NUM_LAYERS && h->io[tid].head >= 0)
+    v.ptr = static_cast<char*>(v.ptr) + (size_t)h->cur_set * h->cur->set_bytes[tid];
   if (tid == T_IM2COL) {   // raw rows over the padded domain
     v.ptr = h->cur->mem[T_IM2COL];
     v.h = h->cur->in_h + 2;
