@@ -179,8 +179,7 @@ jde_status jde_stream_reset(jde_handle* h, int stream_id, void* stream);
 
 /* Copy an internal tensor to `dst` (device pointer, dst_bytes capacity) for
  * inspection: id 0..77 = output of conv layer id (after its fused epilogue:
- * bias, leaky-ReLU, residual add), 100 = letterboxed input, 101 = stem im2col
- * rows (BF16 only).  dims receives {n, h, w, c} of the unpadded tensor, *dtype
+ * bias, leaky-ReLU, residual add), 100 = letterboxed input.  dims receives {n, h, w, c} of the unpadded tensor, *dtype
  * 0 = f32, 1 = bf16; the copy is the unpadded tensor in NHWC order.  dst NULL
  * only reports dims and dtype. */
 jde_status jde_get_tensor(jde_handle* h, int id, void* dst, size_t dst_bytes, int* dims, int* dtype,

@@ -39,7 +39,7 @@ struct TcArgs {
 // warp 0: TMA producer; warp 1: MMA issuer + TMEM owner; warps 2..9: epilogue in two
 // groups of four, group g draining TMEM accumulator buffer g (tiles alternate).
 constexpr int EPI_WARPS = 8;
-constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;
+__host__ __device__ constexpr int tc_threads(int gw) { return 32 * (gw + 1 + EPI_WARPS); }
 
 template <int BN, int BKC, int STAGES>
 struct TcCfg {
@@ -123,7 +123,7 @@ __device__ __forceinline__ TileCoord tile_coord(const TcArgs& a, int tile, int b
   t.img = 0;
   t.oy0 = 0;
   t.ox0 = 0;
-  if (a.mode == 0) {
+  if (a.mode != 1) {
     t.m0 = m_tile * 128;
   } else {
     const int per_img = a.tiles_x * a.tiles_y;
@@ -138,8 +138,10 @@ __device__ __forceinline__ TileCoord tile_coord(const TcArgs& a, int tile, int b
 __device__ __forceinline__ bool aborted(const int* flag) { return *((volatile const int*)flag) != 0; }
 
 // Persistent CTA (one per SM): tiles blockIdx.x, blockIdx.x + gridDim.x, ...
-template <int BN, int BKC, int STAGES>
-__global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_constant__ TcPlan plan, const TcArgs a) {
+// Warps 0..GW-1 produce (GW = 1: lane 0 of warp 0 issues TMA; the stem uses GW gather
+// warps), warp GW issues the MMAs and owns TMEM, the last 8 warps run the epilogue.
+template <int BN, int BKC, int STAGES, int GW>
+__global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid_constant__ TcPlan plan, const TcArgs a) {
   using Cfg = TcCfg<BN, BKC, STAGES>;
   extern __shared__ uint8_t smem_raw[];
   __shared__ int s_abort;
@@ -159,7 +161,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], 1);
+      mbar_init(&full[s], a.mode == 2 ? 2 : 1);   // stem: TMA (B) arrival + the gather warp's arrival
       mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -170,13 +172,78 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
     fence_barrier_init();
     s_abort = 0;
   }
-  if (warp == 1) tmem_alloc(tmem_slot, Cfg::TMEM_COLS);
+  if (warp == GW) tmem_alloc(tmem_slot, Cfg::TMEM_COLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 0) {
+  if (warp < GW && a.mode == 2) {
+    // ---------------- stem producer: gather warp w fills the stage of every GW-th tile with the
+    // 3x3x3 im2col rows (27 bf16 values padded to 32, order (ky, kx, c)) read from the haloed
+    // RGB0 letterbox image, in the 64-byte swizzle the MMA expects; its lane 0 streams the weights.
+    if (lane == 0 && warp == 0) tma_prefetch(&plan.b);
+    const __nv_bfloat16* lb = static_cast<const __nv_bfloat16*>(c.in.ptr);
+    const int plane = a.Hp * a.Wp;
+    uint32_t lt = 0;   // local tile index of this CTA
+    for (int tile = blockIdx.x; tile < a.total_tiles && !aborted(&s_abort); tile += gridDim.x, ++lt) {
+      if ((int)(lt % GW) != warp) continue;
+      const TileCoord tc = tile_coord(a, tile, BN);
+      const uint32_t s = lt % STAGES;
+      const uint32_t ph = (lt / STAGES) & 1u;
+      bool ok = true;
+      if (lane == 0 && lt >= (uint32_t)STAGES) ok = mbar_wait(&empty[s], ph ^ 1u);
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (!ok) {
+        if (lane == 0) {
+          flag_error(c.err, KERR_TIMEOUT);
+          atomicExch(&s_abort, 1);
+        }
+        break;
+      }
+      if (lane == 0) {
+        mbar_expect_tx(&full[s], Cfg::B_BYTES);
+        tma_load_2d(sB + s * Cfg::B_BYTES, &plan.b, &full[s], 0, tc.n0);
+      }
+      uint8_t* dA = sA + s * Cfg::A_BYTES;
+      uint2 q[4][9];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {          // issue all 36 loads before using any
+        const int r = lane + 32 * i;
+        const int m = tc.m0 + r;
+        const int n = m / plane, rem = m % plane;
+        const int y = rem / a.Wp - 1, x = rem % a.Wp - 1;
+        const bool in = m < a.M_total && y >= 0 && y < c.Ho && x >= 0 && x < c.Wo;
+#pragma unroll
+        for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+          for (int kx = 0; kx < 3; ++kx)
+            // the letterbox halo is zero: (y + ky - 1, x + kx - 1) is always addressable
+            q[i][ky * 3 + kx] = in ? *reinterpret_cast<const uint2*>(lb + tview_off(c.in, n, y + ky - 1, x + kx - 1))
+                                   : make_uint2(0u, 0u);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int r = lane + 32 * i;
+        __nv_bfloat16 v[32];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+          const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&q[i][t]);
+          v[3 * t] = e[0];
+          v[3 * t + 1] = e[1];
+          v[3 * t + 2] = e[2];
+        }
+#pragma unroll
+        for (int j = 27; j < 32; ++j) v[j] = __float2bfloat16_rn(0.f);
+        const uint4* v4 = reinterpret_cast<const uint4*>(v);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) *reinterpret_cast<uint4*>(dA + stage_off<32>(r, u)) = v4[u];
+      }
+      fence_proxy_async();              // generic-proxy smem writes -> visible to tcgen05.mma
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&full[s]);
+    }
+  } else if (warp == 0 && GW == 1) {
     if (lane == 0) {
       // ---------------- TMA producer
       for (int i = 0; i < 4; ++i)
@@ -208,7 +275,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
         }
       }
     }
-  } else if (warp == 1) {
+  } else if (warp == GW) {
     if (lane == 0) {
       // ---------------- MMA issuer
       constexpr uint32_t idesc = idesc_bf16(128, BN);
@@ -247,9 +314,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
         if (!ok) break;
       }
     }
-  } else {
-    // ---------------- epilogue: group g = (warp - 2) / 4 takes the tiles whose local index has parity g
-    const int ew = warp - 2;
+  } else if (warp > GW) {
+    // ---------------- epilogue: group g takes the tiles whose local index has parity g
+    const int ew = warp - GW - 1;
     const int g = ew >> 2;
     const int quarter = warp & 3;           // TMEM lanes a warp may read: 32 * (warp % 4) ...
     const int row = quarter * 32 + lane;
@@ -270,7 +337,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
       const TileCoord tc = tile_coord(a, tile, BN);
       int n = 0, y = 0, x = 0;
       bool valid;
-      if (a.mode == 0) {
+      if (a.mode != 1) {
         const int m = tc.m0 + row;
         const int plane = a.Hp * a.Wp;
         n = m / plane;
@@ -354,7 +421,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
           if (elected && ok && !aborted(&s_abort)) {
             for (int j = 0; j < Cfg::NSUB; ++j) {
               const int ch = tc.n0 + p * Cfg::SWC + j * Cfg::SUB;
-              if (a.mode == 0)
+              if (a.mode != 1)
                 tma_store_2d(&plan.o, stg + j * Cfg::SUB_BYTES, ch, tc.m0);
               else
                 tma_store_4d(&plan.o, stg + j * Cfg::SUB_BYTES, ch, tc.ox0 + 1, tc.oy0 + 1, tc.img);
@@ -400,7 +467,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
   __syncwarp();
   tc_fence_before();
   __syncthreads();
-  if (warp == 1) tmem_dealloc(tmem, Cfg::TMEM_COLS);
+  if (warp == GW) tmem_dealloc(tmem, Cfg::TMEM_COLS);
 }
 
 // ----------------------------------------------------------------------------- host side
@@ -442,12 +509,12 @@ int sm_count() {
   return n;
 }
 
-template <int BN, int BKC, int STAGES>
+template <int BN, int BKC, int STAGES, int GW = 1>
 cudaError_t launch_cfg(const TcPlan& p, const TcArgs& a, cudaStream_t st) {
   using Cfg = TcCfg<BN, BKC, STAGES>;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<BN, BKC, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<BN, BKC, STAGES, GW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          Cfg::SMEM);
     if (e != cudaSuccess) return e;
     attr_set = true;
@@ -455,7 +522,7 @@ cudaError_t launch_cfg(const TcPlan& p, const TcArgs& a, cudaStream_t st) {
   const int tiles = p.m_tiles * p.n_tiles;
   const int grid = tiles < sm_count() ? tiles : sm_count();
   jde_count_launch();
-  conv_tc_kernel<BN, BKC, STAGES><<<grid, TC_THREADS, Cfg::SMEM, st>>>(p, a);
+  conv_tc_kernel<BN, BKC, STAGES, GW><<<grid, tc_threads(GW), Cfg::SMEM, st>>>(p, a);
   return cudaGetLastError();
 }
 
@@ -472,6 +539,34 @@ bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const __nv_bfloat16* w, int c
                   size_t msg_len) {
   plan = TcPlan();
   plan.spec = c;
+  if (c.cin == 3 && c.k == 3 && c.stride == 1 && c.in.dtype == 1 && c.in.pad == 1 && c.in.pixstride == 4 &&
+      (bn == 32 || bn == 64)) {
+    // stem: im2col rows gathered in the kernel (K = 27 padded to 32), flat over the padded image
+    plan.mode = 2;
+    plan.bn = bn;
+    plan.bkc = 32;
+    plan.cin_blocks = 1;
+    plan.kt_total = 1;
+    plan.n_tiles = cout_pad / bn;
+    plan.Hp = c.in.h + 2;
+    plan.Wp = c.in.w + 2;
+    plan.M_total = c.in.n * plan.Hp * plan.Wp;
+    plan.m_tiles = (plan.M_total + 127) / 128;
+    cuuint64_t dims[2] = {32, (cuuint64_t)cout_pad};
+    cuuint64_t strides[1] = {32 * 2};
+    cuuint32_t box[2] = {32, (cuuint32_t)bn};
+    bool ok = encode(&plan.b, 2, const_cast<__nv_bfloat16*>(w), dims, strides, box, 32);
+    const int sub = bn < 64 ? bn : 64;
+    plan.tma_out = c.out.dtype == 1 && c.out.pad == 1 && !c.upsample && c.cout % sub == 0;
+    if (plan.tma_out) {
+      cuuint64_t od[2] = {(cuuint64_t)c.cout, (cuuint64_t)plan.M_total};
+      cuuint64_t os[1] = {(cuuint64_t)c.out.pixstride * 2};
+      cuuint32_t ob[2] = {(cuuint32_t)sub, 128};
+      ok &= encode(&plan.o, 2, c.out.ptr, od, os, ob, sub);
+    }
+    if (!ok) snprintf(msg, msg_len, "cuTensorMapEncodeTiled failed (stem)");
+    return ok;
+  }
   const int bkc = (c.cin % 64 == 0) ? 64 : (c.cin % 32 == 0 ? 32 : 0);
   if (!bkc || c.in.dtype != 1 || c.in.pad != 1 || !(c.k == 1 || c.k == 3) || !(c.stride == 1 || c.stride == 2) ||
       (c.stride == 2 && c.k != 3) || (bn != 32 && bn != 64 && bn != 128 && bn != 256) || cout_pad % bn) {
@@ -582,6 +677,11 @@ cudaError_t conv_tc_launch(const TcPlan& p, cudaStream_t st) {
   a.tma_out = p.tma_out;
   a.tma_res = p.tma_res;
   a.c = p.spec;
+  if (p.mode == 2) {
+    if (p.bn == 32) return launch_cfg<32, 32, 16, 4>(p, a, st);
+    if (p.bn == 64) return launch_cfg<64, 32, 16, 4>(p, a, st);
+    return cudaErrorInvalidValue;
+  }
   if (p.bkc == 64) {
     switch (p.bn) {
       case 32: return launch_cfg<32, 64, 10>(p, a, st);

@@ -57,7 +57,6 @@ void letterbox_f32_launch(const uint8_t* frames, int n, int src_w, int src_h, co
                           TView out, cudaStream_t st);
 void letterbox_bf16x4_launch(const uint8_t* frames, int n, int src_w, int src_h, const LbAxis* xs,
                              const LbAxis* ys, TView out, cudaStream_t st);
-void stem_im2col_launch(TView lb4, __nv_bfloat16* rows, cudaStream_t st);
 
 // Post-processing.
 struct HeadGeom {

@@ -94,8 +94,8 @@ struct LayerIO {
   int head;        // output is a head tensor (f32, unpadded): 0..2 det, 3..5 emb, -1 otherwise
 };
 
-// Tensor ids: 0..77 = output of layer l, 78 = cat16, 79 = cat8, 80 = letterbox, 81 = stem im2col rows.
-enum { T_CAT16 = 78, T_CAT8 = 79, T_LB = 80, T_IM2COL = 81, T_COUNT = 82 };
+// Tensor ids: 0..77 = output of layer l, 78 = cat16, 79 = cat8, 80 = letterbox.
+enum { T_CAT16 = 78, T_CAT8 = 79, T_LB = 80, T_COUNT = 81 };
 
 struct TensorDesc {
   int h, w, c;     // unpadded size at the given input resolution (per frame)
@@ -269,7 +269,6 @@ void tensor_desc_table(const jde_handle* h, int in_w, int in_h, std::vector<Tens
   td[T_CAT16] = TensorDesc{in_h / 16, in_w / 16, 768, 1, bf16 ? 0 : 1, -1, 0};
   td[T_CAT8] = TensorDesc{in_h / 8, in_w / 8, 384, 1, bf16 ? 0 : 1, -1, 0};
   td[T_LB] = TensorDesc{in_h, in_w, bf16 ? 4 : 3, 1, bf16 ? 0 : 1, -1, 0};
-  td[T_IM2COL] = TensorDesc{in_h, in_w, 32, 1, 0, -1, 0};
 }
 
 size_t tensor_bytes(const TensorDesc& d, int n) {
@@ -295,7 +294,6 @@ jde_status get_res(jde_handle* h, int in_w, int in_h, ResBuffers** out) {
   const bool bf16 = h->cfg.precision == JDE_BF16;
   for (int t = 0; t < T_COUNT; ++t) {
     if (rb.td[t].alias >= 0) continue;
-    if (t == T_IM2COL && !bf16) continue;
     const bool head = t < JDE_NUM_LAYERS && h->io[t].head >= 0;
     rb.set_bytes[t] = tensor_bytes(rb.td[t], n);
     const size_t b = rb.set_bytes[t] * (head ? 2 : 1);
@@ -372,21 +370,6 @@ jde_status get_plan(jde_handle* h, ResBuffers* rb, int n, Plan** out) {
     c.upsample = io.upsample;
     c.bias = h->w[l].bias;
     c.err = h->d_err;
-    if (bf16 && l == 0) {
-      // the stem runs as a 1x1 conv over its im2col rows (27 values padded to 32)
-      TView r;
-      r.ptr = rb->mem[T_IM2COL];
-      r.n = n;
-      r.h = rb->in_h;
-      r.w = rb->in_w;
-      r.c = 32;
-      r.pad = 1;
-      r.pixstride = 32;
-      r.dtype = 1;
-      c.in = r;
-      c.k = 1;
-      c.cin = 32;
-    }
     p.specs[l] = c;
     if (bf16) {
       char msg[256];
@@ -680,7 +663,6 @@ jde_status jde_forward(jde_handle* h, const uint8_t* frames, int n, int src_w, i
   if (h->prof[0]) cudaEventRecord(h->prof[0], st);
   if (bf16) {
     letterbox_bf16x4_launch(frames, n, src_w, src_h, h->lb_x, h->lb_y, lb, st);
-    stem_im2col_launch(lb, static_cast<__nv_bfloat16*>(rb->mem[T_IM2COL]), st);
   } else {
     letterbox_f32_launch(frames, n, src_w, src_h, h->lb_x, h->lb_y, lb, st);
   }
@@ -823,22 +805,11 @@ jde_status jde_get_tensor(jde_handle* h, int id, void* dst, size_t dst_bytes, in
     tid = id;
   else if (id == 100)
     tid = T_LB;
-  else if (id == 101 && h->cfg.precision == JDE_BF16)
-    tid = T_IM2COL;
   else
     return fail(h, JDE_ERR_NOT_FOUND, "unknown tensor id %d", id);
   TView v = view_of(*h->cur, tid, h->cur_n);
   if (tid < JDE_NUM_LAYERS && h->io[tid].head >= 0)
     v.ptr = static_cast<char*>(v.ptr) + (size_t)h->cur_set * h->cur->set_bytes[tid];
-  if (tid == T_IM2COL) {   // raw rows over the padded domain
-    v.ptr = h->cur->mem[T_IM2COL];
-    v.h = h->cur->in_h + 2;
-    v.w = h->cur->in_w + 2;
-    v.c = 32;
-    v.pad = 0;
-    v.pixstride = 32;
-    v.dtype = 1;
-  }
   if (dims) {
     dims[0] = v.n;
     dims[1] = v.h;

@@ -1,4 +1,4 @@
-// Letterbox resize of uint8 RGB frames to the network input, and the stem's im2col rows.
+// Letterbox resize of uint8 RGB frames to the network input.
 //
 // Geometry (the paper only states FullHD input, Sec. 5.1): r = min(dst_w/src_w,
 // dst_h/src_h); the image is resized to floor(src r + 0.5) on each axis,
@@ -95,40 +95,6 @@ __global__ void letterbox_bf16x4_kernel(const uint8_t* frames, int n, int src_w,
   *reinterpret_cast<uint2*>(static_cast<__nv_bfloat16*>(out.ptr) + tview_off(out, f, y, x)) = q;
 }
 
-// Stem im2col: one 32-value bf16 row per pixel of the padded output domain,
-// value (ky*3 + kx)*3 + c = lb[n, y + ky - 1, x + kx - 1, c] (0 outside the
-// image, i.e. the conv's zero padding), values 27..31 = 0.  Halo rows are left
-// untouched (they are zero and their outputs are discarded).
-__global__ void stem_im2col_kernel(TView lb, __nv_bfloat16* rows) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long total = (long long)lb.n * lb.h * lb.w;
-  if (idx >= total) return;
-  const int x = (int)(idx % lb.w);
-  const int y = (int)((idx / lb.w) % lb.h);
-  const int f = (int)(idx / ((long long)lb.w * lb.h));
-  const __nv_bfloat16* src = static_cast<const __nv_bfloat16*>(lb.ptr);
-  __nv_bfloat16 v[32];
-#pragma unroll
-  for (int ky = 0; ky < 3; ++ky)
-#pragma unroll
-    for (int kx = 0; kx < 3; ++kx) {
-      // the halo of lb is zero, so (y + ky - 1, x + kx - 1) is always addressable
-      const uint2 q = *reinterpret_cast<const uint2*>(src + tview_off(lb, f, y + ky - 1, x + kx - 1));
-      const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&q);
-      const int t = (ky * 3 + kx) * 3;
-      v[t] = e[0];
-      v[t + 1] = e[1];
-      v[t + 2] = e[2];
-    }
-#pragma unroll
-  for (int j = 27; j < 32; ++j) v[j] = __float2bfloat16_rn(0.f);
-  const size_t row = ((size_t)f * (lb.h + 2) + y + 1) * (lb.w + 2) + x + 1;
-  uint4* o = reinterpret_cast<uint4*>(rows + row * 32);
-  const uint4* s4 = reinterpret_cast<const uint4*>(v);
-#pragma unroll
-  for (int j = 0; j < 4; ++j) o[j] = s4[j];
-}
-
 }  // namespace
 
 void letterbox_tables_launch(LbAxis* xs, LbAxis* ys, int src_w, int src_h, int dst_w, int dst_h, double r, int nw,
@@ -150,10 +116,4 @@ void letterbox_bf16x4_launch(const uint8_t* frames, int n, int src_w, int src_h,
   const long long total = (long long)n * out.h * out.w;
   jde_count_launch();
   letterbox_bf16x4_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(frames, n, src_w, src_h, xs, ys, out);
-}
-
-void stem_im2col_launch(TView lb4, __nv_bfloat16* rows, cudaStream_t st) {
-  const long long total = (long long)lb4.n * lb4.h * lb4.w;
-  jde_count_launch();
-  stem_im2col_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(lb4, rows);
 }
