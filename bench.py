@@ -116,6 +116,20 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def whole_job_rate(units_per_rank, local_ms, dist=None, device=None):
+    """Replicas: every rank processed `units_per_rank` units in `local_ms`; the job took the
+    slowest rank's time.  Returns (units/s over all ranks, max ms)."""
+    ms = local_ms
+    world = 1
+    if dist is not None and dist.is_initialized():
+        import torch
+        world = dist.get_world_size()
+        t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return world * units_per_rank / (ms / 1000.0), ms
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -328,11 +342,77 @@ def main():
     total_ms = t_start.elapsed_time(t_end)
     conv_ms = sum(p[1].elapsed_time(p[2]) for p in prof)
     fwd_ms = sum(p[0].elapsed_time(p[2]) for p in prof)
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * B * K / (total_ms / 1000.0)
+    value, total_ms = whole_job_rate(B * K, total_ms, dist, dev)
+
+    # batch sweep (the batches of the BF16 configuration), same pipelined step on n frames / n streams
+    sweep = {}
+    if rank == 0:
+        for n in [b for b in (1, 4, 8, 16) if b <= B]:
+            ks, ws = 10, 3
+            ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(ks + ws)]
+            ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(ks + ws)]
+            evf = [torch.cuda.Event() for _ in range(ks + ws)]
+            sub_dets = jde.make_dets(rows[:n], count[:n], None, cap=cap)
+            sub_tr = jde.make_tracks(*[x[:n] for x in tr], cap=tcap)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            for i in range(ks + ws):
+                if i == ws:
+                    a0.record(F)
+                    P.wait_event(a0)
+                t = W + args.soak + (i % K)
+                if i >= 2:
+                    F.wait_event(ev1[i - 2])
+                ev0[i].record(F)
+                jde.jde_forward(h, frames[i % NF][:n], n, SRC_W, SRC_H, IN_W, IN_H, True, F)
+                evf[i].record(F)
+                P.wait_event(evf[i])
+                jde.jde_postprocess(h, [x[:n] for x in heads[t]], n, IN_W, IN_H, SRC_W, SRC_H, sub_dets, P)
+                jde.jde_track_step(h, list(range(n)), sub_dets, sub_tr, P)
+                ev1[i].record(P)
+            F.wait_event(ev1[ks + ws - 1])
+            a1.record(F)
+            torch.cuda.synchronize()
+            lat = sorted(ev0[i].elapsed_time(ev1[i]) for i in range(ws, ws + ks))
+            sweep[str(n)] = {"fps": n * ks / (a0.elapsed_time(a1) / 1000.0), "p50_ms": lat[len(lat) // 2],
+                             "p99_ms": lat[-1]}
+
+        # batch 1 captured in one CUDA graph (forward + post-processing + tracker step): launch-bound regime
+        g1_dets = jde.make_dets(rows[:1], count[:1], None, cap=cap)
+        g1_tr = jde.make_tracks(*[x[:1] for x in tr], cap=tcap)
+        gs = torch.cuda.Stream(device=dev)
+        hd1 = [x[:1] for x in heads[W]]
+
+        def one():
+            jde.jde_forward(h, frames[0][:1], 1, SRC_W, SRC_H, IN_W, IN_H, True, gs)
+            jde.jde_postprocess(h, hd1, 1, IN_W, IN_H, SRC_W, SRC_H, g1_dets, gs)
+            jde.jde_track_step(h, [0], g1_dets, g1_tr, gs)
+
+        with torch.cuda.stream(gs):
+            for _ in range(3):
+                one()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(gs)
+        for _ in range(20):
+            one()
+        e1.record(gs)
+        torch.cuda.synchronize()
+        eager_ms = e0.elapsed_time(e1) / 20
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=gs):
+            one()
+        with torch.cuda.stream(gs):
+            graph.replay()
+            torch.cuda.synchronize()
+            e0.record(gs)
+            for _ in range(20):
+                graph.replay()
+            e1.record(gs)
+        torch.cuda.synchronize()
+        graph_ms = e0.elapsed_time(e1) / 20
+        sweep["1_graph"] = {"fps": 1000.0 / graph_ms, "ms": graph_ms, "eager_ms": eager_ms}
+        assert jde.jde_kernel_errors(h) == 0
 
     # roofline of the convolutions (tcgen05 implicit GEMM): algorithmic FLOPs / measured conv time
     flops_frame = conv_flops(table, IN_W, IN_H)
@@ -425,6 +505,7 @@ def main():
                                    "(two-stream pipeline: post-processing of batch t overlaps the forward of t+1)"},
             "stages_ms_per_step": {"forward": fwd_ms / K, "convs": conv_ms / K},
             "fp32_plain_batch1": fp32,
+            "batch_sweep": sweep,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -191,3 +191,22 @@ def test_detect_batch_host_buffers_end_to_end_320x192():
             assert count[f] > 0
     finally:
         j.jde_destroy(h)
+
+
+@pytest.mark.parametrize("in_w,in_h,n", [(864, 480, 4), (576, 320, 8)])
+def test_bf16_other_resolutions_and_batches_on_one_handle(in_w, in_h, n):
+    """One handle serves several model input sizes (buffers and plans per resolution): run
+    1088x608 first, then the smaller size, and check the last frame of the batch against the oracle."""
+    j = jde()
+    h = make_handle(j.JDE_BF16, max_batch=8, in_w=1088, in_h=608)
+    try:
+        forward(h, synth.frames_uniform(5, 2, 1080, 1920), 1088, 608)
+        frames = synth.frames_uniform(6, n, 1080, 1920)
+        heads = forward(h, frames, in_w, in_h)
+        x = net.letterbox(frames[n - 1:n], in_w, in_h)
+        dets, embs, _ = net.forward(x, oracle_layers())
+        errs = [rel_maxabs(g[n - 1:n], o) for g, o in zip(heads, dets + embs)]
+        print(in_w, in_h, "head errors", errs)
+        assert max(errs) < 2e-2
+    finally:
+        j.jde_destroy(h)
