@@ -33,8 +33,14 @@ struct TcArgs {
   int M_total, Hp, Wp;
   int TW, TH, tiles_x, tiles_y, n_tiles, total_tiles;
   int tma_out, tma_res;
+  int stride, WW, WH, win_bytes;   // window gather (mode 3): input window of one output patch
   ConvSpec c;
 };
+
+// Modes: 0 flat stride-1 (TMA per tap), 1 stride-2 patch (TMA per tap from parity maps),
+// 2 stem (im2col gathered from the letterbox), 3 32-channel 3x3 (input window of a patch
+// loaded once, two taps per K=64 block built in shared memory, weights resident).
+__device__ __forceinline__ bool patch_mode(int mode) { return mode == 1 || mode == 3; }
 
 // warp 0: TMA producer; warp 1: MMA issuer + TMEM owner; warps 2..9: epilogue in two
 // groups of four, group g draining TMEM accumulator buffer g (tiles alternate).
@@ -123,7 +129,7 @@ __device__ __forceinline__ TileCoord tile_coord(const TcArgs& a, int tile, int b
   t.img = 0;
   t.oy0 = 0;
   t.ox0 = 0;
-  if (a.mode != 1) {
+  if (!patch_mode(a.mode)) {
     t.m0 = m_tile * 128;
   } else {
     const int per_img = a.tiles_x * a.tiles_y;
@@ -147,28 +153,38 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
   __shared__ int s_abort;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
-  uint8_t* sB = smem + STAGES * Cfg::A_BYTES;
-  uint8_t* sC = sB + STAGES * Cfg::B_BYTES;              // 2 staging tiles
+  uint8_t* sB = smem + STAGES * Cfg::A_BYTES;            // B ring, or all K-blocks of B (mode 3)
+  const int b_region = a.mode == 3 ? a.kt_total * Cfg::B_BYTES : STAGES * Cfg::B_BYTES;
+  uint8_t* sWin = sB + b_region;                         // mode 3: two input windows
+  uint8_t* sC = sWin + (a.mode == 3 ? 2 * a.win_bytes : 0);   // 2 staging tiles
   uint64_t* full = reinterpret_cast<uint64_t*>(sC + 2 * Cfg::C_BYTES);
   uint64_t* empty = full + STAGES;
   uint64_t* acc_full = empty + STAGES;   // [2] MMA -> epilogue group
   uint64_t* acc_empty = acc_full + 2;    // [2] epilogue group -> MMA
   uint64_t* res_full = acc_empty + 2;    // [2] residual tile landed in staging tile g
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(res_full + 2);
+  uint64_t* win_full = res_full + 2;     // [2] mode 3: input window landed
+  uint64_t* win_empty = win_full + 2;    // [2] mode 3: window consumed by the gather warps
+  uint64_t* b_full = win_empty + 2;      // mode 3: resident weights landed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(b_full + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const ConvSpec& c = a.c;
 
   if (threadIdx.x == 0) {
+    // stem: TMA (B) arrival + the gather warp's arrival; mode 3: one arrival per gather warp
+    const int full_count = a.mode == 2 ? 2 : (a.mode == 3 ? GW : 1);
     for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], a.mode == 2 ? 2 : 1);   // stem: TMA (B) arrival + the gather warp's arrival
+      mbar_init(&full[s], full_count);
       mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
       mbar_init(&acc_empty[b], EPI_WARPS / 2);
       mbar_init(&res_full[b], 1);
+      mbar_init(&win_full[b], 1);
+      mbar_init(&win_empty[b], GW);
     }
+    mbar_init(b_full, 1);
     fence_barrier_init();
     s_abort = 0;
   }
@@ -243,6 +259,75 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
       __syncwarp();
       if (lane == 0) mbar_arrive(&full[s]);
     }
+  } else if (warp < GW && a.mode == 3) {
+    // ---------------- window gather: per output patch one TMA load of the input window
+    // (32 channels, SWIZZLE_NONE, double-buffered); every K=64 block packs two taps
+    // (taps 2kb, 2kb+1; the tenth is zero) into a 128-byte-swizzled A stage; warp w builds rows
+    // 32w .. 32w+31.  The weights of all K-blocks are loaded once and stay resident.
+    const int r = warp * 32 + lane;
+    const int ly = r / a.TW, lx = r % a.TW;
+    if (warp == 0 && lane == 0) {
+      tma_prefetch(&plan.a[0]);
+      mbar_expect_tx(b_full, (uint32_t)(a.kt_total * Cfg::B_BYTES));
+      for (int kb = 0; kb < a.kt_total; ++kb) tma_load_2d(sB + kb * Cfg::B_BYTES, &plan.b, b_full, kb * 64, 0);
+    }
+    auto issue_window = [&](int tile, uint32_t lt) -> bool {
+      const uint32_t wb = lt & 1u;
+      if (lt >= 2 && !mbar_wait(&win_empty[wb], ((lt >> 1) - 1) & 1u)) return false;
+      const TileCoord tc = tile_coord(a, tile, BN);
+      mbar_expect_tx(&win_full[wb], (uint32_t)(a.WW * a.WH * 64));
+      tma_load_4d(sWin + wb * a.win_bytes, &plan.a[0], &win_full[wb], 0, a.stride * tc.ox0, a.stride * tc.oy0,
+                  tc.img);
+      return true;
+    };
+    bool ok = true;
+    if (warp == 0 && lane == 0 && (int)blockIdx.x < a.total_tiles) ok = issue_window(blockIdx.x, 0);
+    uint32_t lt = 0, it = 0;
+    for (int tile = blockIdx.x; tile < a.total_tiles && ok && !aborted(&s_abort); tile += gridDim.x, ++lt) {
+      const uint32_t wb = lt & 1u;
+      if (warp == 0 && lane == 0 && tile + (int)gridDim.x < a.total_tiles)
+        ok = issue_window(tile + gridDim.x, lt + 1);       // prefetch the next patch's window
+      if (!mbar_wait(&win_full[wb], (lt >> 1) & 1u)) ok = false;
+      const uint8_t* win = sWin + wb * a.win_bytes;
+      for (int kb = 0; kb < a.kt_total && ok; ++kb, ++it) {
+        const uint32_t s = it % STAGES;
+        const uint32_t ph = (it / STAGES) & 1u;
+        if (it >= (uint32_t)STAGES && !mbar_wait(&empty[s], ph ^ 1u)) {
+          ok = false;
+          break;
+        }
+        uint8_t* dA = sA + s * Cfg::A_BYTES + r * 128;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          const int tap = 2 * kb + half;
+          // lanes start at different 16-byte units (rotation) to spread shared-memory banks
+          uint4 q[4];
+          if (tap < 9) {
+            const int wy = a.stride * ly + tap / 3, wx = a.stride * lx + tap % 3;
+            const uint4* src = reinterpret_cast<const uint4*>(win + (wy * a.WW + wx) * 64);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) q[j] = src[(j + lane) & 3];
+          } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) q[j] = make_uint4(0u, 0u, 0u, 0u);
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int u = half * 4 + ((j + lane) & 3);
+            *reinterpret_cast<uint4*>(dA + ((u ^ (r & 7)) << 4)) = q[j];
+          }
+        }
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&full[s]);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&win_empty[wb]);
+    }
+    if (!ok && lane == 0) {
+      flag_error(c.err, KERR_TIMEOUT);
+      atomicExch(&s_abort, 1);
+    }
   } else if (warp == 0 && GW == 1) {
     if (lane == 0) {
       // ---------------- TMA producer
@@ -287,6 +372,11 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
           atomicExch(&s_abort, 1);
           break;
         }
+        if (local == 0 && a.mode == 3 && !mbar_wait(b_full, 0)) {
+          flag_error(c.err, KERR_TIMEOUT);
+          atomicExch(&s_abort, 1);
+          break;
+        }
         tc_fence_after();
         const uint32_t d = tmem + buf * BN;
         bool ok = true;
@@ -301,7 +391,7 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
           }
           tc_fence_after();
           const uint32_t a_base = smem_u32(sA + s * Cfg::A_BYTES);
-          const uint32_t b_base = smem_u32(sB + s * Cfg::B_BYTES);
+          const uint32_t b_base = smem_u32(sB + (a.mode == 3 ? kt : (int)s) * Cfg::B_BYTES);
 #pragma unroll
           for (int kk = 0; kk < BKC / 16; ++kk) {
             const uint64_t ad = smem_desc(a_base + kk * 32, Cfg::SBO, Cfg::LAYOUT);
@@ -337,7 +427,7 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
       const TileCoord tc = tile_coord(a, tile, BN);
       int n = 0, y = 0, x = 0;
       bool valid;
-      if (a.mode != 1) {
+      if (!patch_mode(a.mode)) {
         const int m = tc.m0 + row;
         const int plane = a.Hp * a.Wp;
         n = m / plane;
@@ -360,9 +450,13 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
             bulk_wait_read0();              // the previous store has finished reading the staging tile
             if (use_res) {
               mbar_expect_tx(&res_full[g], Cfg::C_BYTES);
-              for (int j = 0; j < Cfg::NSUB; ++j)
-                tma_load_2d(stg + j * Cfg::SUB_BYTES, &plan.r, &res_full[g], tc.n0 + p * Cfg::SWC + j * Cfg::SUB,
-                            tc.m0);
+              for (int j = 0; j < Cfg::NSUB; ++j) {
+                const int ch = tc.n0 + p * Cfg::SWC + j * Cfg::SUB;
+                if (patch_mode(a.mode))
+                  tma_load_4d(stg + j * Cfg::SUB_BYTES, &plan.r, &res_full[g], ch, tc.ox0 + 1, tc.oy0 + 1, tc.img);
+                else
+                  tma_load_2d(stg + j * Cfg::SUB_BYTES, &plan.r, &res_full[g], ch, tc.m0);
+              }
             }
           }
           named_bar(bar_id, 128);
@@ -421,7 +515,7 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
           if (elected && ok && !aborted(&s_abort)) {
             for (int j = 0; j < Cfg::NSUB; ++j) {
               const int ch = tc.n0 + p * Cfg::SWC + j * Cfg::SUB;
-              if (a.mode != 1)
+              if (!patch_mode(a.mode))
                 tma_store_2d(&plan.o, stg + j * Cfg::SUB_BYTES, ch, tc.m0);
               else
                 tma_store_4d(&plan.o, stg + j * Cfg::SUB_BYTES, ch, tc.ox0 + 1, tc.oy0 + 1, tc.img);
@@ -493,8 +587,10 @@ bool encode(CUtensorMap* m, int rank, void* base, const cuuint64_t* dims, const 
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  const CUtensorMapSwizzle swz =
+      bkc == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : (bkc == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE);
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, base, dims, strides_bytes, box, es,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, bkc == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -510,19 +606,20 @@ int sm_count() {
 }
 
 template <int BN, int BKC, int STAGES, int GW = 1>
-cudaError_t launch_cfg(const TcPlan& p, const TcArgs& a, cudaStream_t st) {
+cudaError_t launch_cfg(const TcPlan& p, const TcArgs& a, cudaStream_t st, int smem = 0) {
   using Cfg = TcCfg<BN, BKC, STAGES>;
-  static bool attr_set = false;
-  if (!attr_set) {
+  if (!smem) smem = Cfg::SMEM;
+  static int attr_set = 0;
+  if (attr_set < smem) {
     cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<BN, BKC, STAGES, GW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Cfg::SMEM);
+                                         smem);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    attr_set = smem;
   }
   const int tiles = p.m_tiles * p.n_tiles;
   const int grid = tiles < sm_count() ? tiles : sm_count();
   jde_count_launch();
-  conv_tc_kernel<BN, BKC, STAGES, GW><<<grid, tc_threads(GW), Cfg::SMEM, st>>>(p, a);
+  conv_tc_kernel<BN, BKC, STAGES, GW><<<grid, tc_threads(GW), smem, st>>>(p, a);
   return cudaGetLastError();
 }
 
@@ -565,6 +662,59 @@ bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const __nv_bfloat16* w, int c
       ok &= encode(&plan.o, 2, c.out.ptr, od, os, ob, sub);
     }
     if (!ok) snprintf(msg, msg_len, "cuTensorMapEncodeTiled failed (stem)");
+    return ok;
+  }
+  if (c.cin == 32 && c.k == 3 && bn == 64 && cout_pad == 64 && c.in.dtype == 1 && c.in.pad == 1 &&
+      c.out.dtype == 1 && c.out.pad == 1 && !c.upsample && c.cout == 64) {
+    // 32-channel 3x3 (stride 1 or 2): input window of each 8x16 output patch, two taps per K block
+    plan.mode = 3;
+    plan.bn = 64;
+    plan.bkc = 64;
+    plan.cin_blocks = 1;
+    plan.kt_total = 5;                       // taps (0,1) (2,3) (4,5) (6,7) (8,-)
+    plan.n_tiles = 1;
+    plan.TW = 16;
+    plan.TH = 8;
+    plan.tiles_x = (c.Wo + plan.TW - 1) / plan.TW;
+    plan.tiles_y = (c.Ho + plan.TH - 1) / plan.TH;
+    plan.m_tiles = c.in.n * plan.tiles_x * plan.tiles_y;
+    plan.WW = c.stride * (plan.TW - 1) + 3;
+    plan.WH = c.stride * (plan.TH - 1) + 3;
+    plan.win_bytes = (plan.WW * plan.WH * 64 + 1023) / 1024 * 1024;
+    const int Hp = c.in.h + 2, Wp = c.in.w + 2;
+    plan.Hp = Hp;
+    plan.Wp = Wp;
+    bool ok = true;
+    {
+      cuuint64_t dims[4] = {32, (cuuint64_t)Wp, (cuuint64_t)Hp, (cuuint64_t)c.in.n};
+      cuuint64_t strides[3] = {(cuuint64_t)c.in.pixstride * 2, (cuuint64_t)Wp * c.in.pixstride * 2,
+                               (cuuint64_t)Hp * Wp * c.in.pixstride * 2};
+      cuuint32_t box[4] = {32, (cuuint32_t)plan.WW, (cuuint32_t)plan.WH, 1};
+      ok &= encode(&plan.a[0], 4, c.in.ptr, dims, strides, box, 0);
+    }
+    {
+      cuuint64_t dims[2] = {320, 64};
+      cuuint64_t strides[1] = {320 * 2};
+      cuuint32_t box[2] = {64, 64};
+      ok &= encode(&plan.b, 2, const_cast<__nv_bfloat16*>(w), dims, strides, box, 64);
+    }
+    plan.tma_out = 1;
+    {
+      cuuint64_t dims[4] = {64, (cuuint64_t)(c.Wo + 2), (cuuint64_t)(c.Ho + 2), (cuuint64_t)c.out.n};
+      cuuint64_t strides[3] = {(cuuint64_t)c.out.pixstride * 2, (cuuint64_t)(c.Wo + 2) * c.out.pixstride * 2,
+                               (cuuint64_t)(c.Ho + 2) * (c.Wo + 2) * c.out.pixstride * 2};
+      cuuint32_t box[4] = {64, (cuuint32_t)plan.TW, (cuuint32_t)plan.TH, 1};
+      ok &= encode(&plan.o, 4, c.out.ptr, dims, strides, box, 64);
+    }
+    plan.tma_res = c.res.ptr != nullptr && c.res.dtype == 1 && c.res.pad == 1;
+    if (plan.tma_res) {
+      cuuint64_t dims[4] = {64, (cuuint64_t)(c.Wo + 2), (cuuint64_t)(c.Ho + 2), (cuuint64_t)c.res.n};
+      cuuint64_t strides[3] = {(cuuint64_t)c.res.pixstride * 2, (cuuint64_t)(c.Wo + 2) * c.res.pixstride * 2,
+                               (cuuint64_t)(c.Ho + 2) * (c.Wo + 2) * c.res.pixstride * 2};
+      cuuint32_t box[4] = {64, (cuuint32_t)plan.TW, (cuuint32_t)plan.TH, 1};
+      ok &= encode(&plan.r, 4, c.res.ptr, dims, strides, box, 64);
+    }
+    if (!ok) snprintf(msg, msg_len, "cuTensorMapEncodeTiled failed (32-channel window conv)");
     return ok;
   }
   const int bkc = (c.cin % 64 == 0) ? 64 : (c.cin % 32 == 0 ? 32 : 0);
@@ -676,11 +826,21 @@ cudaError_t conv_tc_launch(const TcPlan& p, cudaStream_t st) {
   a.total_tiles = p.m_tiles * p.n_tiles;
   a.tma_out = p.tma_out;
   a.tma_res = p.tma_res;
+  a.stride = p.spec.stride;
+  a.WW = p.WW;
+  a.WH = p.WH;
+  a.win_bytes = p.win_bytes;
   a.c = p.spec;
   if (p.mode == 2) {
     if (p.bn == 32) return launch_cfg<32, 32, 16, 4>(p, a, st);
     if (p.bn == 64) return launch_cfg<64, 32, 16, 4>(p, a, st);
     return cudaErrorInvalidValue;
+  }
+  if (p.mode == 3) {
+    using Cfg = TcCfg<64, 64, 4>;
+    const int smem = 4 * Cfg::A_BYTES + p.kt_total * Cfg::B_BYTES + 2 * p.win_bytes + 2 * Cfg::C_BYTES + 1024 + 512;
+    if (p.bn != 64 || smem > 227 * 1024) return cudaErrorInvalidValue;
+    return launch_cfg<64, 64, 4, 4>(p, a, st, smem);
   }
   if (p.bkc == 64) {
     switch (p.bn) {

@@ -35,6 +35,7 @@ struct TcPlan {
   int m_tiles, n_tiles;
   int M_total, Hp, Wp;
   int TW, TH, tiles_x, tiles_y;
+  int WW, WH, win_bytes;         // mode 3: input window of one output patch
   ConvSpec spec;
 };
 // Fill plan (tensor maps and grid) for a conv whose input is a padded bf16

@@ -446,7 +446,8 @@ jde_status load_weights(jde_handle* h, const void* blob, size_t nbytes) {
     lw.cout_pad64 = align_up(L[l].cout, 64);
     lw.bn = conv_tc_pick_bn(L[l].cout);
     lw.cout_pad_tc = align_up(L[l].cout, lw.bn);
-    lw.k_tc = l == 0 ? 32 : K;
+    // stem: 27 taps x channels padded to 32; 32-channel 3x3: 9 taps padded to 10 (two taps per K=64 block)
+    lw.k_tc = l == 0 ? 32 : (L[l].cin == 32 && L[l].k == 3 ? 320 : K);
     const int bias_len = (lw.cout_pad64 > lw.cout_pad_tc ? lw.cout_pad64 : lw.cout_pad_tc) + 256;
     bool ok = dmalloc((void**)&lw.bias, sizeof(float) * bias_len);
     if (bf16)
