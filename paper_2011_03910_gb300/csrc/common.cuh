@@ -108,6 +108,14 @@ JDE_DEV void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c
       : "memory");
 }
 
+JDE_DEV void tma_load_5d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2, int c3, int c4) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6, %7}], "
+      "[%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+      : "memory");
+}
+
 // smem -> global tensor store (bulk async group of the issuing thread)
 JDE_DEV void tma_store_2d(const CUtensorMap* map, const void* src, int c0, int c1) {
   asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
@@ -174,6 +182,16 @@ JDE_DEV uint64_t smem_desc(uint32_t saddr, uint32_t sbo_bytes, uint32_t layout) 
   d |= (uint64_t)1 << 46;
   d |= (uint64_t)layout << 61;
   return d;
+}
+
+// Descriptor of a K-major tile without swizzle: core matrices of 8 rows x 16 bytes (rows 16 B
+// apart), `lbo` bytes between core matrices adjacent along K, `sbo` bytes between 8-row groups.
+JDE_DEV uint64_t smem_desc_noswz(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;   // layout type 0: no swizzle
 }
 
 // 32 lanes x 32 consecutive 32-bit TMEM columns -> 32 registers per thread.

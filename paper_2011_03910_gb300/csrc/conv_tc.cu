@@ -33,13 +33,16 @@ struct TcArgs {
   int M_total, Hp, Wp;
   int TW, TH, tiles_x, tiles_y, n_tiles, total_tiles;
   int tma_out, tma_res;
-  int stride, WW, WH, win_bytes;   // window gather (mode 3): input window of one output patch
+  int stride, WW, WH, win_bytes;   // mode 3: window (or parity sub-window) size in pixels, bytes per buffer
+  int plane;                       // mode 3: stride between 8-channel planes (128-byte aligned: TMA destinations)
+  int plane_tx;                    // mode 3: bytes one plane load delivers (WW * WH * 16)
   ConvSpec c;
 };
 
 // Modes: 0 flat stride-1 (TMA per tap), 1 stride-2 patch (TMA per tap from parity maps),
-// 2 stem (im2col gathered from the letterbox), 3 32-channel 3x3 (input window of a patch
-// loaded once, two taps per K=64 block built in shared memory, weights resident).
+// 2 stem (im2col gathered from the letterbox), 3 32-channel 3x3: the input window of an
+// 8x16 output patch is loaded once as four 8-channel planes, which is the no-swizzle K-major
+// operand layout, so each tap is the same window at another descriptor start; weights resident.
 __device__ __forceinline__ bool patch_mode(int mode) { return mode == 1 || mode == 3; }
 
 // warp 0: TMA producer; warp 1: MMA issuer + TMEM owner; warps 2..9: epilogue in two
@@ -61,7 +64,8 @@ struct TcCfg {
   static constexpr int SMEM = STAGES * STAGE_BYTES + 2 * C_BYTES + 1024 /*align*/ + 512 /*barriers*/;
   static constexpr uint32_t LAYOUT = BKC == 64 ? 2u : 4u;     // SW128 : SW64 (MMA operand tiles)
   static constexpr uint32_t SBO = 8 * BKC * 2;                 // bytes per 8-row group
-  static constexpr uint32_t TMEM_COLS = 2 * BN;                // two accumulator buffers
+  static constexpr int NBUF = BN <= 128 ? 4 : 2;               // TMEM accumulator buffers
+  static constexpr uint32_t TMEM_COLS = NBUF * BN;
   static_assert(SMEM <= 227 * 1024, "shared memory budget");
   static_assert(TMEM_COLS >= 32 && TMEM_COLS <= 512, "TMEM budget");
 };
@@ -152,16 +156,17 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
   extern __shared__ uint8_t smem_raw[];
   __shared__ int s_abort;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  // mode 3: [2 windows][resident B][staging]; otherwise [A ring][B ring][staging]
+  uint8_t* sWin = smem;
   uint8_t* sA = smem;
-  uint8_t* sB = smem + STAGES * Cfg::A_BYTES;            // B ring, or all K-blocks of B (mode 3)
+  uint8_t* sB = a.mode == 3 ? smem + 2 * a.win_bytes : smem + STAGES * Cfg::A_BYTES;
   const int b_region = a.mode == 3 ? a.kt_total * Cfg::B_BYTES : STAGES * Cfg::B_BYTES;
-  uint8_t* sWin = sB + b_region;                         // mode 3: two input windows
-  uint8_t* sC = sWin + (a.mode == 3 ? 2 * a.win_bytes : 0);   // 2 staging tiles
+  uint8_t* sC = sB + b_region;                           // 2 staging tiles
   uint64_t* full = reinterpret_cast<uint64_t*>(sC + 2 * Cfg::C_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* acc_full = empty + STAGES;   // [2] MMA -> epilogue group
-  uint64_t* acc_empty = acc_full + 2;    // [2] epilogue group -> MMA
-  uint64_t* res_full = acc_empty + 2;    // [2] residual tile landed in staging tile g
+  uint64_t* acc_full = empty + STAGES;   // [NBUF] MMA -> epilogue group
+  uint64_t* acc_empty = acc_full + Cfg::NBUF;   // [NBUF] epilogue group -> MMA
+  uint64_t* res_full = acc_empty + Cfg::NBUF;   // [2] residual tile landed in staging tile g
   uint64_t* win_full = res_full + 2;     // [2] mode 3: input window landed
   uint64_t* win_empty = win_full + 2;    // [2] mode 3: window consumed by the gather warps
   uint64_t* b_full = win_empty + 2;      // mode 3: resident weights landed
@@ -171,18 +176,20 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
   const ConvSpec& c = a.c;
 
   if (threadIdx.x == 0) {
-    // stem: TMA (B) arrival + the gather warp's arrival; mode 3: one arrival per gather warp
-    const int full_count = a.mode == 2 ? 2 : (a.mode == 3 ? GW : 1);
+    // stem: TMA (B) arrival + the gather warp's arrival
+    const int full_count = a.mode == 2 ? 2 : 1;
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], full_count);
       mbar_init(&empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < Cfg::NBUF; ++b) {
       mbar_init(&acc_full[b], 1);
       mbar_init(&acc_empty[b], EPI_WARPS / 2);
+    }
+    for (int b = 0; b < 2; ++b) {
       mbar_init(&res_full[b], 1);
       mbar_init(&win_full[b], 1);
-      mbar_init(&win_empty[b], GW);
+      mbar_init(&win_empty[b], 1);      // tcgen05.commit after the tile's MMAs
     }
     mbar_init(b_full, 1);
     fence_barrier_init();
@@ -259,74 +266,33 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
       __syncwarp();
       if (lane == 0) mbar_arrive(&full[s]);
     }
-  } else if (warp < GW && a.mode == 3) {
-    // ---------------- window gather: per output patch one TMA load of the input window
-    // (32 channels, SWIZZLE_NONE, double-buffered); every K=64 block packs two taps
-    // (taps 2kb, 2kb+1; the tenth is zero) into a 128-byte-swizzled A stage; warp w builds rows
-    // 32w .. 32w+31.  The weights of all K-blocks are loaded once and stay resident.
-    const int r = warp * 32 + lane;
-    const int ly = r / a.TW, lx = r % a.TW;
-    if (warp == 0 && lane == 0) {
-      tma_prefetch(&plan.a[0]);
+  } else if (warp == 0 && GW == 1 && a.mode == 3) {
+    if (lane == 0) {
+      // ---------------- window producer: resident weights once, then per patch the 8-channel
+      // planes of its input window (stride 2: of its four parity sub-windows)
       mbar_expect_tx(b_full, (uint32_t)(a.kt_total * Cfg::B_BYTES));
       for (int kb = 0; kb < a.kt_total; ++kb) tma_load_2d(sB + kb * Cfg::B_BYTES, &plan.b, b_full, kb * 64, 0);
-    }
-    auto issue_window = [&](int tile, uint32_t lt) -> bool {
-      const uint32_t wb = lt & 1u;
-      if (lt >= 2 && !mbar_wait(&win_empty[wb], ((lt >> 1) - 1) & 1u)) return false;
-      const TileCoord tc = tile_coord(a, tile, BN);
-      mbar_expect_tx(&win_full[wb], (uint32_t)(a.WW * a.WH * 64));
-      tma_load_4d(sWin + wb * a.win_bytes, &plan.a[0], &win_full[wb], 0, a.stride * tc.ox0, a.stride * tc.oy0,
-                  tc.img);
-      return true;
-    };
-    bool ok = true;
-    if (warp == 0 && lane == 0 && (int)blockIdx.x < a.total_tiles) ok = issue_window(blockIdx.x, 0);
-    uint32_t lt = 0, it = 0;
-    for (int tile = blockIdx.x; tile < a.total_tiles && ok && !aborted(&s_abort); tile += gridDim.x, ++lt) {
-      const uint32_t wb = lt & 1u;
-      if (warp == 0 && lane == 0 && tile + (int)gridDim.x < a.total_tiles)
-        ok = issue_window(tile + gridDim.x, lt + 1);       // prefetch the next patch's window
-      if (!mbar_wait(&win_full[wb], (lt >> 1) & 1u)) ok = false;
-      const uint8_t* win = sWin + wb * a.win_bytes;
-      for (int kb = 0; kb < a.kt_total && ok; ++kb, ++it) {
-        const uint32_t s = it % STAGES;
-        const uint32_t ph = (it / STAGES) & 1u;
-        if (it >= (uint32_t)STAGES && !mbar_wait(&empty[s], ph ^ 1u)) {
-          ok = false;
+      const int npar = a.stride == 2 ? 4 : 1;
+      uint32_t lt = 0;
+      for (int tile = blockIdx.x; tile < a.total_tiles && !aborted(&s_abort); tile += gridDim.x, ++lt) {
+        const uint32_t wb = lt & 1u;
+        if (lt >= 2 && !mbar_wait(&win_empty[wb], ((lt >> 1) - 1) & 1u)) {
+          flag_error(c.err, KERR_TIMEOUT);
+          atomicExch(&s_abort, 1);
           break;
         }
-        uint8_t* dA = sA + s * Cfg::A_BYTES + r * 128;
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-          const int tap = 2 * kb + half;
-          // lanes start at different 16-byte units (rotation) to spread shared-memory banks
-          uint4 q[4];
-          if (tap < 9) {
-            const int wy = a.stride * ly + tap / 3, wx = a.stride * lx + tap % 3;
-            const uint4* src = reinterpret_cast<const uint4*>(win + (wy * a.WW + wx) * 64);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) q[j] = src[(j + lane) & 3];
-          } else {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) q[j] = make_uint4(0u, 0u, 0u, 0u);
-          }
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int u = half * 4 + ((j + lane) & 3);
-            *reinterpret_cast<uint4*>(dA + ((u ^ (r & 7)) << 4)) = q[j];
-          }
+        const TileCoord tc = tile_coord(a, tile, BN);
+        if ((smem_u32(sWin + wb * a.win_bytes) | (uint32_t)a.plane) & 127u) {   // TMA destinations: 128-B aligned
+          flag_error(c.err, KERR_TIMEOUT);
+          atomicExch(&s_abort, 1);
+          break;
         }
-        fence_proxy_async();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&full[s]);
+        mbar_expect_tx(&win_full[wb], (uint32_t)(npar * 4 * a.plane_tx));
+        for (int par = 0; par < npar; ++par)
+          for (int j = 0; j < 4; ++j)
+            tma_load_5d(sWin + wb * a.win_bytes + (par * 4 + j) * a.plane, &plan.a[par], &win_full[wb], 0, j, tc.ox0,
+                        tc.oy0, tc.img);
       }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&win_empty[wb]);
-    }
-    if (!ok && lane == 0) {
-      flag_error(c.err, KERR_TIMEOUT);
-      atomicExch(&s_abort, 1);
     }
   } else if (warp == 0 && GW == 1) {
     if (lane == 0) {
@@ -366,8 +332,8 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
       constexpr uint32_t idesc = idesc_bf16(128, BN);
       uint32_t it = 0, local = 0;
       for (int tile = blockIdx.x; tile < a.total_tiles; tile += gridDim.x, ++local) {
-        const uint32_t buf = local & 1u, use = local >> 1;
-        if (local >= 2 && !mbar_wait(&acc_empty[buf], (use - 1) & 1u)) {
+        const uint32_t buf = local % Cfg::NBUF, use = local / Cfg::NBUF;
+        if (local >= (uint32_t)Cfg::NBUF && !mbar_wait(&acc_empty[buf], (use - 1) & 1u)) {
           flag_error(c.err, KERR_TIMEOUT);
           atomicExch(&s_abort, 1);
           break;
@@ -379,6 +345,35 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
         }
         tc_fence_after();
         const uint32_t d = tmem + buf * BN;
+        if (a.mode == 3) {
+          const uint32_t wb = local & 1u;
+          if (!mbar_wait(&win_full[wb], (local >> 1) & 1u)) {
+            flag_error(c.err, KERR_TIMEOUT);
+            atomicExch(&s_abort, 1);
+            break;
+          }
+          tc_fence_after();
+          const uint32_t win = smem_u32(sWin + wb * a.win_bytes);
+          const uint32_t row_bytes = (uint32_t)a.WW * 16u;
+#pragma unroll 1
+          for (int tap = 0; tap < 9; ++tap) {
+            const int ky = tap / 3, kx = tap % 3;
+            const int par = a.stride == 2 ? (ky & 1) * 2 + (kx & 1) : 0;
+            const int pix = a.stride == 2 ? (ky >> 1) * a.WW + (kx >> 1) : ky * a.WW + kx;
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk) {
+              const uint32_t a_addr = win + (uint32_t)((par * 4 + 2 * kk) * a.plane + pix * 16);
+              const uint64_t ad = smem_desc_noswz(a_addr, (uint32_t)a.plane, row_bytes);
+              const int kidx = tap * 32 + kk * 16;          // K index of this MMA's first element
+              const uint32_t b_addr = smem_u32(sB + (kidx >> 6) * Cfg::B_BYTES) + (uint32_t)((kidx & 63) * 2);
+              const uint64_t bd = smem_desc(b_addr, Cfg::SBO, Cfg::LAYOUT);
+              umma_bf16(d, ad, bd, idesc, (tap | kk) != 0 ? 1u : 0u);
+            }
+          }
+          umma_commit(&acc_full[buf]);
+          umma_commit(&win_empty[wb]);
+          continue;
+        }
         bool ok = true;
         for (int kt = 0; kt < a.kt_total; ++kt, ++it) {
           const uint32_t s = it % STAGES;
@@ -416,7 +411,7 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
     uint32_t res_uses = 0, local = 0;
     for (int tile = blockIdx.x; tile < a.total_tiles; tile += gridDim.x, ++local) {
       if ((local & 1u) != (uint32_t)g) continue;
-      const uint32_t buf = (uint32_t)g, use = local >> 1;
+      const uint32_t buf = local % Cfg::NBUF, use = local / Cfg::NBUF;
       bool ok = mbar_wait(&acc_full[buf], use & 1u);
       if (!ok) {
         flag_error(c.err, KERR_TIMEOUT);
@@ -666,31 +661,42 @@ bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const __nv_bfloat16* w, int c
   }
   if (c.cin == 32 && c.k == 3 && bn == 64 && cout_pad == 64 && c.in.dtype == 1 && c.in.pad == 1 &&
       c.out.dtype == 1 && c.out.pad == 1 && !c.upsample && c.cout == 64) {
-    // 32-channel 3x3 (stride 1 or 2): input window of each 8x16 output patch, two taps per K block
+    // 32-channel 3x3 (stride 1 or 2): the input window of each 8-wide, 16-high output patch
     plan.mode = 3;
     plan.bn = 64;
     plan.bkc = 64;
     plan.cin_blocks = 1;
-    plan.kt_total = 5;                       // taps (0,1) (2,3) (4,5) (6,7) (8,-)
+    plan.kt_total = 5;                       // resident weights: K = 9 taps x 32 ch, padded to 320
     plan.n_tiles = 1;
-    plan.TW = 16;
-    plan.TH = 8;
+    plan.TW = 8;
+    plan.TH = 16;
     plan.tiles_x = (c.Wo + plan.TW - 1) / plan.TW;
     plan.tiles_y = (c.Ho + plan.TH - 1) / plan.TH;
     plan.m_tiles = c.in.n * plan.tiles_x * plan.tiles_y;
-    plan.WW = c.stride * (plan.TW - 1) + 3;
-    plan.WH = c.stride * (plan.TH - 1) + 3;
-    plan.win_bytes = (plan.WW * plan.WH * 64 + 1023) / 1024 * 1024;
+    const int st = c.stride;
+    plan.WW = st == 1 ? plan.TW + 2 : plan.TW + 1;   // (sub-)window width in pixels
+    plan.WH = st == 1 ? plan.TH + 2 : plan.TH + 1;
+    // every plane is a TMA destination: its shared-memory address must be 128-byte aligned
+    plan.plane = (plan.WW * plan.WH * 16 + 127) / 128 * 128;
+    plan.win_bytes = ((st == 1 ? 4 : 16) * plan.plane + 1023) / 1024 * 1024;
+    if (plan.plane % 128 || plan.win_bytes % 1024) {
+      snprintf(msg, msg_len, "window planes not 128-byte aligned");
+      return false;
+    }
     const int Hp = c.in.h + 2, Wp = c.in.w + 2;
     plan.Hp = Hp;
     plan.Wp = Wp;
     bool ok = true;
-    {
-      cuuint64_t dims[4] = {32, (cuuint64_t)Wp, (cuuint64_t)Hp, (cuuint64_t)c.in.n};
-      cuuint64_t strides[3] = {(cuuint64_t)c.in.pixstride * 2, (cuuint64_t)Wp * c.in.pixstride * 2,
-                               (cuuint64_t)Hp * Wp * c.in.pixstride * 2};
-      cuuint32_t box[4] = {32, (cuuint32_t)plan.WW, (cuuint32_t)plan.WH, 1};
-      ok &= encode(&plan.a[0], 4, c.in.ptr, dims, strides, box, 0);
+    const size_t ps = (size_t)c.in.pixstride;
+    for (int par = 0; par < (st == 2 ? 4 : 1); ++par) {
+      // 5-D view (8 channels, 4 channel chunks, x, y, image); stride 2: parity sub-lattice (py, px)
+      const int py = par >> 1, px = par & 1;
+      void* base = static_cast<__nv_bfloat16*>(c.in.ptr) + (st == 2 ? ((size_t)py * Wp + px) * ps : 0);
+      cuuint64_t dims[5] = {8, 4, (cuuint64_t)(st == 2 ? Wp / 2 : Wp), (cuuint64_t)(st == 2 ? Hp / 2 : Hp),
+                            (cuuint64_t)c.in.n};
+      cuuint64_t strides[4] = {16, (cuuint64_t)st * ps * 2, (cuuint64_t)st * Wp * ps * 2, (cuuint64_t)Hp * Wp * ps * 2};
+      cuuint32_t box[5] = {8, 1, (cuuint32_t)plan.WW, (cuuint32_t)plan.WH, 1};
+      ok &= encode(&plan.a[par], 5, base, dims, strides, box, 0);
     }
     {
       cuuint64_t dims[2] = {320, 64};
@@ -830,6 +836,8 @@ cudaError_t conv_tc_launch(const TcPlan& p, cudaStream_t st) {
   a.WW = p.WW;
   a.WH = p.WH;
   a.win_bytes = p.win_bytes;
+  a.plane = p.plane;
+  a.plane_tx = p.WW * p.WH * 16;
   a.c = p.spec;
   if (p.mode == 2) {
     if (p.bn == 32) return launch_cfg<32, 32, 16, 4>(p, a, st);
@@ -837,10 +845,10 @@ cudaError_t conv_tc_launch(const TcPlan& p, cudaStream_t st) {
     return cudaErrorInvalidValue;
   }
   if (p.mode == 3) {
-    using Cfg = TcCfg<64, 64, 4>;
-    const int smem = 4 * Cfg::A_BYTES + p.kt_total * Cfg::B_BYTES + 2 * p.win_bytes + 2 * Cfg::C_BYTES + 1024 + 512;
+    using Cfg8 = TcCfg<64, 64, 8>;
+    const int smem = 2 * p.win_bytes + p.kt_total * Cfg8::B_BYTES + 2 * Cfg8::C_BYTES + 1024 + 512;
     if (p.bn != 64 || smem > 227 * 1024) return cudaErrorInvalidValue;
-    return launch_cfg<64, 64, 4, 4>(p, a, st, smem);
+    return launch_cfg<64, 64, 8, 1>(p, a, st, smem);
   }
   if (p.bkc == 64) {
     switch (p.bn) {

@@ -35,7 +35,7 @@ struct TcPlan {
   int m_tiles, n_tiles;
   int M_total, Hp, Wp;
   int TW, TH, tiles_x, tiles_y;
-  int WW, WH, win_bytes;         // mode 3: input window of one output patch
+  int WW, WH, win_bytes, plane;  // mode 3: (sub-)window pixels, bytes per buffer, bytes per 8-channel plane
   ConvSpec spec;
 };
 // Fill plan (tensor maps and grid) for a conv whose input is a padded bf16
