@@ -36,6 +36,8 @@ struct TcArgs {
   int stride, WW, WH, win_bytes;   // mode 3: window (or parity sub-window) size in pixels, bytes per buffer
   int plane;                       // mode 3: stride between 8-channel planes (128-byte aligned: TMA destinations)
   int plane_tx;                    // mode 3: bytes one plane load delivers (WW * WH * 16)
+  int nwin;                        // mode 3: window buffers in the ring (2 .. MAX_WIN)
+  int total_units;                 // work units: tiles, or (CTA pairs) pairs of M tiles x N tiles
   ConvSpec c;
 };
 
@@ -48,25 +50,33 @@ __device__ __forceinline__ bool patch_mode(int mode) { return mode == 1 || mode 
 // warp 0: TMA producer; warp 1: MMA issuer + TMEM owner; warps 2..9: epilogue in two
 // groups of four, group g draining TMEM accumulator buffer g (tiles alternate).
 constexpr int EPI_WARPS = 8;
+constexpr int MAX_WIN = 16;   // mode 3: most window buffers in flight
 __host__ __device__ constexpr int tc_threads(int gw) { return 32 * (gw + 1 + EPI_WARPS); }
 
-template <int BN, int BKC, int STAGES>
+// CG = 2: a CTA pair computes a 256 x BN tile with one M=256 MMA; each CTA holds its own
+// 128 rows of A and half (BN/2 rows) of B.
+template <int BN, int BKC, int STAGES, int CG = 1>
 struct TcCfg {
   static constexpr int A_BYTES = 128 * BKC * 2;
-  static constexpr int B_BYTES = BN * BKC * 2;
+  static constexpr int B_BYTES = (BN / CG) * BKC * 2;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr int SWC = BN < 64 ? BN : 64;         // columns staged per epilogue pass
   static constexpr int PASSES = BN / SWC;
   static constexpr int SUB = SWC < 64 ? SWC : 64;       // channels per TMA store box (64 or 128-byte rows)
   static constexpr int NSUB = SWC / SUB;
   static constexpr int SUB_BYTES = 128 * SUB * 2;
-  static constexpr int C_BYTES = NSUB * SUB_BYTES;      // staging tile of one epilogue group
-  static constexpr int SMEM = STAGES * STAGE_BYTES + 2 * C_BYTES + 1024 /*align*/ + 512 /*barriers*/;
+  static constexpr int C_BYTES = NSUB * SUB_BYTES;      // one staging tile (one epilogue pass)
+  static constexpr int SDEPTH = 2;                      // staging tiles per epilogue group
+  static constexpr int BIAS_BYTES = 2 * BN * 4;         // each epilogue group's bias slice (f32)
+  static constexpr int BAR_BYTES = 768;                 // mbarriers + TMEM address slot
+  static constexpr int SMEM =
+      STAGES * STAGE_BYTES + 2 * SDEPTH * C_BYTES + 1024 /*align*/ + BAR_BYTES + BIAS_BYTES;
   static constexpr uint32_t LAYOUT = BKC == 64 ? 2u : 4u;     // SW128 : SW64 (MMA operand tiles)
   static constexpr uint32_t SBO = 8 * BKC * 2;                 // bytes per 8-row group
   static constexpr int NBUF = BN <= 128 ? 4 : 2;               // TMEM accumulator buffers
   static constexpr uint32_t TMEM_COLS = NBUF * BN;
-  static_assert(SMEM <= 227 * 1024, "shared memory budget");
+  static_assert(SMEM <= 227 * 1024 - 64, "shared memory budget (64 bytes left for static shared variables)");
+  static_assert((2 * STAGES + 2 * NBUF + 2 + 2 * MAX_WIN + 1) * 8 + 4 <= BAR_BYTES, "barrier region");
   static_assert(TMEM_COLS >= 32 && TMEM_COLS <= 512, "TMEM budget");
 };
 
@@ -147,30 +157,51 @@ __device__ __forceinline__ TileCoord tile_coord(const TcArgs& a, int tile, int b
 
 __device__ __forceinline__ bool aborted(const int* flag) { return *((volatile const int*)flag) != 0; }
 
-// Persistent CTA (one per SM): tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+// Tile of work unit u for this CTA.  CG = 1: unit = tile.  CG = 2: unit = (M-tile pair, N tile);
+// CTA `rank` of the pair takes M tile 2 * pair + rank.
+template <int CG>
+__device__ __forceinline__ int unit_tile(const TcArgs& a, int u, uint32_t rank) {
+  if (CG == 1) return u;
+  const int n_tile = u % a.n_tiles, m_pair = u / a.n_tiles;
+  return (2 * m_pair + (int)rank) * a.n_tiles + n_tile;
+}
+
+// False for the idle second tile of a CTA pair whose M tile lies past the end.
+__device__ __forceinline__ bool tile_live(const TcArgs& a, const TileCoord& t) {
+  if (!patch_mode(a.mode)) return t.m0 < a.M_total;
+  return t.img < a.c.out.n;
+}
+
+// Persistent CTA (one per SM): work units blockIdx.x, blockIdx.x + gridDim.x, ... (CG = 2:
+// per CTA pair of a 2-CTA cluster, the leader CTA of the pair issuing the M=256 MMAs).
 // Warps 0..GW-1 produce (GW = 1: lane 0 of warp 0 issues TMA; the stem uses GW gather
 // warps), warp GW issues the MMAs and owns TMEM, the last 8 warps run the epilogue.
-template <int BN, int BKC, int STAGES, int GW>
+template <int BN, int BKC, int STAGES, int GW, int CG>
 __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid_constant__ TcPlan plan, const TcArgs a) {
-  using Cfg = TcCfg<BN, BKC, STAGES>;
+  using Cfg = TcCfg<BN, BKC, STAGES, CG>;
+  const uint32_t rank = CG == 2 ? cluster_rank() : 0u;
+  const int u0 = CG == 2 ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+  const int ustep = CG == 2 ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+  const int nunits = CG == 2 ? a.total_units : a.total_tiles;
   extern __shared__ uint8_t smem_raw[];
   __shared__ int s_abort;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   // mode 3: [2 windows][resident B][staging]; otherwise [A ring][B ring][staging]
   uint8_t* sWin = smem;
   uint8_t* sA = smem;
-  uint8_t* sB = a.mode == 3 ? smem + 2 * a.win_bytes : smem + STAGES * Cfg::A_BYTES;
+  uint8_t* sB = a.mode == 3 ? smem + a.nwin * a.win_bytes : smem + STAGES * Cfg::A_BYTES;
   const int b_region = a.mode == 3 ? a.kt_total * Cfg::B_BYTES : STAGES * Cfg::B_BYTES;
   uint8_t* sC = sB + b_region;                           // 2 staging tiles
-  uint64_t* full = reinterpret_cast<uint64_t*>(sC + 2 * Cfg::C_BYTES);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sC + 2 * Cfg::SDEPTH * Cfg::C_BYTES);
   uint64_t* empty = full + STAGES;
   uint64_t* acc_full = empty + STAGES;   // [NBUF] MMA -> epilogue group
   uint64_t* acc_empty = acc_full + Cfg::NBUF;   // [NBUF] epilogue group -> MMA
   uint64_t* res_full = acc_empty + Cfg::NBUF;   // [2] residual tile landed in staging tile g
-  uint64_t* win_full = res_full + 2;     // [2] mode 3: input window landed
-  uint64_t* win_empty = win_full + 2;    // [2] mode 3: window consumed by the gather warps
-  uint64_t* b_full = win_empty + 2;      // mode 3: resident weights landed
+  uint64_t* win_full = res_full + 2;     // [MAX_WIN] mode 3: input window landed
+  uint64_t* win_empty = win_full + MAX_WIN;   // [MAX_WIN] mode 3: window consumed by the MMAs
+  uint64_t* b_full = win_empty + MAX_WIN;     // mode 3: resident weights landed
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(b_full + 1);
+  float* const sBiasAll = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(full) + Cfg::BAR_BYTES);   // [2][BN]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const ConvSpec& c = a.c;
@@ -184,10 +215,12 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
     }
     for (int b = 0; b < Cfg::NBUF; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], EPI_WARPS / 2);
+      mbar_init(&acc_empty[b], CG * EPI_WARPS / 2);   // CG = 2: both CTAs' epilogue groups
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&res_full[b], 1);
+    }
+    for (int b = 0; b < MAX_WIN; ++b) {
       mbar_init(&win_full[b], 1);
       mbar_init(&win_empty[b], 1);      // tcgen05.commit after the tile's MMAs
     }
@@ -195,9 +228,15 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
     fence_barrier_init();
     s_abort = 0;
   }
-  if (warp == GW) tmem_alloc(tmem_slot, Cfg::TMEM_COLS);
+  if (warp == GW) {
+    if constexpr (CG == 2)
+      tmem_alloc_pair(tmem_slot, Cfg::TMEM_COLS);
+    else
+      tmem_alloc(tmem_slot, Cfg::TMEM_COLS);
+  }
   tc_fence_before();
   __syncthreads();
+  if constexpr (CG == 2) cluster_sync();   // both CTAs' barriers initialised before any remote signal
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -209,8 +248,9 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
     const __nv_bfloat16* lb = static_cast<const __nv_bfloat16*>(c.in.ptr);
     const int plane = a.Hp * a.Wp;
     uint32_t lt = 0;   // local tile index of this CTA
-    for (int tile = blockIdx.x; tile < a.total_tiles && !aborted(&s_abort); tile += gridDim.x, ++lt) {
+    for (int u = u0; u < nunits && !aborted(&s_abort); u += ustep, ++lt) {
       if ((int)(lt % GW) != warp) continue;
+      const int tile = unit_tile<CG>(a, u, rank);
       const TileCoord tc = tile_coord(a, tile, BN);
       const uint32_t s = lt % STAGES;
       const uint32_t ph = (lt / STAGES) & 1u;
@@ -274,9 +314,10 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
       for (int kb = 0; kb < a.kt_total; ++kb) tma_load_2d(sB + kb * Cfg::B_BYTES, &plan.b, b_full, kb * 64, 0);
       const int npar = a.stride == 2 ? 4 : 1;
       uint32_t lt = 0;
-      for (int tile = blockIdx.x; tile < a.total_tiles && !aborted(&s_abort); tile += gridDim.x, ++lt) {
-        const uint32_t wb = lt & 1u;
-        if (lt >= 2 && !mbar_wait(&win_empty[wb], ((lt >> 1) - 1) & 1u)) {
+      for (int u = u0; u < nunits && !aborted(&s_abort); u += ustep, ++lt) {
+        const int tile = unit_tile<CG>(a, u, rank);
+        const uint32_t wb = lt % (uint32_t)a.nwin;
+        if (lt >= (uint32_t)a.nwin && !mbar_wait(&win_empty[wb], ((lt / (uint32_t)a.nwin) - 1) & 1u)) {
           flag_error(c.err, KERR_TIMEOUT);
           atomicExch(&s_abort, 1);
           break;
@@ -301,7 +342,9 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
         if (a.mode == 1 || i == 0) tma_prefetch(&plan.a[i]);
       tma_prefetch(&plan.b);
       uint32_t it = 0;
-      for (int tile = blockIdx.x; tile < a.total_tiles && !aborted(&s_abort); tile += gridDim.x) {
+      const uint32_t full_leader0 = CG == 2 ? mapa_rank(smem_u32(&full[0]), 0) : 0u;
+      for (int u = u0; u < nunits && !aborted(&s_abort); u += ustep) {
+        const int tile = unit_tile<CG>(a, u, rank);
         const TileCoord tc = tile_coord(a, tile, BN);
         for (int kt = 0; kt < a.kt_total; ++kt, ++it) {
           const uint32_t s = it % STAGES;
@@ -313,25 +356,39 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
           }
           const int tap = kt / a.cin_blocks, cb = kt % a.cin_blocks;
           const int ky = tap / a.k, kx = tap % a.k;
-          mbar_expect_tx(&full[s], Cfg::STAGE_BYTES);
           uint8_t* dA = sA + s * Cfg::A_BYTES;
-          if (a.mode == 0) {
-            const int shift = a.k == 3 ? (ky - 1) * a.Wp + (kx - 1) : 0;
-            tma_load_2d(dA, &plan.a[0], &full[s], cb * BKC, tc.m0 + shift);
+          if constexpr (CG == 2) {
+            // both CTAs' bytes are counted on the leader's full[s]
+            const uint32_t bar = full_leader0 + s * 8u;
+            if (rank == 0) mbar_expect_tx(&full[s], 2 * Cfg::STAGE_BYTES);
+            if (a.mode == 0) {
+              const int shift = a.k == 3 ? (ky - 1) * a.Wp + (kx - 1) : 0;
+              tma_load_2d_pair(dA, &plan.a[0], bar, cb * BKC, tc.m0 + shift);
+            } else {
+              tma_load_4d_pair(dA, &plan.a[(ky & 1) * 2 + (kx & 1)], bar, cb * BKC, tc.ox0 + (kx >> 1),
+                               tc.oy0 + (ky >> 1), tc.img);
+            }
+            tma_load_2d_pair(sB + s * Cfg::B_BYTES, &plan.b, bar, kt * BKC, tc.n0 + (int)rank * (BN / 2));
           } else {
-            tma_load_4d(dA, &plan.a[(ky & 1) * 2 + (kx & 1)], &full[s], cb * BKC, tc.ox0 + (kx >> 1),
-                        tc.oy0 + (ky >> 1), tc.img);
+            mbar_expect_tx(&full[s], Cfg::STAGE_BYTES);
+            if (a.mode == 0) {
+              const int shift = a.k == 3 ? (ky - 1) * a.Wp + (kx - 1) : 0;
+              tma_load_2d(dA, &plan.a[0], &full[s], cb * BKC, tc.m0 + shift);
+            } else {
+              tma_load_4d(dA, &plan.a[(ky & 1) * 2 + (kx & 1)], &full[s], cb * BKC, tc.ox0 + (kx >> 1),
+                          tc.oy0 + (ky >> 1), tc.img);
+            }
+            tma_load_2d(sB + s * Cfg::B_BYTES, &plan.b, &full[s], kt * BKC, tc.n0);
           }
-          tma_load_2d(sB + s * Cfg::B_BYTES, &plan.b, &full[s], kt * BKC, tc.n0);
         }
       }
     }
   } else if (warp == GW) {
-    if (lane == 0) {
-      // ---------------- MMA issuer
-      constexpr uint32_t idesc = idesc_bf16(128, BN);
+    if (lane == 0 && rank == 0) {
+      // ---------------- MMA issuer (CG = 2: the leader CTA, for both CTAs of the pair)
+      constexpr uint32_t idesc = idesc_bf16(128 * CG, BN);
       uint32_t it = 0, local = 0;
-      for (int tile = blockIdx.x; tile < a.total_tiles; tile += gridDim.x, ++local) {
+      for (int u = u0; u < nunits; u += ustep, ++local) {
         const uint32_t buf = local % Cfg::NBUF, use = local / Cfg::NBUF;
         if (local >= (uint32_t)Cfg::NBUF && !mbar_wait(&acc_empty[buf], (use - 1) & 1u)) {
           flag_error(c.err, KERR_TIMEOUT);
@@ -345,9 +402,9 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
         }
         tc_fence_after();
         const uint32_t d = tmem + buf * BN;
-        if (a.mode == 3) {
-          const uint32_t wb = local & 1u;
-          if (!mbar_wait(&win_full[wb], (local >> 1) & 1u)) {
+        if constexpr (CG == 1) if (a.mode == 3) {
+          const uint32_t wb = local % (uint32_t)a.nwin;
+          if (!mbar_wait(&win_full[wb], (local / (uint32_t)a.nwin) & 1u)) {
             flag_error(c.err, KERR_TIMEOUT);
             atomicExch(&s_abort, 1);
             break;
@@ -391,11 +448,20 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
           for (int kk = 0; kk < BKC / 16; ++kk) {
             const uint64_t ad = smem_desc(a_base + kk * 32, Cfg::SBO, Cfg::LAYOUT);
             const uint64_t bd = smem_desc(b_base + kk * 32, Cfg::SBO, Cfg::LAYOUT);
-            umma_bf16(d, ad, bd, idesc, (kt | kk) != 0 ? 1u : 0u);
+            if constexpr (CG == 2)
+              umma_bf16_pair(d, ad, bd, idesc, (kt | kk) != 0 ? 1u : 0u);
+            else
+              umma_bf16(d, ad, bd, idesc, (kt | kk) != 0 ? 1u : 0u);
           }
-          umma_commit(&empty[s]);
+          if constexpr (CG == 2)
+            umma_commit_pair(&empty[s], 3);      // the stage is free in both CTAs
+          else
+            umma_commit(&empty[s]);
         }
-        umma_commit(&acc_full[buf]);
+        if constexpr (CG == 2)
+          umma_commit_pair(&acc_full[buf], 3);
+        else
+          umma_commit(&acc_full[buf]);
         if (!ok) break;
       }
     }
@@ -407,10 +473,20 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
     const int row = quarter * 32 + lane;
     const bool elected = (ew & 3) == 0 && lane == 0;
     const int bar_id = 1 + g;
-    uint8_t* stg = sC + g * Cfg::C_BYTES;
-    uint32_t res_uses = 0, local = 0;
-    for (int tile = blockIdx.x; tile < a.total_tiles; tile += gridDim.x, ++local) {
+    // the group's SDEPTH staging tiles take the passes in turn, so a pass only waits for the
+    // store issued SDEPTH passes earlier to have read its tile
+    uint8_t* const stg_base = sC + g * Cfg::SDEPTH * Cfg::C_BYTES;
+    uint8_t* stg = stg_base;
+    uint32_t res_uses = 0, local = 0, npass = 0;
+    // bias of the group's current N tile, in shared memory (refilled when the N tile changes)
+    float* const sBias = sBiasAll + g * BN;
+    const int gtid = (ew & 3) * 32 + lane;
+    int bias_n0 = -1;
+    // CG = 2: the accumulator buffer is released on the leader's barrier
+    const uint32_t acc_empty_leader0 = CG == 2 ? mapa_rank(smem_u32(&acc_empty[0]), 0) : 0u;
+    for (int u = u0; u < nunits; u += ustep, ++local) {
       if ((local & 1u) != (uint32_t)g) continue;
+      const int tile = unit_tile<CG>(a, u, rank);
       const uint32_t buf = local % Cfg::NBUF, use = local / Cfg::NBUF;
       bool ok = mbar_wait(&acc_full[buf], use & 1u);
       if (!ok) {
@@ -420,6 +496,12 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
       ok = bar_and(ok, bar_id, 128);        // the group's four warps take the same path
       tc_fence_after();
       const TileCoord tc = tile_coord(a, tile, BN);
+      if (tc.n0 != bias_n0) {
+        // the group finished reading the previous slice before the last pass's barrier
+        for (int i = gtid; i < BN; i += 128) sBias[i] = c.bias[tc.n0 + i];
+        named_bar(bar_id, 128);
+        bias_n0 = tc.n0;
+      }
       int n = 0, y = 0, x = 0;
       bool valid;
       if (!patch_mode(a.mode)) {
@@ -434,15 +516,17 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
         n = tc.img;
         y = tc.oy0 + row / a.TW;
         x = tc.ox0 + row % a.TW;
-        valid = y < c.Ho && x < c.Wo;
+        valid = y < c.Ho && x < c.Wo && tile_live(a, tc);
       }
       if (a.tma_out) {
         // staged: TMEM -> (bias, leaky, + residual) -> bf16 staging tile -> TMA store.
         // Rows on the halo are written as zeros, which keeps the halo zero.
         for (int p = 0; p < Cfg::PASSES; ++p) {
-          const bool use_res = a.tma_res && ok;
+          stg = stg_base + (npass++ % Cfg::SDEPTH) * Cfg::C_BYTES;
+          const bool live = tile_live(a, tc);
+          const bool use_res = a.tma_res && ok && live;
           if (elected) {
-            bulk_wait_read0();              // the previous store has finished reading the staging tile
+            bulk_wait_read<Cfg::SDEPTH - 1>();   // the store that last used this staging tile has read it
             if (use_res) {
               mbar_expect_tx(&res_full[g], Cfg::C_BYTES);
               for (int j = 0; j < Cfg::NSUB; ++j) {
@@ -467,7 +551,7 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
             uint32_t r[32];
             tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + buf * BN + (uint32_t)(p * Cfg::SWC + c0), r);
             tmem_ld_wait();
-            const float4* b4 = reinterpret_cast<const float4*>(c.bias + tc.n0 + p * Cfg::SWC + c0);
+            const float4* b4 = reinterpret_cast<const float4*>(sBias + p * Cfg::SWC + c0);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
               const int col = c0 + 8 * u;                       // column inside this pass
@@ -503,11 +587,16 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
           if (p == Cfg::PASSES - 1) {
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&acc_empty[buf]);   // accumulator buffer free for the MMA
+            if (lane == 0) {                   // accumulator buffer free for the MMA
+              if (CG == 2)
+                mbar_arrive_cluster(acc_empty_leader0 + buf * 8u);
+              else
+                mbar_arrive(&acc_empty[buf]);
+            }
           }
           fence_proxy_async();               // staging writes visible to the TMA store
           named_bar(bar_id, 128);
-          if (elected && ok && !aborted(&s_abort)) {
+          if (elected && ok && live && !aborted(&s_abort)) {
             for (int j = 0; j < Cfg::NSUB; ++j) {
               const int ch = tc.n0 + p * Cfg::SWC + j * Cfg::SUB;
               if (!patch_mode(a.mode))
@@ -532,7 +621,7 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
             float v[32];
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
-              const float t = __uint_as_float(r[j]) + c.bias[ch0 + j];
+              const float t = __uint_as_float(r[j]) + sBias[c0 + j];
               v[j] = c.act ? leaky01(t) : t;
             }
             if (c.res.ptr) {
@@ -547,7 +636,12 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&acc_empty[buf]);
+        if (lane == 0) {
+          if (CG == 2)
+            mbar_arrive_cluster(acc_empty_leader0 + buf * 8u);
+          else
+            mbar_arrive(&acc_empty[buf]);
+        }
       }
       if (!ok) break;
     }
@@ -556,7 +650,13 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
   __syncwarp();
   tc_fence_before();
   __syncthreads();
-  if (warp == GW) tmem_dealloc(tmem, Cfg::TMEM_COLS);
+  if constexpr (CG == 2) cluster_sync();   // no CTA leaves while its peer may still signal it
+  if (warp == GW) {
+    if constexpr (CG == 2)
+      tmem_dealloc_pair(tmem, Cfg::TMEM_COLS);
+    else
+      tmem_dealloc(tmem, Cfg::TMEM_COLS);
+  }
 }
 
 // ----------------------------------------------------------------------------- host side
@@ -600,22 +700,50 @@ int sm_count() {
   return n;
 }
 
-template <int BN, int BKC, int STAGES, int GW = 1>
+template <int BN, int BKC, int STAGES, int GW = 1, int CG = 1>
 cudaError_t launch_cfg(const TcPlan& p, const TcArgs& a, cudaStream_t st, int smem = 0) {
-  using Cfg = TcCfg<BN, BKC, STAGES>;
+  using Cfg = TcCfg<BN, BKC, STAGES, CG>;
+  auto kernel = conv_tc_kernel<BN, BKC, STAGES, GW, CG>;
   if (!smem) smem = Cfg::SMEM;
   static int attr_set = 0;
   if (attr_set < smem) {
-    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<BN, BKC, STAGES, GW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         smem);
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     attr_set = smem;
   }
-  const int tiles = p.m_tiles * p.n_tiles;
-  const int grid = tiles < sm_count() ? tiles : sm_count();
+  if (CG == 1) {
+    const int tiles = p.m_tiles * p.n_tiles;
+    const int grid = tiles < sm_count() ? tiles : sm_count();
+    jde_count_launch();
+    kernel<<<grid, tc_threads(GW), smem, st>>>(p, a);
+    return cudaGetLastError();
+  }
+  // CTA pairs: 2-CTA clusters, as many as can be resident at once (persistent)
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(tc_threads(GW));
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  static int max_clusters = 0;
+  if (!max_clusters) {
+    cfg.gridDim = dim3(2 * (sm_count() / 2));
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kernel, &cfg) != cudaSuccess || n < 1) {
+      cudaGetLastError();
+      n = sm_count() / 2;
+    }
+    max_clusters = n;
+  }
+  const int clusters = a.total_units < max_clusters ? a.total_units : max_clusters;
+  cfg.gridDim = dim3(2 * clusters);
   jde_count_launch();
-  conv_tc_kernel<BN, BKC, STAGES, GW><<<grid, tc_threads(GW), smem, st>>>(p, a);
-  return cudaGetLastError();
+  return cudaLaunchKernelEx(&cfg, kernel, p, a);
 }
 
 }  // namespace
@@ -679,6 +807,17 @@ bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const __nv_bfloat16* w, int c
     // every plane is a TMA destination: its shared-memory address must be 128-byte aligned
     plan.plane = (plan.WW * plan.WH * 16 + 127) / 128 * 128;
     plan.win_bytes = ((st == 1 ? 4 : 16) * plan.plane + 1023) / 1024 * 1024;
+    {
+      // as many window buffers as shared memory holds next to the resident weights and the two
+      // staging tiles (at most MAX_WIN)
+      const int fixed = plan.kt_total * 64 * 64 * 2 + 2 * 2 * 128 * 64 * 2 + 1024 + 768 + 2 * 64 * 4;
+      plan.nwin = (227 * 1024 - 64 - fixed) / plan.win_bytes;
+      if (plan.nwin > MAX_WIN) plan.nwin = MAX_WIN;
+    }
+    if (plan.nwin < 2) {
+      snprintf(msg, msg_len, "window ring does not fit in shared memory");
+      return false;
+    }
     if (plan.plane % 128 || plan.win_bytes % 1024) {
       snprintf(msg, msg_len, "window planes not 128-byte aligned");
       return false;
@@ -776,10 +915,12 @@ bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const __nv_bfloat16* w, int c
         ok &= encode(&plan.a[py * 2 + px], 4, pb, dims, strides, box, bkc);
       }
   }
+  // 256-wide tiles run on CTA pairs (M = 256 per MMA, each CTA loads half of B)
+  plan.cg = bn == 256 && bkc == 64 ? 2 : 1;
   {
     cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)cout_pad};
     cuuint64_t strides[1] = {(cuuint64_t)K * 2};
-    cuuint32_t box[2] = {(cuuint32_t)bkc, (cuuint32_t)bn};
+    cuuint32_t box[2] = {(cuuint32_t)bkc, (cuuint32_t)(bn / plan.cg)};
     ok &= encode(&plan.b, 2, const_cast<__nv_bfloat16*>(w), dims, strides, box, bkc);
   }
   // TMA-stored epilogue: bf16 padded outputs written in place (no upsample), channel
@@ -830,39 +971,44 @@ cudaError_t conv_tc_launch(const TcPlan& p, cudaStream_t st) {
   a.tiles_y = p.tiles_y;
   a.n_tiles = p.n_tiles;
   a.total_tiles = p.m_tiles * p.n_tiles;
+  a.total_units = p.cg == 2 ? (p.m_tiles + 1) / 2 * p.n_tiles : a.total_tiles;
   a.tma_out = p.tma_out;
   a.tma_res = p.tma_res;
   a.stride = p.spec.stride;
   a.WW = p.WW;
   a.WH = p.WH;
   a.win_bytes = p.win_bytes;
+  a.nwin = p.nwin;
   a.plane = p.plane;
   a.plane_tx = p.WW * p.WH * 16;
   a.c = p.spec;
   if (p.mode == 2) {
     if (p.bn == 32) return launch_cfg<32, 32, 16, 4>(p, a, st);
-    if (p.bn == 64) return launch_cfg<64, 32, 16, 4>(p, a, st);
+    if (p.bn == 64) return launch_cfg<64, 32, 12, 4>(p, a, st);
     return cudaErrorInvalidValue;
   }
   if (p.mode == 3) {
-    using Cfg8 = TcCfg<64, 64, 8>;
-    const int smem = 2 * p.win_bytes + p.kt_total * Cfg8::B_BYTES + 2 * Cfg8::C_BYTES + 1024 + 512;
-    if (p.bn != 64 || smem > 227 * 1024) return cudaErrorInvalidValue;
-    return launch_cfg<64, 64, 8, 1>(p, a, st, smem);
+    using Cfg8 = TcCfg<64, 64, 6>;
+    const int smem = p.nwin * p.win_bytes + p.kt_total * Cfg8::B_BYTES + 2 * Cfg8::SDEPTH * Cfg8::C_BYTES + 1024 +
+                     Cfg8::BAR_BYTES + Cfg8::BIAS_BYTES;
+    if (p.bn != 64 || smem > 227 * 1024 - 64) return cudaErrorInvalidValue;
+    return launch_cfg<64, 64, 6, 1>(p, a, st, smem);
   }
   if (p.bkc == 64) {
     switch (p.bn) {
-      case 32: return launch_cfg<32, 64, 10>(p, a, st);
-      case 64: return launch_cfg<64, 64, 8>(p, a, st);
-      case 128: return launch_cfg<128, 64, 6>(p, a, st);
-      case 256: return launch_cfg<256, 64, 4>(p, a, st);
+      case 32: return launch_cfg<32, 64, 9>(p, a, st);
+      case 64: return launch_cfg<64, 64, 6>(p, a, st);
+      case 128: return launch_cfg<128, 64, 5>(p, a, st);
+      case 256:
+        if (p.cg == 2) return launch_cfg<256, 64, 4, 1, 2>(p, a, st);
+        return launch_cfg<256, 64, 3>(p, a, st);
     }
   } else {
     switch (p.bn) {
       case 32: return launch_cfg<32, 32, 16>(p, a, st);
-      case 64: return launch_cfg<64, 32, 16>(p, a, st);
-      case 128: return launch_cfg<128, 32, 12>(p, a, st);
-      case 256: return launch_cfg<256, 32, 8>(p, a, st);
+      case 64: return launch_cfg<64, 32, 12>(p, a, st);
+      case 128: return launch_cfg<128, 32, 10>(p, a, st);
+      case 256: return launch_cfg<256, 32, 6>(p, a, st);
     }
   }
   return cudaErrorInvalidValue;

@@ -36,6 +36,8 @@ struct TcPlan {
   int M_total, Hp, Wp;
   int TW, TH, tiles_x, tiles_y;
   int WW, WH, win_bytes, plane;  // mode 3: (sub-)window pixels, bytes per buffer, bytes per 8-channel plane
+  int nwin;                      // mode 3: window buffers in the ring
+  int cg;                        // 2: 256-wide tiles on CTA pairs (cta_group::2), else 1
   ConvSpec spec;
 };
 // Fill plan (tensor maps and grid) for a conv whose input is a padded bf16
