@@ -48,6 +48,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp32", action="store_true")
     p.add_argument("--soak", type=int, default=40, help="untimed steps while the clock sampler starts")
+    p.add_argument("--serve-seconds", type=float, default=20.0,
+                   help="serving run: seconds of Poisson arrivals measured after a 2 s warm-up (0: skip)")
+    p.add_argument("--serve-budget-gb", type=float, default=64.0, help="serving run: device memory budget")
     return p.parse_args()
 
 
@@ -184,6 +187,40 @@ def build_heads_device(torch, clips, t, device):
                 xs = torch.tensor([e[2] for e in ee], device=device)
                 embs[s][b][ys, xs] = torch.from_numpy(np.stack([e[3] for e in ee])).to(device)
     return dets + embs
+
+
+def run_serving(torch, jde, dev, blob, seconds, budget_gb, n_streams=16, warm_s=2.0):
+    """Serving: 16 streams, Poisson arrivals at 30 fps each, input 1088x608 / 864x480 / 576x320 by stream,
+    20 + 80u planted objects per stream; continuous batching (paper_2011_03910_gb300.serve)."""
+    import synth
+    from paper_2011_03910_gb300 import serve
+    sizes = [(1088, 608), (864, 480), (576, 320)]
+    g = np.random.Generator(np.random.PCG64(4))
+    specs = [serve.StreamSpec(i, *sizes[i % 3], fps=30.0, n_objects=int(20 + 80 * g.uniform()), seed=4000 + i)
+             for i in range(n_streams)]
+    srv = serve.Server(jde, torch, dev, blob, budget_bytes=int(budget_gb * 1e9))
+    total_s = seconds + warm_s
+    for sp in specs:
+        fr = torch.from_numpy(synth.frames_uniform(5000 + sp.stream_id, 4, SRC_H, SRC_W)).to(dev)
+        srv.open_stream(sp, [fr[k] for k in range(4)])
+    reqs = serve.poisson_arrivals([sp for sp in specs if sp.stream_id in srv.group_of], total_s, seed=4)
+    l0 = jde.jde_launch_count()
+    stats = srv.run(reqs, warm_s=warm_s)
+    stats.update({"streams": n_streams, "admitted": len(srv.group_of), "refused": list(srv.refused),
+                  "offered_fps": 30.0 * len(srv.group_of), "seconds": seconds, "warmup_s": warm_s,
+                  "inputs": {f"{w}x{h}": sum(1 for sp in specs if (sp.in_w, sp.in_h) == (w, h)) for w, h in sizes},
+                  "device_bytes": srv.device_bytes(), "budget_bytes": srv.ledger.budget,
+                  "gpu_launches": int(jde.jde_launch_count() - l0),
+                  "what": "latency per frame: device time its tracker step finished minus its Poisson arrival; "
+                          "fps = frames served / time from the end of warm-up to the last frame's completion"})
+    # capacity: the same streams with every frame released at once (batches fill to max_batch per size)
+    sat = [serve.Request(0.0, sp.stream_id, k) for k in range(60) for sp in specs if sp.stream_id in srv.group_of]
+    st2 = srv.run(sat, realtime=False)
+    stats["saturated_fps"] = st2["fps"]
+    for sp in specs:
+        if sp.stream_id in srv.group_of:
+            srv.close_stream(sp.stream_id)
+    return stats
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -484,6 +521,10 @@ def main():
         fp32 = {"fps": 1000.0 / ms32, "ms_per_frame": ms32, "steps": n32, "batch": 1, "graph": False}
         jde.jde_destroy(h32)
 
+    serving = None
+    if args.serve_seconds > 0 and rank == 0:
+        serving = run_serving(torch, jde, dev, blob, args.serve_seconds, args.serve_budget_gb)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         ts = cpu_oracle_frames(1)
@@ -506,6 +547,7 @@ def main():
             "stages_ms_per_step": {"forward": fwd_ms / K, "convs": conv_ms / K},
             "fp32_plain_batch1": fp32,
             "batch_sweep": sweep,
+            "serving": serving,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -189,6 +189,16 @@ jde_status jde_get_tensor(jde_handle* h, int id, void* dst, size_t dst_bytes, in
  * bit 1: capacity overflow); reading it synchronises `stream` and clears it. */
 jde_status jde_kernel_errors(jde_handle* h, int* word, void* stream);
 
+/* Device memory the handle holds now (weights, activation buffers of every
+ * input size used so far, post-processing and tracker state, staging), in bytes. */
+jde_status jde_device_bytes(jde_handle* h, size_t* out);
+
+/* Device memory a handle created with *cfg holds once it has run batches of
+ * cfg->max_batch frames at in_w x in_h with device-resident frames (host-fed
+ * frames add max_batch * src_w * src_h * 3 bytes of staging).  For admission
+ * against a memory budget before jde_create; allocates nothing. */
+jde_status jde_estimate_device_bytes(const jde_config* cfg, int in_w, int in_h, size_t* out);
+
 /* Number of kernels libjde has launched in this process (all handles), for launch accounting. */
 unsigned long long jde_launch_count(void);
 

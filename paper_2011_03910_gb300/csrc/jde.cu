@@ -148,6 +148,7 @@ struct jde_handle {
   cudaEvent_t prof[3] = {nullptr, nullptr, nullptr};
   int head_set = 0;   // head-tensor set the next forward writes
   int cur_set = 0;    // set written by the last forward
+  size_t weight_bytes = 0;   // device bytes of the packed weights
 };
 
 namespace {
@@ -410,6 +411,31 @@ __global__ void pack_kernel(const float* W, const float* gamma, const float* bet
   }
 }
 
+// Device bytes of one layer's packed weights (bias + tensor-core or SIMT layout).
+size_t layer_weight_bytes(const LayerDef& L, bool bf16, int l) {
+  const int K = L.k * L.k * L.cin;
+  const int cout_pad64 = align_up(L.cout, 64);
+  const int bn = conv_tc_pick_bn(L.cout);
+  const int cout_pad_tc = align_up(L.cout, bn);
+  const int k_tc = l == 0 ? 32 : (L.cin == 32 && L.k == 3 ? 320 : K);
+  const int bias_len = (cout_pad64 > cout_pad_tc ? cout_pad64 : cout_pad_tc) + 256;
+  size_t b = sizeof(float) * (size_t)bias_len;
+  b += bf16 ? sizeof(__nv_bfloat16) * (size_t)cout_pad_tc * k_tc : sizeof(float) * (size_t)align_up(K, 16) * cout_pad64;
+  return b;
+}
+
+// Device bytes of the post-processing scratch for n frames.
+size_t post_bytes(int n, int anchors, int kmax) {
+  const size_t N = (size_t)n, K = (size_t)kmax;
+  return N * anchors * sizeof(uint64_t) + N * sizeof(int) + N * K * sizeof(uint64_t) + N * sizeof(int) +
+         N * K * sizeof(float4) + 2 * N * K * sizeof(float) + N * K * (K / 64) * sizeof(unsigned long long) +
+         N * K * sizeof(int) + N * sizeof(int);
+}
+
+int anchors_for(int in_w, int in_h) {
+  return 4 * ((in_w / 32) * (in_h / 32) + (in_w / 16) * (in_h / 16) + (in_w / 8) * (in_h / 8));
+}
+
 jde_status load_weights(jde_handle* h, const void* blob, size_t nbytes) {
   const auto& L = layers();
   const uint8_t* p = static_cast<const uint8_t*>(blob);
@@ -459,6 +485,7 @@ jde_status load_weights(jde_handle* h, const void* blob, size_t nbytes) {
       return fail(h, JDE_ERR_OOM, "weights of layer %zu", l);
     }
     cudaMemset(lw.bias, 0, sizeof(float) * bias_len);
+    h->weight_bytes += layer_weight_bytes(L[l], bf16, (int)l);
     const float* base = reinterpret_cast<const float*>(static_cast<uint8_t*>(dblob) + offs[l]);
     const size_t nw = (size_t)L[l].cout * L[l].cin * L[l].k * L[l].k;
     const float* W = base;
@@ -502,8 +529,7 @@ jde_status ensure_post(jde_handle* h, int n) {
   for (void* q : ptrs)
     if (q) cudaFree(q);
   const int kmax = h->cfg.max_cand;
-  const int anchors = 4 * ((h->cfg.max_in_w / 32) * (h->cfg.max_in_h / 32) + (h->cfg.max_in_w / 16) * (h->cfg.max_in_h / 16) +
-                           (h->cfg.max_in_w / 8) * (h->cfg.max_in_h / 8));
+  const int anchors = anchors_for(h->cfg.max_in_w, h->cfg.max_in_h);
   b.cand_cap = anchors;
   b.kmax = kmax;
   bool ok = dmalloc((void**)&b.cand_keys, sizeof(uint64_t) * (size_t)n * anchors) &&
@@ -825,6 +851,44 @@ jde_status jde_get_tensor(jde_handle* h, int id, void* dst, size_t dst_bytes, in
   (jde_count_launch(), gather_view_kernel<<<(unsigned)((total + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(v, dst, el));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(h, JDE_ERR_CUDA, "gather: %s", cudaGetErrorString(e));
+  return JDE_OK;
+}
+
+jde_status jde_device_bytes(jde_handle* h, size_t* out) {
+  if (!h || !out) return fail(h, JDE_ERR_INVALID_ARG, "jde_device_bytes: NULL argument");
+  size_t b = h->weight_bytes + sizeof(int) + sizeof(LbAxis) * (size_t)(h->cfg.max_in_w + h->cfg.max_in_h);
+  for (const auto& kv : h->res)
+    for (size_t t : kv.second.bytes) b += t;
+  if (h->pb.cand_keys) b += post_bytes(h->pb_n, h->pb.cand_cap, h->pb.kmax);
+  b += h->frames_cap;
+  if (h->rows_stage) b += h->rows_stage_cap * sizeof(float) + sizeof(int32_t) * (size_t)h->cfg.max_batch +
+                         h->rows_stage_cap / 518 * sizeof(int32_t);
+  b += track_bytes(h->cfg);
+  *out = b;
+  return JDE_OK;
+}
+
+jde_status jde_estimate_device_bytes(const jde_config* cfg, int in_w, int in_h, size_t* out) {
+  if (!cfg || !out || in_w < 32 || in_h < 32 || in_w % 32 || in_h % 32 || in_w > cfg->max_in_w ||
+      in_h > cfg->max_in_h || cfg->max_batch < 1)
+    return fail(nullptr, JDE_ERR_INVALID_ARG, "jde_estimate_device_bytes: bad arguments");
+  jde_handle tmp;
+  tmp.cfg = *cfg;
+  tmp.io = build_io();
+  const bool bf16 = cfg->precision == JDE_BF16;
+  const auto& L = layers();
+  size_t b = sizeof(int) + sizeof(LbAxis) * (size_t)(cfg->max_in_w + cfg->max_in_h);
+  for (size_t l = 0; l < L.size(); ++l) b += layer_weight_bytes(L[l], bf16, (int)l);
+  std::vector<TensorDesc> td;
+  tensor_desc_table(&tmp, in_w, in_h, td);
+  for (int t = 0; t < T_COUNT; ++t) {
+    if (td[t].alias >= 0) continue;
+    const bool head = t < JDE_NUM_LAYERS && tmp.io[t].head >= 0;
+    b += tensor_bytes(td[t], cfg->max_batch) * (head ? 2 : 1);
+  }
+  b += post_bytes(cfg->max_batch, anchors_for(cfg->max_in_w, cfg->max_in_h), cfg->max_cand);
+  b += track_bytes(*cfg);
+  *out = b;
   return JDE_OK;
 }
 

@@ -545,6 +545,15 @@ bool dalloc(void** p, size_t bytes) {
 
 }  // namespace
 
+size_t track_bytes(const jde_config& cfg) {
+  const size_t S = cfg.max_streams, T = cfg.max_tracks, D = cfg.max_track_dets;
+  const size_t B = cfg.max_batch < MAXB ? cfg.max_batch : MAXB;
+  return sizeof(int) * S + sizeof(long long) * S + 2 * sizeof(int) * S * T + sizeof(int) * S +
+         sizeof(long long) * S * T + 2 * sizeof(int) * S * T + sizeof(double) * S * T * (8 + 64) +
+         sizeof(float) * S * T * 512 + sizeof(int) * S * T + sizeof(double) * B * T * (16 + 4) +
+         sizeof(double) * B * T * D + sizeof(int) * B;
+}
+
 int track_alloc(TrackState& t, const jde_config& cfg) {
   t.max_streams = cfg.max_streams;
   t.max_tracks = cfg.max_tracks;

@@ -40,6 +40,7 @@ struct TrackState {
 };
 
 int track_alloc(TrackState& t, const jde_config& cfg);
+size_t track_bytes(const jde_config& cfg);   // device bytes track_alloc takes
 void track_free(TrackState& t);
 int track_reset(TrackState& t, int stream_id, cudaStream_t st);
 // Returns a jde_status value; msg receives a reason on failure.

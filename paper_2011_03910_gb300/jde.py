@@ -65,6 +65,8 @@ _sig = {
     "jde_stream_reset": (C.c_int, [_P, C.c_int, _P]),
     "jde_get_tensor": (C.c_int, [_P, C.c_int, _P, C.c_size_t, C.POINTER(C.c_int), C.POINTER(C.c_int), _P]),
     "jde_kernel_errors": (C.c_int, [_P, C.POINTER(C.c_int), _P]),
+    "jde_device_bytes": (C.c_int, [_P, C.POINTER(C.c_size_t)]),
+    "jde_estimate_device_bytes": (C.c_int, [C.POINTER(jde_config), C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
     "jde_launch_count": (C.c_ulonglong, []),
     "jde_set_profile_events": (C.c_int, [_P, _P, _P, _P]),
     "jde_postprocess_noalloc": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float, C.c_float,
@@ -192,6 +194,18 @@ def jde_kernel_errors(h, stream=None) -> int:
     w = C.c_int()
     _check(h, lib.jde_kernel_errors(h, C.byref(w), stream_ptr(stream)))
     return w.value
+
+
+def jde_device_bytes(h) -> int:
+    out = C.c_size_t()
+    _check(h, lib.jde_device_bytes(h, C.byref(out)))
+    return int(out.value)
+
+
+def jde_estimate_device_bytes(cfg: jde_config, in_w: int, in_h: int) -> int:
+    out = C.c_size_t()
+    _check(None, lib.jde_estimate_device_bytes(C.byref(cfg), in_w, in_h, C.byref(out)))
+    return int(out.value)
 
 
 def jde_launch_count() -> int:

@@ -1,0 +1,72 @@
+"""Host logic of the serving loop (no GPU): arrivals, admission ledger, device-memory estimates."""
+import numpy as np
+import pytest
+
+from paper_2011_03910_gb300 import serve
+
+
+def specs(n=16):
+    sizes = [(1088, 608), (864, 480), (576, 320)]
+    return [serve.StreamSpec(i, *sizes[i % 3], fps=30.0) for i in range(n)]
+
+
+def test_poisson_arrivals_are_seeded_sorted_and_at_the_stream_rate():
+    a = serve.poisson_arrivals(specs(), 20.0, seed=4)
+    b = serve.poisson_arrivals(specs(), 20.0, seed=4)
+    assert [(r.t, r.stream_id) for r in a] == [(r.t, r.stream_id) for r in b]
+    assert all(x.t <= y.t for x, y in zip(a, a[1:]))
+    per = np.bincount([r.stream_id for r in a], minlength=16)
+    # 600 expected frames per stream; Poisson count sd ~ 24.5
+    assert np.all(np.abs(per - 600) < 6 * 24.5)
+    # frame numbers of each stream are consecutive from 0
+    for s in range(16):
+        idx = [r.index for r in a if r.stream_id == s]
+        assert idx == list(range(len(idx)))
+    gaps = np.diff([r.t for r in a if r.stream_id == 0])
+    assert abs(gaps.mean() - 1 / 30) < 0.005
+
+
+def test_admission_ledger_charges_once_and_refuses_over_budget():
+    led = serve.AdmissionLedger(10_000)
+    assert led.try_charge("a", 6000)
+    assert led.try_charge("a", 6000)          # already charged: no second charge
+    assert led.used == 6000
+    assert not led.try_charge("b", 4001)
+    assert led.try_charge("c", 4000)
+    assert led.used == 10_000
+    led.credit("a")
+    assert led.used == 4000
+    assert led.try_charge("b", 4001)
+
+
+def test_estimated_device_bytes_scale_with_input_size_and_batch():
+    from paper_2011_03910_gb300 import jde
+    cfg = jde.jde_default_config()
+    cfg.precision = jde.JDE_BF16
+    cfg.max_batch = 16
+    est = [jde.jde_estimate_device_bytes(cfg, w, h) for w, h in [(1088, 608), (864, 480), (576, 320)]]
+    assert est[0] > est[1] > est[2] > 0
+    cfg.max_batch = 8
+    half = jde.jde_estimate_device_bytes(cfg, 1088, 608)
+    assert half < est[0]
+    # the batch-dependent part (activations, post-processing scratch) is most of it
+    assert est[0] - half > 0.4 * (est[0] - 0.131e9)
+    with pytest.raises(jde.JdeError):
+        jde.jde_estimate_device_bytes(cfg, 1100, 608)      # not a multiple of 32
+
+
+def test_budget_admits_groups_in_arrival_order_until_full():
+    """Admission rule of Server.open_stream with the library's own estimates: a group is charged when
+    its first stream arrives; a size whose group does not fit is refused."""
+    from paper_2011_03910_gb300 import jde
+    cfg = jde.jde_default_config()
+    cfg.precision = jde.JDE_BF16
+    cfg.max_batch = 16
+    cost = {}
+    for w, h in [(1088, 608), (864, 480), (576, 320)]:
+        cfg.max_in_w, cfg.max_in_h = w, h
+        cost[(w, h)] = jde.jde_estimate_device_bytes(cfg, w, h) + serve._Group.buffer_bytes(16, w, h, 256, 256)
+    budget = cost[(1088, 608)] + cost[(576, 320)] + 1
+    led = serve.AdmissionLedger(budget)
+    admitted = [led.try_charge((s.in_w, s.in_h), cost[(s.in_w, s.in_h)]) for s in specs(6)]
+    assert admitted == [True, False, True, True, False, True]
