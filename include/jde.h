@@ -49,7 +49,12 @@ typedef enum {
   JDE_ERR_UNSUPPORTED = 9  /* option not built into this library */
 } jde_status;
 
-typedef enum { JDE_FP32 = 0, JDE_BF16 = 1 } jde_precision;
+/* JDE_FP8_E4M3: convolutions from the first stride-2 stage's output on take E4M3 activations
+ * (one scale per stored tensor, amax / 448, set with jde_set_act_amax) and E4M3 weights (one
+ * scale per output channel, max |W'| / 448 of the BN-folded weights, computed at create time),
+ * accumulate in f32 and store E4M3 outputs; the stem and the next three layers run in BF16 and
+ * the heads are written in f32. */
+typedef enum { JDE_FP32 = 0, JDE_BF16 = 1, JDE_FP8_E4M3 = 2 } jde_precision;
 
 /* Track states reported by jde_track_step (Appendix A: active / lost). */
 enum { JDE_TRACK_TRACKED = 1, JDE_TRACK_LOST = 2 };
@@ -180,7 +185,8 @@ jde_status jde_stream_reset(jde_handle* h, int stream_id, void* stream);
 /* Copy an internal tensor to `dst` (device pointer, dst_bytes capacity) for
  * inspection: id 0..77 = output of conv layer id (after its fused epilogue:
  * bias, leaky-ReLU, residual add), 100 = letterboxed input.  dims receives {n, h, w, c} of the unpadded tensor, *dtype
- * 0 = f32, 1 = bf16; the copy is the unpadded tensor in NHWC order.  dst NULL
+ * 0 = f32, 1 = bf16, 2 = E4M3 codes (value = code * amax / 448 of its tensor); the copy is
+ * the unpadded tensor in NHWC order.  dst NULL
  * only reports dims and dtype. */
 jde_status jde_get_tensor(jde_handle* h, int id, void* dst, size_t dst_bytes, int* dims, int* dtype,
                           void* stream);
@@ -188,6 +194,19 @@ jde_status jde_get_tensor(jde_handle* h, int id, void* dst, size_t dst_bytes, in
 /* Device error word accumulated by the kernels (bit 0: bounded wait timed out,
  * bit 1: capacity overflow); reading it synchronises `stream` and clears it. */
 jde_status jde_kernel_errors(jde_handle* h, int* word, void* stream);
+
+/* E4M3 handles: per-layer output amax (n = JDE_NUM_LAYERS values, layer order of the weights
+ * blob, finite and >= 0) from calibration frames, e.g. the elementwise maximum of
+ * jde_act_amax over calibration batches run on a BF16 handle.  The scale of a stored tensor is
+ * amax / 448; a concat buffer takes the larger amax of the two layers writing into it.  Must be
+ * called before the handle's first jde_forward (else that returns JDE_ERR_INVALID_ARG); calling
+ * it again replaces the scales.  Other handles: JDE_ERR_INVALID_ARG. */
+jde_status jde_set_act_amax(jde_handle* h, const float* amax, int n);
+
+/* max |value| of every layer output of the handle's last jde_forward (all its frames), into
+ * amax[JDE_NUM_LAYERS] (host); synchronises `stream`.  Heads and BF16/f32 tensors as stored;
+ * E4M3 tensors as code times scale. */
+jde_status jde_act_amax(jde_handle* h, float* amax, void* stream);
 
 /* Device memory the handle holds now (weights, activation buffers of every
  * input size used so far, post-processing and tracker state, staging), in bytes. */

@@ -119,6 +119,25 @@ def is_head(spec) -> bool:
 
 
 # ----------------------------------------------------------------------------- forward
+def conv_layer(l: int, inp: np.ndarray, layers, out_scales, res=None) -> np.ndarray:
+    """One conv of the scheme: FP8 weights when its input is FP8, epilogue in float64, FP8 store of
+    its output when that tensor is FP8 (heads stay float)."""
+    specs = net.layer_specs()
+    L = layers[l]
+    w, b = net.fold_bn(L)
+    if l > FIRST_FP8_OUTPUT:                   # FP8 input tensor: per-channel FP8 weights
+        sw = weight_scales(w)
+        w = e4m3(w / sw[:, None, None, None]) * sw[:, None, None, None]
+    y = net.conv2d(inp, w, b, L["stride"])
+    if not is_head(specs[l]):
+        y = net.leaky(y)
+    if res is not None:
+        y = res + y
+    if l >= FIRST_FP8_OUTPUT and not is_head(specs[l]):
+        y = fake_quant(y, out_scales[l])
+    return y
+
+
 def forward(x: np.ndarray, layers, out_scales, keep_all: bool = False):
     """Fake-quantised forward: same structure as ``network.forward``; FP8 stores and FP8 weights where
     the scheme above puts them.  ``out_scales[l]`` is the scale of layer l's output tensor."""
@@ -128,18 +147,8 @@ def forward(x: np.ndarray, layers, out_scales, keep_all: bool = False):
 
     def conv(inp, linear=False, res=None):
         l = next(it)
-        L = layers[l]
-        w, b = net.fold_bn(L)
-        if l > FIRST_FP8_OUTPUT:                   # FP8 input tensor: per-channel FP8 weights
-            sw = weight_scales(w)
-            w = e4m3(w / sw[:, None, None, None]) * sw[:, None, None, None]
-        y = net.conv2d(inp, w, b, L["stride"])
-        if not linear:
-            y = net.leaky(y)
-        if res is not None:
-            y = res + y
-        if l >= FIRST_FP8_OUTPUT and not is_head(specs[l]):
-            y = fake_quant(y, out_scales[l])
+        assert linear == is_head(specs[l])
+        y = conv_layer(l, inp, layers, out_scales, res)
         if keep_all:
             acts.append(y)
         return y

@@ -193,6 +193,36 @@ def forward(x: np.ndarray, layers, keep_all: bool = False):
     return dets, embs, acts
 
 
+def layer_io():
+    """Wiring of ``forward`` as data: per conv ``(input, residual)``.  ``input`` is a layer id, -1 for
+    the network input, or ``("cat", lateral, skip)`` for the concat of the upsampled lateral's output
+    and a skip feature; ``residual`` is the layer id whose output is added, or None."""
+    io = []
+
+    def conv(inp, res=None):
+        io.append((inp, res))
+        return len(io) - 1
+
+    x = conv(-1)
+    feats = {}
+    for c, nb in STAGES:
+        x = conv(x)
+        for _ in range(nb):
+            x = conv(conv(x), res=x)
+        feats[c] = x
+    inp = feats[1024]
+    for cin, mid, lat in SCALES:
+        f = inp
+        for _ in range(5):
+            f = conv(f)
+        conv(conv(f))
+        conv(f)
+        if lat:
+            up = conv(f)
+            inp = ("cat", up, feats[2 * lat])
+    return io
+
+
 def flops(in_w: int, in_h: int) -> int:
     """Multiply-add FLOPs (2 M N K summed over convs) of one frame at the given input size."""
     specs = layer_specs()

@@ -38,6 +38,7 @@ struct TcArgs {
   int plane_tx;                    // mode 3: bytes one plane load delivers (WW * WH * 16)
   int nwin;                        // mode 3: window buffers in the ring (2 .. MAX_WIN)
   int total_units;                 // work units: tiles, or (CTA pairs) pairs of M tiles x N tiles
+  int kel;                         // elements of one k-block along K (E4M3: twice the bf16 count, same bytes)
   ConvSpec c;
 };
 
@@ -55,7 +56,9 @@ __host__ __device__ constexpr int tc_threads(int gw) { return 32 * (gw + 1 + EPI
 
 // CG = 2: a CTA pair computes a 256 x BN tile with one M=256 MMA; each CTA holds its own
 // 128 rows of A and half (BN/2 rows) of B.
-template <int BN, int BKC, int STAGES, int CG = 1>
+// Q = 1: E4M3 operands (one byte per element; a k-block row holds 2 * BKC elements, the same
+// bytes as BKC bf16 ones) and E4M3 staged outputs.
+template <int BN, int BKC, int STAGES, int CG = 1, int Q = 0>
 struct TcCfg {
   static constexpr int A_BYTES = 128 * BKC * 2;
   static constexpr int B_BYTES = (BN / CG) * BKC * 2;
@@ -65,9 +68,9 @@ struct TcCfg {
   static constexpr int SUB = SWC < 64 ? SWC : 64;       // channels per TMA store box (64 or 128-byte rows)
   static constexpr int NSUB = SWC / SUB;
   static constexpr int SUB_BYTES = 128 * SUB * 2;
-  static constexpr int C_BYTES = NSUB * SUB_BYTES;      // one staging tile (one epilogue pass)
+  static constexpr int C_BYTES = Q ? 128 * SWC : NSUB * SUB_BYTES;   // one staging tile (one epilogue pass)
   static constexpr int SDEPTH = 2;                      // staging tiles per epilogue group
-  static constexpr int BIAS_BYTES = 2 * BN * 4;         // each epilogue group's bias slice (f32)
+  static constexpr int BIAS_BYTES = 2 * BN * 4 * (Q ? 2 : 1);   // per epilogue group: bias (and E4M3 scale) slice
   static constexpr int BAR_BYTES = 768;                 // mbarriers + TMEM address slot
   static constexpr int SMEM =
       STAGES * STAGE_BYTES + 2 * SDEPTH * C_BYTES + 1024 /*align*/ + BAR_BYTES + BIAS_BYTES;
@@ -113,6 +116,22 @@ __device__ __forceinline__ void store_chunk(const ConvSpec& c, int n, int y, int
 #pragma unroll
         for (int j = 0; j < 32; ++j)
           if (j < nvalid) o[j] = __float2bfloat16_rn(v[j]);
+      }
+    } else if (c.out.dtype == 2) {
+      uint8_t* o = static_cast<uint8_t*>(c.out.ptr) + off;
+      if (nvalid == 32) {
+        uint32_t packed[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          packed[j] = e4m3x2(v[4 * j] * c.out_inv_scale, v[4 * j + 1] * c.out_inv_scale) |
+                      (e4m3x2(v[4 * j + 2] * c.out_inv_scale, v[4 * j + 3] * c.out_inv_scale) << 16);
+        uint4* o4 = reinterpret_cast<uint4*>(o);
+        o4[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+        o4[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (j < nvalid) o[j] = (uint8_t)(e4m3x2(v[j] * c.out_inv_scale, 0.f) & 0xFFu);
       }
     } else {
       float* o = static_cast<float*>(c.out.ptr) + off;
@@ -176,9 +195,9 @@ __device__ __forceinline__ bool tile_live(const TcArgs& a, const TileCoord& t) {
 // per CTA pair of a 2-CTA cluster, the leader CTA of the pair issuing the M=256 MMAs).
 // Warps 0..GW-1 produce (GW = 1: lane 0 of warp 0 issues TMA; the stem uses GW gather
 // warps), warp GW issues the MMAs and owns TMEM, the last 8 warps run the epilogue.
-template <int BN, int BKC, int STAGES, int GW, int CG>
+template <int BN, int BKC, int STAGES, int GW, int CG, int Q>
 __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid_constant__ TcPlan plan, const TcArgs a) {
-  using Cfg = TcCfg<BN, BKC, STAGES, CG>;
+  using Cfg = TcCfg<BN, BKC, STAGES, CG, Q>;
   const uint32_t rank = CG == 2 ? cluster_rank() : 0u;
   const int u0 = CG == 2 ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
   const int ustep = CG == 2 ? (int)(gridDim.x >> 1) : (int)gridDim.x;
@@ -363,22 +382,22 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
             if (rank == 0) mbar_expect_tx(&full[s], 2 * Cfg::STAGE_BYTES);
             if (a.mode == 0) {
               const int shift = a.k == 3 ? (ky - 1) * a.Wp + (kx - 1) : 0;
-              tma_load_2d_pair(dA, &plan.a[0], bar, cb * BKC, tc.m0 + shift);
+              tma_load_2d_pair(dA, &plan.a[0], bar, cb * a.kel, tc.m0 + shift);
             } else {
-              tma_load_4d_pair(dA, &plan.a[(ky & 1) * 2 + (kx & 1)], bar, cb * BKC, tc.ox0 + (kx >> 1),
+              tma_load_4d_pair(dA, &plan.a[(ky & 1) * 2 + (kx & 1)], bar, cb * a.kel, tc.ox0 + (kx >> 1),
                                tc.oy0 + (ky >> 1), tc.img);
             }
-            tma_load_2d_pair(sB + s * Cfg::B_BYTES, &plan.b, bar, kt * BKC, tc.n0 + (int)rank * (BN / 2));
+            tma_load_2d_pair(sB + s * Cfg::B_BYTES, &plan.b, bar, kt * a.kel, tc.n0 + (int)rank * (BN / 2));
           } else {
             mbar_expect_tx(&full[s], Cfg::STAGE_BYTES);
             if (a.mode == 0) {
               const int shift = a.k == 3 ? (ky - 1) * a.Wp + (kx - 1) : 0;
-              tma_load_2d(dA, &plan.a[0], &full[s], cb * BKC, tc.m0 + shift);
+              tma_load_2d(dA, &plan.a[0], &full[s], cb * a.kel, tc.m0 + shift);
             } else {
-              tma_load_4d(dA, &plan.a[(ky & 1) * 2 + (kx & 1)], &full[s], cb * BKC, tc.ox0 + (kx >> 1),
+              tma_load_4d(dA, &plan.a[(ky & 1) * 2 + (kx & 1)], &full[s], cb * a.kel, tc.ox0 + (kx >> 1),
                           tc.oy0 + (ky >> 1), tc.img);
             }
-            tma_load_2d(sB + s * Cfg::B_BYTES, &plan.b, &full[s], kt * BKC, tc.n0);
+            tma_load_2d(sB + s * Cfg::B_BYTES, &plan.b, &full[s], kt * a.kel, tc.n0);
           }
         }
       }
@@ -386,7 +405,7 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
   } else if (warp == GW) {
     if (lane == 0 && rank == 0) {
       // ---------------- MMA issuer (CG = 2: the leader CTA, for both CTAs of the pair)
-      constexpr uint32_t idesc = idesc_bf16(128 * CG, BN);
+      constexpr uint32_t idesc = Q ? idesc_e4m3(128 * CG, BN) : idesc_bf16(128 * CG, BN);
       uint32_t it = 0, local = 0;
       for (int u = u0; u < nunits; u += ustep, ++local) {
         const uint32_t buf = local % Cfg::NBUF, use = local / Cfg::NBUF;
@@ -402,7 +421,7 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
         }
         tc_fence_after();
         const uint32_t d = tmem + buf * BN;
-        if constexpr (CG == 1) if (a.mode == 3) {
+        if constexpr (CG == 1 && !Q) if (a.mode == 3) {
           const uint32_t wb = local % (uint32_t)a.nwin;
           if (!mbar_wait(&win_full[wb], (local / (uint32_t)a.nwin) & 1u)) {
             flag_error(c.err, KERR_TIMEOUT);
@@ -448,10 +467,15 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
           for (int kk = 0; kk < BKC / 16; ++kk) {
             const uint64_t ad = smem_desc(a_base + kk * 32, Cfg::SBO, Cfg::LAYOUT);
             const uint64_t bd = smem_desc(b_base + kk * 32, Cfg::SBO, Cfg::LAYOUT);
-            if constexpr (CG == 2)
-              umma_bf16_pair(d, ad, bd, idesc, (kt | kk) != 0 ? 1u : 0u);
+            const uint32_t accum = (kt | kk) != 0 ? 1u : 0u;
+            if constexpr (CG == 2 && Q)
+              umma_e4m3_pair(d, ad, bd, idesc, accum);
+            else if constexpr (CG == 2)
+              umma_bf16_pair(d, ad, bd, idesc, accum);
+            else if constexpr (Q)
+              umma_e4m3(d, ad, bd, idesc, accum);
             else
-              umma_bf16(d, ad, bd, idesc, (kt | kk) != 0 ? 1u : 0u);
+              umma_bf16(d, ad, bd, idesc, accum);
           }
           if constexpr (CG == 2)
             umma_commit_pair(&empty[s], 3);      // the stage is free in both CTAs
@@ -480,6 +504,7 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
     uint32_t res_uses = 0, local = 0, npass = 0;
     // bias of the group's current N tile, in shared memory (refilled when the N tile changes)
     float* const sBias = sBiasAll + g * BN;
+    float* const sMult = sBiasAll + 2 * BN + g * BN;       // Q: input scale x weight scale per channel
     const int gtid = (ew & 3) * 32 + lane;
     int bias_n0 = -1;
     // CG = 2: the accumulator buffer is released on the leader's barrier
@@ -498,7 +523,10 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
       const TileCoord tc = tile_coord(a, tile, BN);
       if (tc.n0 != bias_n0) {
         // the group finished reading the previous slice before the last pass's barrier
-        for (int i = gtid; i < BN; i += 128) sBias[i] = c.bias[tc.n0 + i];
+        for (int i = gtid; i < BN; i += 128) {
+          sBias[i] = c.bias[tc.n0 + i];
+          if (Q) sMult[i] = c.mult[tc.n0 + i];
+        }
         named_bar(bar_id, 128);
         bias_n0 = tc.n0;
       }
@@ -519,8 +547,13 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
         valid = y < c.Ho && x < c.Wo && tile_live(a, tc);
       }
       if (a.tma_out) {
-        // staged: TMEM -> (bias, leaky, + residual) -> bf16 staging tile -> TMA store.
-        // Rows on the halo are written as zeros, which keeps the halo zero.
+        // staged: TMEM -> (scale, bias, leaky, + residual) -> bf16 or E4M3 staging tile -> TMA store.
+        // Rows on the halo are written as zeros, which keeps the halo zero.  E4M3 rows are SWC
+        // bytes (64-byte swizzle), one box per pass.
+        const bool o8 = c.out.dtype == 2;
+        const int nsub = o8 ? 1 : Cfg::NSUB;
+        const int sub_ch = o8 ? Cfg::SWC : Cfg::SUB;
+        const int sub_bytes = o8 ? 128 * Cfg::SWC : Cfg::SUB_BYTES;
         for (int p = 0; p < Cfg::PASSES; ++p) {
           stg = stg_base + (npass++ % Cfg::SDEPTH) * Cfg::C_BYTES;
           const bool live = tile_live(a, tc);
@@ -528,13 +561,13 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
           if (elected) {
             bulk_wait_read<Cfg::SDEPTH - 1>();   // the store that last used this staging tile has read it
             if (use_res) {
-              mbar_expect_tx(&res_full[g], Cfg::C_BYTES);
-              for (int j = 0; j < Cfg::NSUB; ++j) {
-                const int ch = tc.n0 + p * Cfg::SWC + j * Cfg::SUB;
+              mbar_expect_tx(&res_full[g], (uint32_t)(nsub * sub_bytes));
+              for (int j = 0; j < nsub; ++j) {
+                const int ch = tc.n0 + p * Cfg::SWC + j * sub_ch;
                 if (patch_mode(a.mode))
-                  tma_load_4d(stg + j * Cfg::SUB_BYTES, &plan.r, &res_full[g], ch, tc.ox0 + 1, tc.oy0 + 1, tc.img);
+                  tma_load_4d(stg + j * sub_bytes, &plan.r, &res_full[g], ch, tc.ox0 + 1, tc.oy0 + 1, tc.img);
                 else
-                  tma_load_2d(stg + j * Cfg::SUB_BYTES, &plan.r, &res_full[g], ch, tc.m0);
+                  tma_load_2d(stg + j * sub_bytes, &plan.r, &res_full[g], ch, tc.m0);
               }
             }
           }
@@ -552,6 +585,59 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
             tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + buf * BN + (uint32_t)(p * Cfg::SWC + c0), r);
             tmem_ld_wait();
             const float4* b4 = reinterpret_cast<const float4*>(sBias + p * Cfg::SWC + c0);
+            if (Q) {
+              const float4* m4 = reinterpret_cast<const float4*>(sMult + p * Cfg::SWC + c0);
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                const float4 m = m4[i];
+                r[4 * i] = __float_as_uint(__uint_as_float(r[4 * i]) * m.x);
+                r[4 * i + 1] = __float_as_uint(__uint_as_float(r[4 * i + 1]) * m.y);
+                r[4 * i + 2] = __float_as_uint(__uint_as_float(r[4 * i + 2]) * m.z);
+                r[4 * i + 3] = __float_as_uint(__uint_as_float(r[4 * i + 3]) * m.w);
+              }
+            }
+            if (o8) {
+              // 32 columns = two 16-byte units of the 64-byte E4M3 row
+              float v[32];
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                const float4 b = b4[i];
+                v[4 * i] = __uint_as_float(r[4 * i]) + b.x;
+                v[4 * i + 1] = __uint_as_float(r[4 * i + 1]) + b.y;
+                v[4 * i + 2] = __uint_as_float(r[4 * i + 2]) + b.z;
+                v[4 * i + 3] = __uint_as_float(r[4 * i + 3]) + b.w;
+              }
+              if (c.act) {
+#pragma unroll
+                for (int e = 0; e < 32; ++e) v[e] = leaky01(v[e]);
+              }
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                uint8_t* q = stg + stage_off<32>(row, (c0 >> 4) + h);
+                if (use_res) {
+                  const uint4 rq = *reinterpret_cast<const uint4*>(q);
+                  const uint32_t rv[4] = {rq.x, rq.y, rq.z, rq.w};
+#pragma unroll
+                  for (int e = 0; e < 4; ++e) {
+                    const float2 lo = e4m3x2_to_float2(rv[e] & 0xFFFFu), hi = e4m3x2_to_float2(rv[e] >> 16);
+                    v[16 * h + 4 * e] += lo.x * c.res_scale;
+                    v[16 * h + 4 * e + 1] += lo.y * c.res_scale;
+                    v[16 * h + 4 * e + 2] += hi.x * c.res_scale;
+                    v[16 * h + 4 * e + 3] += hi.y * c.res_scale;
+                  }
+                }
+                uint32_t pk[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                  const float* w = v + 16 * h + 4 * e;
+                  pk[e] = valid ? (e4m3x2(w[0] * c.out_inv_scale, w[1] * c.out_inv_scale) |
+                                   (e4m3x2(w[2] * c.out_inv_scale, w[3] * c.out_inv_scale) << 16))
+                                : 0u;
+                }
+                *reinterpret_cast<uint4*>(q) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+              }
+              continue;
+            }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
               const int col = c0 + 8 * u;                       // column inside this pass
@@ -597,12 +683,12 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
           fence_proxy_async();               // staging writes visible to the TMA store
           named_bar(bar_id, 128);
           if (elected && ok && live && !aborted(&s_abort)) {
-            for (int j = 0; j < Cfg::NSUB; ++j) {
-              const int ch = tc.n0 + p * Cfg::SWC + j * Cfg::SUB;
+            for (int j = 0; j < nsub; ++j) {
+              const int ch = tc.n0 + p * Cfg::SWC + j * sub_ch;
               if (!patch_mode(a.mode))
-                tma_store_2d(&plan.o, stg + j * Cfg::SUB_BYTES, ch, tc.m0);
+                tma_store_2d(&plan.o, stg + j * sub_bytes, ch, tc.m0);
               else
-                tma_store_4d(&plan.o, stg + j * Cfg::SUB_BYTES, ch, tc.ox0 + 1, tc.oy0 + 1, tc.img);
+                tma_store_4d(&plan.o, stg + j * sub_bytes, ch, tc.ox0 + 1, tc.oy0 + 1, tc.img);
             }
             bulk_commit();
           }
@@ -621,15 +707,22 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
             float v[32];
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
-              const float t = __uint_as_float(r[j]) + sBias[c0 + j];
+              const float acc = Q ? __uint_as_float(r[j]) * sMult[c0 + j] : __uint_as_float(r[j]);
+              const float t = acc + sBias[c0 + j];
               v[j] = c.act ? leaky01(t) : t;
             }
             if (c.res.ptr) {
+              const size_t ro = tview_off(c.res, n, y, x) + ch0;
 #pragma unroll
               for (int j = 0; j < 32; ++j)
-                if (j < nvalid)
-                  v[j] += __bfloat162float(
-                      static_cast<const __nv_bfloat16*>(c.res.ptr)[tview_off(c.res, n, y, x) + ch0 + j]);
+                if (j < nvalid) {
+                  if (c.res.dtype == 2) {
+                    const uint8_t code = static_cast<const uint8_t*>(c.res.ptr)[ro + j];
+                    v[j] += e4m3x2_to_float2(code).x * c.res_scale;
+                  } else {
+                    v[j] += __bfloat162float(static_cast<const __nv_bfloat16*>(c.res.ptr)[ro + j]);
+                  }
+                }
             }
             store_chunk(c, n, y, x, ch0, nvalid, v);
           }
@@ -677,14 +770,19 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
+// bkc: elements of the innermost box dimension; its bytes (2 per bf16, 1 per E4M3 code when u8)
+// choose the swizzle: 128 -> 128-byte, 64 -> 64-byte, otherwise none.
 bool encode(CUtensorMap* m, int rank, void* base, const cuuint64_t* dims, const cuuint64_t* strides_bytes,
-            const cuuint32_t* box, int bkc) {
+            const cuuint32_t* box, int bkc, bool u8 = false) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   cuuint32_t es[5] = {1, 1, 1, 1, 1};
-  const CUtensorMapSwizzle swz =
-      bkc == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : (bkc == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE);
-  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, base, dims, strides_bytes, box, es,
+  const int row_bytes = bkc * (u8 ? 1 : 2);
+  const CUtensorMapSwizzle swz = row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                 : row_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                                   : CU_TENSOR_MAP_SWIZZLE_NONE;
+  CUresult r = fn(m, u8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, base,
+                  dims, strides_bytes, box, es,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -700,10 +798,10 @@ int sm_count() {
   return n;
 }
 
-template <int BN, int BKC, int STAGES, int GW = 1, int CG = 1>
+template <int BN, int BKC, int STAGES, int GW = 1, int CG = 1, int Q = 0>
 cudaError_t launch_cfg(const TcPlan& p, const TcArgs& a, cudaStream_t st, int smem = 0) {
-  using Cfg = TcCfg<BN, BKC, STAGES, CG>;
-  auto kernel = conv_tc_kernel<BN, BKC, STAGES, GW, CG>;
+  using Cfg = TcCfg<BN, BKC, STAGES, CG, Q>;
+  auto kernel = conv_tc_kernel<BN, BKC, STAGES, GW, CG, Q>;
   if (!smem) smem = Cfg::SMEM;
   static int attr_set = 0;
   if (attr_set < smem) {
@@ -755,8 +853,9 @@ int conv_tc_pick_bn(int cout) {
   return 256;
 }
 
-bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const __nv_bfloat16* w, int cout_pad, int bn, char* msg,
+bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const void* w_any, int cout_pad, int bn, char* msg,
                   size_t msg_len) {
+  const __nv_bfloat16* w = static_cast<const __nv_bfloat16*>(w_any);
   plan = TcPlan();
   plan.spec = c;
   if (c.cin == 3 && c.k == 3 && c.stride == 1 && c.in.dtype == 1 && c.in.pad == 1 && c.in.pixstride == 4 &&
@@ -862,15 +961,26 @@ bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const __nv_bfloat16* w, int c
     if (!ok) snprintf(msg, msg_len, "cuTensorMapEncodeTiled failed (32-channel window conv)");
     return ok;
   }
-  const int bkc = (c.cin % 64 == 0) ? 64 : (c.cin % 32 == 0 ? 32 : 0);
-  if (!bkc || c.in.dtype != 1 || c.in.pad != 1 || !(c.k == 1 || c.k == 3) || !(c.stride == 1 || c.stride == 2) ||
-      (c.stride == 2 && c.k != 3) || (bn != 32 && bn != 64 && bn != 128 && bn != 256) || cout_pad % bn) {
-    snprintf(msg, msg_len, "tensor-core conv: unsupported shape cin=%d k=%d s=%d bn=%d", c.cin, c.k, c.stride, bn);
+  // k-block: 128-byte rows (64 bf16 or 128 E4M3 elements), or 64-byte rows for narrower inputs
+  const bool q = c.q != 0;
+  const int ie = q ? 1 : 2;                 // bytes per input / weight element
+  const int kel = q ? ((c.cin % 128 == 0) ? 128 : (c.cin % 64 == 0 ? 64 : 0))
+                    : ((c.cin % 64 == 0) ? 64 : (c.cin % 32 == 0 ? 32 : 0));
+  const int bkc = q ? kel / 2 : kel;        // the kernel's row unit: row bytes / 2
+  const bool o8 = c.out.dtype == 2;
+  if (!kel || c.in.dtype != (q ? 2 : 1) || c.in.pad != 1 || !(c.k == 1 || c.k == 3) ||
+      !(c.stride == 1 || c.stride == 2) || (c.stride == 2 && c.k != 3) ||
+      (bn != 32 && bn != 64 && bn != 128 && bn != 256) || cout_pad % bn || (o8 && bn < 64) ||
+      (q && c.out.dtype == 1)) {
+    snprintf(msg, msg_len, "tensor-core conv: unsupported shape cin=%d k=%d s=%d bn=%d q=%d out=%d", c.cin, c.k,
+             c.stride, bn, (int)q, c.out.dtype);
     return false;
   }
   plan.bn = bn;
   plan.bkc = bkc;
-  plan.cin_blocks = c.cin / bkc;
+  plan.kel = kel;
+  plan.q = q;
+  plan.cin_blocks = c.cin / kel;
   plan.kt_total = c.k * c.k * plan.cin_blocks;
   plan.n_tiles = cout_pad / bn;
   const int K = c.k * c.k * c.cin;
@@ -884,9 +994,9 @@ bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const __nv_bfloat16* w, int c
     plan.M_total = c.in.n * Hp * Wp;
     plan.m_tiles = (plan.M_total + 127) / 128;
     cuuint64_t dims[2] = {(cuuint64_t)c.cin, (cuuint64_t)plan.M_total};
-    cuuint64_t strides[1] = {(cuuint64_t)c.in.pixstride * 2};
-    cuuint32_t box[2] = {(cuuint32_t)bkc, 128};
-    ok &= encode(&plan.a[0], 2, base, dims, strides, box, bkc);
+    cuuint64_t strides[1] = {(cuuint64_t)c.in.pixstride * ie};
+    cuuint32_t box[2] = {(cuuint32_t)kel, 128};
+    ok &= encode(&plan.a[0], 2, base, dims, strides, box, kel, q);
   } else {
     plan.mode = 1;
     if ((c.in.h & 1) || (c.in.w & 1)) {
@@ -907,47 +1017,53 @@ bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const __nv_bfloat16* w, int c
     plan.m_tiles = c.in.n * plan.tiles_x * plan.tiles_y;
     for (int py = 0; py < 2; ++py)
       for (int px = 0; px < 2; ++px) {
-        void* pb = static_cast<__nv_bfloat16*>(base) + ((size_t)py * Wp + px) * c.in.pixstride;
+        void* pb = static_cast<uint8_t*>(base) + ((size_t)py * Wp + px) * c.in.pixstride * ie;
         cuuint64_t dims[4] = {(cuuint64_t)c.cin, (cuuint64_t)(Wp / 2), (cuuint64_t)(Hp / 2), (cuuint64_t)c.in.n};
-        cuuint64_t strides[3] = {(cuuint64_t)2 * c.in.pixstride * 2, (cuuint64_t)2 * Wp * c.in.pixstride * 2,
-                                 (cuuint64_t)Hp * Wp * c.in.pixstride * 2};
-        cuuint32_t box[4] = {(cuuint32_t)bkc, (cuuint32_t)plan.TW, (cuuint32_t)plan.TH, 1};
-        ok &= encode(&plan.a[py * 2 + px], 4, pb, dims, strides, box, bkc);
+        cuuint64_t strides[3] = {(cuuint64_t)2 * c.in.pixstride * ie, (cuuint64_t)2 * Wp * c.in.pixstride * ie,
+                                 (cuuint64_t)Hp * Wp * c.in.pixstride * ie};
+        cuuint32_t box[4] = {(cuuint32_t)kel, (cuuint32_t)plan.TW, (cuuint32_t)plan.TH, 1};
+        ok &= encode(&plan.a[py * 2 + px], 4, pb, dims, strides, box, kel, q);
       }
   }
   // 256-wide tiles run on CTA pairs (M = 256 per MMA, each CTA loads half of B)
   plan.cg = bn == 256 && bkc == 64 ? 2 : 1;
   {
     cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)cout_pad};
-    cuuint64_t strides[1] = {(cuuint64_t)K * 2};
-    cuuint32_t box[2] = {(cuuint32_t)bkc, (cuuint32_t)(bn / plan.cg)};
-    ok &= encode(&plan.b, 2, const_cast<__nv_bfloat16*>(w), dims, strides, box, bkc);
+    cuuint64_t strides[1] = {(cuuint64_t)K * ie};
+    cuuint32_t box[2] = {(cuuint32_t)kel, (cuuint32_t)(bn / plan.cg)};
+    ok &= encode(&plan.b, 2, const_cast<void*>(w_any), dims, strides, box, kel, q);
   }
-  // TMA-stored epilogue: bf16 padded outputs written in place (no upsample), channel
-  // count a multiple of the store box (64, or 32 for 32-wide tiles)
-  const int sub = bn < 64 ? bn : 64;
-  plan.tma_out = c.out.dtype == 1 && !c.upsample && c.out.pad == 1 && c.cout % sub == 0;
-  plan.tma_res = plan.tma_out && c.res.ptr != nullptr && c.stride == 1 && c.res.dtype == 1 && c.res.pad == 1;
+  // TMA-stored epilogue: bf16 or E4M3 padded outputs written in place (no upsample), channel
+  // count a multiple of the store box (64 channels, or 32 for 32-wide bf16 tiles)
+  const int sub = o8 ? 64 : (bn < 64 ? bn : 64);
+  const int oe = o8 ? 1 : 2;
+  plan.tma_out = (c.out.dtype == 1 || o8) && !c.upsample && c.out.pad == 1 && c.cout % sub == 0;
+  plan.tma_res = plan.tma_out && c.res.ptr != nullptr && c.stride == 1 && c.res.dtype == c.out.dtype &&
+                 c.res.pad == 1;
+  if (q && !o8 && plan.tma_out) {
+    snprintf(msg, msg_len, "E4M3 conv: staged outputs must be E4M3");
+    return false;
+  }
   if (plan.tma_out) {
     const int Ho = c.Ho, Wo = c.Wo;
     if (plan.mode == 0) {
       cuuint64_t dims[2] = {(cuuint64_t)c.cout, (cuuint64_t)plan.M_total};
-      cuuint64_t strides[1] = {(cuuint64_t)c.out.pixstride * 2};
+      cuuint64_t strides[1] = {(cuuint64_t)c.out.pixstride * oe};
       cuuint32_t box[2] = {(cuuint32_t)sub, 128};
-      ok &= encode(&plan.o, 2, c.out.ptr, dims, strides, box, sub);
+      ok &= encode(&plan.o, 2, c.out.ptr, dims, strides, box, sub, o8);
     } else {
       cuuint64_t dims[4] = {(cuuint64_t)c.cout, (cuuint64_t)(Wo + 2), (cuuint64_t)(Ho + 2), (cuuint64_t)c.out.n};
-      cuuint64_t strides[3] = {(cuuint64_t)c.out.pixstride * 2, (cuuint64_t)(Wo + 2) * c.out.pixstride * 2,
-                               (cuuint64_t)(Ho + 2) * (Wo + 2) * c.out.pixstride * 2};
+      cuuint64_t strides[3] = {(cuuint64_t)c.out.pixstride * oe, (cuuint64_t)(Wo + 2) * c.out.pixstride * oe,
+                               (cuuint64_t)(Ho + 2) * (Wo + 2) * c.out.pixstride * oe};
       cuuint32_t box[4] = {(cuuint32_t)sub, (cuuint32_t)plan.TW, (cuuint32_t)plan.TH, 1};
-      ok &= encode(&plan.o, 4, c.out.ptr, dims, strides, box, sub);
+      ok &= encode(&plan.o, 4, c.out.ptr, dims, strides, box, sub, o8);
     }
   }
   if (plan.tma_res) {
     cuuint64_t dims[2] = {(cuuint64_t)c.cout, (cuuint64_t)plan.M_total};
-    cuuint64_t strides[1] = {(cuuint64_t)c.res.pixstride * 2};
+    cuuint64_t strides[1] = {(cuuint64_t)c.res.pixstride * oe};
     cuuint32_t box[2] = {(cuuint32_t)sub, 128};
-    ok &= encode(&plan.r, 2, c.res.ptr, dims, strides, box, sub);
+    ok &= encode(&plan.r, 2, c.res.ptr, dims, strides, box, sub, o8);
   }
   if (!ok) {
     snprintf(msg, msg_len, "cuTensorMapEncodeTiled failed (cin=%d k=%d s=%d)", c.cin, c.k, c.stride);
@@ -979,6 +1095,7 @@ cudaError_t conv_tc_launch(const TcPlan& p, cudaStream_t st) {
   a.WH = p.WH;
   a.win_bytes = p.win_bytes;
   a.nwin = p.nwin;
+  a.kel = p.kel ? p.kel : p.bkc;
   a.plane = p.plane;
   a.plane_tx = p.WW * p.WH * 16;
   a.c = p.spec;
@@ -993,6 +1110,22 @@ cudaError_t conv_tc_launch(const TcPlan& p, cudaStream_t st) {
                      Cfg8::BAR_BYTES + Cfg8::BIAS_BYTES;
     if (p.bn != 64 || smem > 227 * 1024 - 64) return cudaErrorInvalidValue;
     return launch_cfg<64, 64, 6, 1>(p, a, st, smem);
+  }
+  if (p.q) {
+    // E4M3 operands: 64-bf16-unit rows hold 128 codes, 32-unit rows 64 codes
+    if (p.bkc == 64) {
+      switch (p.bn) {
+        case 32: return launch_cfg<32, 64, 10, 1, 1, 1>(p, a, st);
+        case 64: return launch_cfg<64, 64, 8, 1, 1, 1>(p, a, st);
+        case 128: return launch_cfg<128, 64, 5, 1, 1, 1>(p, a, st);
+        case 256:
+          if (p.cg == 2) return launch_cfg<256, 64, 5, 1, 2, 1>(p, a, st);
+          break;
+      }
+    } else if (p.bkc == 32 && p.bn == 128) {
+      return launch_cfg<128, 32, 11, 1, 1, 1>(p, a, st);
+    }
+    return cudaErrorInvalidValue;
   }
   if (p.bkc == 64) {
     switch (p.bn) {

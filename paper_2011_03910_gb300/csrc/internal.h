@@ -17,6 +17,11 @@ struct ConvSpec {
   int upsample;         // 1: write each output pixel to a 2x2 block of `out`
   const float* bias;    // [cout_pad] f32
   int* err;
+  // FP8 (E4M3) operands: acc * mult[co] + bias[co] (mult = input scale * weight scale of channel co)
+  int q;                // 1: input and weights are E4M3 codes
+  const float* mult;    // [cout_pad] f32 when q
+  float res_scale;      // value of one residual code (res.dtype == 2)
+  float out_inv_scale;  // 1 / scale of the output tensor (out.dtype == 2)
 };
 
 // SIMT f32 path: weights [K_pad16][cout_pad64] f32, K = (ky*k + kx)*cin + ci.
@@ -38,12 +43,15 @@ struct TcPlan {
   int WW, WH, win_bytes, plane;  // mode 3: (sub-)window pixels, bytes per buffer, bytes per 8-channel plane
   int nwin;                      // mode 3: window buffers in the ring
   int cg;                        // 2: 256-wide tiles on CTA pairs (cta_group::2), else 1
+  int q;                         // 1: E4M3 operands (kind::f8f6f4)
+  int kel;                       // elements of one k-block along K (bf16: bkc, E4M3: 2 * bkc)
   ConvSpec spec;
 };
 // Fill plan (tensor maps and grid) for a conv whose input is a padded bf16
 // view and whose weights are w ([cout_pad][K] bf16).  Returns false with a
 // message if the shape is not supported by the tensor-core path.
-bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const __nv_bfloat16* w, int cout_pad, int bn, char* msg,
+// w: [cout_pad][K] bf16, or E4M3 codes when c.q.
+bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const void* w, int cout_pad, int bn, char* msg,
                   size_t msg_len);
 cudaError_t conv_tc_launch(const TcPlan& plan, cudaStream_t st);
 int conv_tc_pick_bn(int cout);

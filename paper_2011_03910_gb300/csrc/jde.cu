@@ -81,9 +81,20 @@ int align_up(int v, int a) { return (v + a - 1) / a * a; }
 struct LayerW {
   float* w_kn = nullptr;           // f32 [K_pad16][cout_pad64]
   __nv_bfloat16* w_nk = nullptr;   // bf16 [cout_pad_tc][K_tc]
+  uint8_t* w_q = nullptr;          // E4M3 codes [cout_pad_tc][K_tc] (E4M3 layers)
+  double* wscale = nullptr;        // E4M3 layers: per-channel weight scale [cout_pad_tc] (exact, for rounding)
+  float* mult = nullptr;           // E4M3 layers: input scale * weight scale [cout_pad_tc]
+  std::vector<double> wscale_host;
   float* bias = nullptr;           // f32 [bias_len]
   int cout_pad64 = 0, cout_pad_tc = 0, bn = 0, k_tc = 0;
+  int q = 0;                       // 1: E4M3 operands
 };
+
+// E4M3 handles: layer outputs from this layer on are stored as E4M3 codes, and the layers
+// after it take E4M3 inputs (the stem and the 32/64-channel layers before stay BF16).
+constexpr int FP8_FIRST_OUT = 4;
+bool is_q_layer(int precision, int l) { return precision == JDE_FP8_E4M3 && l > FP8_FIRST_OUT; }
+int el_size(int dt) { return dt == 0 ? 4 : (dt == 1 ? 2 : 1); }
 
 // Where each conv reads and writes (tensor ids below, -1 = none).
 struct LayerIO {
@@ -100,7 +111,7 @@ enum { T_CAT16 = 78, T_CAT8 = 79, T_LB = 80, T_COUNT = 81 };
 struct TensorDesc {
   int h, w, c;     // unpadded size at the given input resolution (per frame)
   int pad;
-  int f32;         // 1: f32 storage
+  int dt;          // storage: 0 f32, 1 bf16, 2 E4M3 codes
   int alias;       // >= 0: lives inside tensor `alias` at channel offset `alias_off`
   int alias_off;
 };
@@ -149,6 +160,11 @@ struct jde_handle {
   int head_set = 0;   // head-tensor set the next forward writes
   int cur_set = 0;    // set written by the last forward
   size_t weight_bytes = 0;   // device bytes of the packed weights
+  // E4M3 handles: scale of each stored tensor (per tensor id; concat buffers shared), set by
+  // jde_set_act_amax
+  std::vector<float> act_scale = std::vector<float>(T_COUNT, 1.0f);
+  bool scales_set = false;
+  float* d_amax = nullptr;   // jde_act_amax scratch [JDE_NUM_LAYERS]
 };
 
 namespace {
@@ -232,7 +248,7 @@ std::vector<LayerIO> build_io() {
 void tensor_desc_table(const jde_handle* h, int in_w, int in_h, std::vector<TensorDesc>& td) {
   const auto& L = layers();
   td.assign(T_COUNT, TensorDesc{0, 0, 0, 1, 0, -1, 0});
-  const bool bf16 = h->cfg.precision == JDE_BF16;
+  const bool bf16 = h->cfg.precision != JDE_FP32;   // tensor-core path (BF16 / E4M3)
   // spatial size of every layer output follows the input chain
   std::vector<int> oh(L.size()), ow(L.size());
   auto in_hw = [&](int tid, int& hh, int& ww) {
@@ -255,7 +271,10 @@ void tensor_desc_table(const jde_handle* h, int in_w, int in_h, std::vector<Tens
     in_hw(h->io[l].in, hh, ww);
     oh[l] = (hh + 2 * (L[l].k / 2) - L[l].k) / L[l].stride + 1;
     ow[l] = (ww + 2 * (L[l].k / 2) - L[l].k) / L[l].stride + 1;
-    TensorDesc d{oh[l], ow[l], L[l].cout, 1, (!bf16 || h->io[l].head >= 0) ? 1 : 0, -1, 0};
+    const int prec = h->cfg.precision;
+    const int dt = (prec == JDE_FP32 || h->io[l].head >= 0) ? 0
+                   : (prec == JDE_FP8_E4M3 && (int)l >= FP8_FIRST_OUT) ? 2 : 1;
+    TensorDesc d{oh[l], ow[l], L[l].cout, 1, dt, -1, 0};
     if (h->io[l].head >= 0) d.pad = 0;
     if (h->io[l].out != (int)l) {
       d.alias = h->io[l].out;
@@ -267,13 +286,14 @@ void tensor_desc_table(const jde_handle* h, int in_w, int in_h, std::vector<Tens
     }
     td[l] = d;
   }
-  td[T_CAT16] = TensorDesc{in_h / 16, in_w / 16, 768, 1, bf16 ? 0 : 1, -1, 0};
-  td[T_CAT8] = TensorDesc{in_h / 8, in_w / 8, 384, 1, bf16 ? 0 : 1, -1, 0};
-  td[T_LB] = TensorDesc{in_h, in_w, bf16 ? 4 : 3, 1, bf16 ? 0 : 1, -1, 0};
+  const int cat_dt = !bf16 ? 0 : (h->cfg.precision == JDE_FP8_E4M3 ? 2 : 1);
+  td[T_CAT16] = TensorDesc{in_h / 16, in_w / 16, 768, 1, cat_dt, -1, 0};
+  td[T_CAT8] = TensorDesc{in_h / 8, in_w / 8, 384, 1, cat_dt, -1, 0};
+  td[T_LB] = TensorDesc{in_h, in_w, bf16 ? 4 : 3, 1, bf16 ? 1 : 0, -1, 0};
 }
 
 size_t tensor_bytes(const TensorDesc& d, int n) {
-  const size_t el = d.f32 ? 4 : 2;
+  const size_t el = el_size(d.dt);
   return (size_t)n * (d.h + 2 * d.pad) * (d.w + 2 * d.pad) * d.c * el;
 }
 
@@ -292,7 +312,7 @@ jde_status get_res(jde_handle* h, int in_w, int in_h, ResBuffers** out) {
   rb.bytes.assign(T_COUNT, 0);
   rb.set_bytes.assign(T_COUNT, 0);
   const int n = h->cfg.max_batch;
-  const bool bf16 = h->cfg.precision == JDE_BF16;
+  const bool bf16 = h->cfg.precision != JDE_FP32;   // tensor-core path (BF16 / E4M3)
   for (int t = 0; t < T_COUNT; ++t) {
     if (rb.td[t].alias >= 0) continue;
     const bool head = t < JDE_NUM_LAYERS && h->io[t].head >= 0;
@@ -317,7 +337,7 @@ TView view_of(const ResBuffers& rb, int tid, int n) {
   TView v;
   if (d.alias >= 0) {
     const TensorDesc& p = rb.td[d.alias];
-    const size_t el = p.f32 ? 4 : 2;
+    const size_t el = el_size(p.dt);
     v.ptr = static_cast<char*>(rb.mem[d.alias]) + (size_t)d.alias_off * el;
     v.n = n;
     v.h = d.h;
@@ -325,7 +345,7 @@ TView view_of(const ResBuffers& rb, int tid, int n) {
     v.c = d.c;
     v.pad = p.pad;
     v.pixstride = p.c;
-    v.dtype = p.f32 ? 0 : 1;
+    v.dtype = p.dt;
   } else {
     v.ptr = rb.mem[tid];
     v.n = n;
@@ -334,10 +354,16 @@ TView view_of(const ResBuffers& rb, int tid, int n) {
     v.c = d.c;
     v.pad = d.pad;
     v.pixstride = d.c;
-    v.dtype = d.f32 ? 0 : 1;
+    v.dtype = d.dt;
   }
   if (tid == T_LB && d.c == 4) v.c = 3;   // bf16 letterbox stores RGB + one zero channel
   return v;
+}
+
+// Storage tensor of tensor id `tid` (a concat buffer for the layers writing into one).
+int buffer_of(const jde_handle* h, int tid) {
+  if (tid >= 0 && tid < JDE_NUM_LAYERS && h->io[tid].out != tid) return h->io[tid].out;
+  return tid;
 }
 
 jde_status get_plan(jde_handle* h, ResBuffers* rb, int n, Plan** out) {
@@ -351,7 +377,7 @@ jde_status get_plan(jde_handle* h, ResBuffers* rb, int n, Plan** out) {
   Plan p;
   p.n = n;
   p.specs.resize(L.size());
-  const bool bf16 = h->cfg.precision == JDE_BF16;
+  const bool bf16 = h->cfg.precision != JDE_FP32;   // tensor-core path (BF16 / E4M3)
   if (bf16) p.tc.resize(L.size());
   for (size_t l = 0; l < L.size(); ++l) {
     const LayerIO& io = h->io[l];
@@ -371,10 +397,15 @@ jde_status get_plan(jde_handle* h, ResBuffers* rb, int n, Plan** out) {
     c.upsample = io.upsample;
     c.bias = h->w[l].bias;
     c.err = h->d_err;
+    c.q = h->w[l].q;
+    c.mult = h->w[l].mult;
+    if (c.res.ptr && c.res.dtype == 2) c.res_scale = h->act_scale[buffer_of(h, io.res)];
+    if (c.out.dtype == 2) c.out_inv_scale = 1.0f / h->act_scale[buffer_of(h, (int)l)];
     p.specs[l] = c;
     if (bf16) {
       char msg[256];
-      if (!conv_tc_plan(p.tc[l], c, h->w[l].w_nk, h->w[l].cout_pad_tc, h->w[l].bn, msg, sizeof(msg)))
+      const void* w = c.q ? static_cast<const void*>(h->w[l].w_q) : static_cast<const void*>(h->w[l].w_nk);
+      if (!conv_tc_plan(p.tc[l], c, w, h->w[l].cout_pad_tc, h->w[l].bn, msg, sizeof(msg)))
         return fail(h, JDE_ERR_UNSUPPORTED, "layer %zu: %s", l, msg);
     }
   }
@@ -411,8 +442,67 @@ __global__ void pack_kernel(const float* W, const float* gamma, const float* bet
   }
 }
 
+// E4M3 layers: per output channel, scale = max |W'[co]| / 448 of the folded weights (1 for a zero channel).
+__global__ void wscale_kernel(const float* W, const float* gamma, const float* var, int cin, int cout, int k,
+                              double* wscale, int cptc) {
+  const int co = blockIdx.x;
+  __shared__ double red[256];
+  double m = 0.0;
+  if (co < cout) {
+    const double scale = gamma ? (double)gamma[co] / sqrt((double)var[co] + 1e-5) : 1.0;
+    const size_t nper = (size_t)cin * k * k;
+    for (size_t i = threadIdx.x; i < nper; i += blockDim.x) m = fmax(m, fabs((double)W[co * nper + i] * scale));
+  }
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && co < cptc) wscale[co] = red[0] > 0.0 ? red[0] / 448.0 : 1.0;
+}
+
+// E4M3 code of a double, rounded once from the exact quotient (no float intermediate, whose own
+// rounding can land on a midpoint of the 8-bit grid): binade 2^k (k >= -6; below that the
+// subnormal spacing 2^-9), spacing 2^(k-3), nearest with ties to even, finite values saturate
+// at 448; then the bit fields (sign, exponent k + 7, 3 mantissa bits; exponent 0 = subnormal).
+__device__ uint8_t e4m3_code(double v) {
+  if (v != v) return 0x7F;
+  const uint8_t sign = v < 0.0 ? 0x80 : 0x00;
+  const double a = fabs(v);
+  int ex = 0;
+  frexp(a, &ex);
+  int k = a > 0.0 ? ex - 1 : -6;
+  if (k < -6) k = -6;
+  double r = rint(a / ldexp(1.0, k - 3)) * ldexp(1.0, k - 3);
+  if (r > 448.0) r = 448.0;
+  if (r == 0.0) return sign;
+  frexp(r, &ex);
+  const int kr = ex - 1;
+  if (kr < -6) return sign | (uint8_t)rint(r / ldexp(1.0, -9));
+  return sign | (uint8_t)((kr + 7) << 3) | (uint8_t)((int)rint(r / ldexp(1.0, kr - 3)) - 8);
+}
+
+// E4M3 layers: w_q[co][kk] = E4M3(W'[co][kk] / wscale[co]), K index = tap * cin + ci.
+__global__ void pack_q_kernel(const float* W, const float* gamma, const float* var, int cin, int cout, int k,
+                              const double* wscale, uint8_t* w_q, int cptc, int ktc) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)cptc * ktc) return;
+  const int co = (int)(idx / ktc), kk = (int)(idx % ktc);
+  double v = 0.0;
+  const int K = cin * k * k;
+  if (co < cout && kk < K) {
+    const double scale = gamma ? (double)gamma[co] / sqrt((double)var[co] + 1e-5) : 1.0;
+    const int tap = kk / cin, ci = kk % cin;
+    const double w = (double)W[(((size_t)co * cin + ci) * k + tap / k) * k + tap % k] * scale;
+    v = w / wscale[co];
+  }
+  w_q[idx] = e4m3_code(v);
+}
+
 // Device bytes of one layer's packed weights (bias + tensor-core or SIMT layout).
-size_t layer_weight_bytes(const LayerDef& L, bool bf16, int l) {
+size_t layer_weight_bytes(const LayerDef& L, int precision, int l) {
+  const bool bf16 = precision != JDE_FP32;
   const int K = L.k * L.k * L.cin;
   const int cout_pad64 = align_up(L.cout, 64);
   const int bn = conv_tc_pick_bn(L.cout);
@@ -420,7 +510,10 @@ size_t layer_weight_bytes(const LayerDef& L, bool bf16, int l) {
   const int k_tc = l == 0 ? 32 : (L.cin == 32 && L.k == 3 ? 320 : K);
   const int bias_len = (cout_pad64 > cout_pad_tc ? cout_pad64 : cout_pad_tc) + 256;
   size_t b = sizeof(float) * (size_t)bias_len;
-  b += bf16 ? sizeof(__nv_bfloat16) * (size_t)cout_pad_tc * k_tc : sizeof(float) * (size_t)align_up(K, 16) * cout_pad64;
+  if (is_q_layer(precision, l))
+    b += (size_t)cout_pad_tc * k_tc + (sizeof(double) + sizeof(float)) * (size_t)cout_pad_tc;
+  else
+    b += bf16 ? sizeof(__nv_bfloat16) * (size_t)cout_pad_tc * k_tc : sizeof(float) * (size_t)align_up(K, 16) * cout_pad64;
   return b;
 }
 
@@ -463,7 +556,7 @@ jde_status load_weights(jde_handle* h, const void* blob, size_t nbytes) {
   void* dblob = nullptr;
   if (!dmalloc(&dblob, nbytes)) return fail(h, JDE_ERR_OOM, "weights staging (%zu bytes)", nbytes);
   CUDA_OR(h, cudaMemcpy(dblob, blob, nbytes, cudaMemcpyHostToDevice));
-  const bool bf16 = h->cfg.precision == JDE_BF16;
+  const bool bf16 = h->cfg.precision != JDE_FP32;   // tensor-core path (BF16 / E4M3)
   h->w.resize(L.size());
   for (size_t l = 0; l < L.size(); ++l) {
     LayerW& lw = h->w[l];
@@ -476,7 +569,12 @@ jde_status load_weights(jde_handle* h, const void* blob, size_t nbytes) {
     lw.k_tc = l == 0 ? 32 : (L[l].cin == 32 && L[l].k == 3 ? 320 : K);
     const int bias_len = (lw.cout_pad64 > lw.cout_pad_tc ? lw.cout_pad64 : lw.cout_pad_tc) + 256;
     bool ok = dmalloc((void**)&lw.bias, sizeof(float) * bias_len);
-    if (bf16)
+    lw.q = is_q_layer(h->cfg.precision, (int)l) ? 1 : 0;
+    if (lw.q)
+      ok = ok && dmalloc((void**)&lw.w_q, (size_t)lw.cout_pad_tc * lw.k_tc) &&
+           dmalloc((void**)&lw.wscale, sizeof(double) * lw.cout_pad_tc) &&
+           dmalloc((void**)&lw.mult, sizeof(float) * lw.cout_pad_tc);
+    else if (bf16)
       ok = ok && dmalloc((void**)&lw.w_nk, sizeof(__nv_bfloat16) * (size_t)lw.cout_pad_tc * lw.k_tc);
     else
       ok = ok && dmalloc((void**)&lw.w_kn, sizeof(float) * (size_t)kpad16 * lw.cout_pad64);
@@ -485,7 +583,7 @@ jde_status load_weights(jde_handle* h, const void* blob, size_t nbytes) {
       return fail(h, JDE_ERR_OOM, "weights of layer %zu", l);
     }
     cudaMemset(lw.bias, 0, sizeof(float) * bias_len);
-    h->weight_bytes += layer_weight_bytes(L[l], bf16, (int)l);
+    h->weight_bytes += layer_weight_bytes(L[l], h->cfg.precision, (int)l);
     const float* base = reinterpret_cast<const float*>(static_cast<uint8_t*>(dblob) + offs[l]);
     const size_t nw = (size_t)L[l].cout * L[l].cin * L[l].k * L[l].k;
     const float* W = base;
@@ -504,7 +602,17 @@ jde_status load_weights(jde_handle* h, const void* blob, size_t nbytes) {
     jde_count_launch();
     pack_kernel<<<(unsigned)((total + 255) / 256), 256>>>(
         W, gamma, beta, mean, var, bias, L[l].cin, L[l].cout, L[l].k, K, bf16 ? 0 : kpad16, bf16 ? 0 : lw.cout_pad64,
-        lw.w_kn, bf16 ? lw.cout_pad_tc : 0, bf16 ? lw.k_tc : 0, lw.w_nk, lw.bias, bias_len);
+        lw.w_kn, bf16 ? lw.cout_pad_tc : 0, bf16 ? lw.k_tc : 0, lw.w_nk, lw.bias, bias_len);   // E4M3 layers:
+                                                                                           // bias only (w_nk NULL)
+    if (lw.q) {
+      jde_count_launch(2);
+      wscale_kernel<<<lw.cout_pad_tc, 256>>>(W, gamma, var, L[l].cin, L[l].cout, L[l].k, lw.wscale, lw.cout_pad_tc);
+      const long long nq = (long long)lw.cout_pad_tc * lw.k_tc;
+      pack_q_kernel<<<(unsigned)((nq + 255) / 256), 256>>>(W, gamma, var, L[l].cin, L[l].cout, L[l].k, lw.wscale,
+                                                            lw.w_q, lw.cout_pad_tc, lw.k_tc);
+      lw.wscale_host.resize(lw.cout_pad_tc);
+      CUDA_OR(h, cudaMemcpy(lw.wscale_host.data(), lw.wscale, sizeof(double) * lw.cout_pad_tc, cudaMemcpyDeviceToHost));
+    }
   }
   cudaError_t e = cudaDeviceSynchronize();
   cudaFree(dblob);
@@ -558,8 +666,37 @@ __global__ void gather_view_kernel(TView v, void* dst, int el) {
   const size_t o = tview_off(v, n, y, x) + c;
   if (el == 4)
     static_cast<float*>(dst)[idx] = static_cast<const float*>(v.ptr)[o];
-  else
+  else if (el == 2)
     static_cast<__nv_bfloat16*>(dst)[idx] = static_cast<const __nv_bfloat16*>(v.ptr)[o];
+  else
+    static_cast<uint8_t*>(dst)[idx] = static_cast<const uint8_t*>(v.ptr)[o];
+}
+
+// max |value| of a tensor view (E4M3 codes times `scale`), folded into *out with an integer max
+// (non-negative floats order like their bit patterns).
+__global__ void amax_kernel(TView v, float scale, float* out) {
+  const long long total = (long long)v.n * v.h * v.w * v.c;
+  float m = 0.f;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(idx % v.c);
+    long long p = idx / v.c;
+    const int x = (int)(p % v.w);
+    p /= v.w;
+    const int y = (int)(p % v.h);
+    const int n = (int)(p / v.h);
+    const size_t o = tview_off(v, n, y, x) + c;
+    float a;
+    if (v.dtype == 0)
+      a = static_cast<const float*>(v.ptr)[o];
+    else if (v.dtype == 1)
+      a = __bfloat162float(static_cast<const __nv_bfloat16*>(v.ptr)[o]);
+    else
+      a = e4m3x2_to_float2(static_cast<const uint8_t*>(v.ptr)[o]).x * scale;
+    m = fmaxf(m, fabsf(a));
+  }
+  for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int*>(out), __float_as_int(m));
 }
 
 }  // namespace
@@ -605,8 +742,12 @@ void jde_destroy(jde_handle* h) {
   for (auto& lw : h->w) {
     cudaFree(lw.w_kn);
     cudaFree(lw.w_nk);
+    cudaFree(lw.w_q);
+    cudaFree(lw.wscale);
+    cudaFree(lw.mult);
     cudaFree(lw.bias);
   }
+  cudaFree(h->d_amax);
   for (auto& kv : h->res)
     for (void* p : kv.second.mem)
       if (p) cudaFree(p);
@@ -624,7 +765,7 @@ jde_status jde_create(const jde_config* cfg, const void* weights, size_t nbytes,
   *out = nullptr;
   if (!cfg) return fail(nullptr, JDE_ERR_INVALID_ARG, "cfg is NULL");
   const jde_config& c = *cfg;
-  if (c.precision != JDE_FP32 && c.precision != JDE_BF16)
+  if (c.precision != JDE_FP32 && c.precision != JDE_BF16 && c.precision != JDE_FP8_E4M3)
     return fail(nullptr, JDE_ERR_UNSUPPORTED, "precision %d not supported", c.precision);
   if (c.max_batch < 1 || c.max_in_w < 32 || c.max_in_h < 32 || c.max_in_w % 32 || c.max_in_h % 32 ||
       c.max_src_w < 1 || c.max_src_h < 1 || c.max_cand < 64 || c.max_cand > 4096 || c.max_cand % 64 ||
@@ -660,6 +801,8 @@ jde_status jde_forward(jde_handle* h, const uint8_t* frames, int n, int src_w, i
       in_w > h->cfg.max_in_w || in_h > h->cfg.max_in_h || src_w < 1 || src_h < 1)
     return fail(h, JDE_ERR_INVALID_ARG, "jde_forward: bad arguments (n=%d in=%dx%d src=%dx%d)", n, in_w, in_h, src_w,
                 src_h);
+  if (h->cfg.precision == JDE_FP8_E4M3 && !h->scales_set)
+    return fail(h, JDE_ERR_INVALID_ARG, "jde_forward: E4M3 handle has no activation scales (call jde_set_act_amax)");
   const size_t fbytes = (size_t)n * src_w * src_h * 3;
   if (!on_device) {
     if (fbytes > h->frames_cap) {
@@ -686,7 +829,7 @@ jde_status jde_forward(jde_handle* h, const uint8_t* frames, int n, int src_w, i
     memcpy(h->lb_key, key, sizeof(key));
   }
   const TView lb = view_of(*rb, T_LB, n);
-  const bool bf16 = h->cfg.precision == JDE_BF16;
+  const bool bf16 = h->cfg.precision != JDE_FP32;   // tensor-core path (BF16 / E4M3)
   if (h->prof[0]) cudaEventRecord(h->prof[0], st);
   if (bf16) {
     letterbox_bf16x4_launch(frames, n, src_w, src_h, h->lb_x, h->lb_y, lb, st);
@@ -845,12 +988,59 @@ jde_status jde_get_tensor(jde_handle* h, int id, void* dst, size_t dst_bytes, in
   }
   if (dtype) *dtype = v.dtype;
   if (!dst) return JDE_OK;
-  const int el = v.dtype ? 2 : 4;
+  const int el = el_size(v.dtype);
   const long long total = (long long)v.n * v.h * v.w * v.c;
   if ((size_t)total * el > dst_bytes) return fail(h, JDE_ERR_CAPACITY, "jde_get_tensor: dst too small");
   (jde_count_launch(), gather_view_kernel<<<(unsigned)((total + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(v, dst, el));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(h, JDE_ERR_CUDA, "gather: %s", cudaGetErrorString(e));
+  return JDE_OK;
+}
+
+jde_status jde_set_act_amax(jde_handle* h, const float* amax, int n) {
+  if (!h) return fail(nullptr, JDE_ERR_INVALID_ARG, "handle is NULL");
+  if (h->cfg.precision != JDE_FP8_E4M3)
+    return fail(h, JDE_ERR_INVALID_ARG, "jde_set_act_amax: only E4M3 handles take activation scales");
+  if (!amax || n != JDE_NUM_LAYERS) return fail(h, JDE_ERR_INVALID_ARG, "jde_set_act_amax: need %d values", JDE_NUM_LAYERS);
+  for (int l = 0; l < n; ++l)
+    if (!(amax[l] >= 0.f) || !isfinite(amax[l]))
+      return fail(h, JDE_ERR_INVALID_ARG, "jde_set_act_amax: amax[%d] = %g", l, (double)amax[l]);
+  // scale of a stored tensor = amax / 448; a concat buffer takes the larger amax of its writers
+  std::vector<float> bmax(T_COUNT, 0.f);
+  for (int l = 0; l < n; ++l) {
+    const int b = buffer_of(h, l);
+    bmax[b] = fmaxf(bmax[b], amax[l]);
+  }
+  for (int t = 0; t < T_COUNT; ++t) h->act_scale[t] = (bmax[t] > 0.f ? bmax[t] : 1.0f) / 448.0f;
+  for (int l = 0; l < n; ++l) {
+    LayerW& lw = h->w[l];
+    if (!lw.q) continue;
+    const float s_in = h->act_scale[buffer_of(h, h->io[l].in)];
+    std::vector<float> m(lw.cout_pad_tc);
+    for (int co = 0; co < lw.cout_pad_tc; ++co) m[co] = (float)((double)s_in * lw.wscale_host[co]);
+    CUDA_OR(h, cudaMemcpy(lw.mult, m.data(), sizeof(float) * m.size(), cudaMemcpyHostToDevice));
+  }
+  h->plans.clear();   // plans carry the scales
+  h->scales_set = true;
+  return JDE_OK;
+}
+
+jde_status jde_act_amax(jde_handle* h, float* amax, void* stream) {
+  if (!h) return fail(nullptr, JDE_ERR_INVALID_ARG, "handle is NULL");
+  if (!amax) return fail(h, JDE_ERR_INVALID_ARG, "jde_act_amax: amax is NULL");
+  if (!h->cur) return fail(h, JDE_ERR_INVALID_ARG, "jde_act_amax: no forward has run");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!h->d_amax && !dmalloc((void**)&h->d_amax, sizeof(float) * JDE_NUM_LAYERS))
+    return fail(h, JDE_ERR_OOM, "amax scratch");
+  CUDA_OR(h, cudaMemsetAsync(h->d_amax, 0, sizeof(float) * JDE_NUM_LAYERS, st));
+  for (int l = 0; l < JDE_NUM_LAYERS; ++l) {
+    TView v = view_of(*h->cur, l, h->cur_n);
+    if (h->io[l].head >= 0) v.ptr = static_cast<char*>(v.ptr) + (size_t)h->cur_set * h->cur->set_bytes[l];
+    jde_count_launch();
+    amax_kernel<<<152, 256, 0, st>>>(v, h->act_scale[buffer_of(h, l)], h->d_amax + l);
+  }
+  CUDA_OR(h, cudaMemcpyAsync(amax, h->d_amax, sizeof(float) * JDE_NUM_LAYERS, cudaMemcpyDeviceToHost, st));
+  CUDA_OR(h, cudaStreamSynchronize(st));
   return JDE_OK;
 }
 
@@ -875,10 +1065,10 @@ jde_status jde_estimate_device_bytes(const jde_config* cfg, int in_w, int in_h, 
   jde_handle tmp;
   tmp.cfg = *cfg;
   tmp.io = build_io();
-  const bool bf16 = cfg->precision == JDE_BF16;
+  const bool bf16 = cfg->precision != JDE_FP32;
   const auto& L = layers();
   size_t b = sizeof(int) + sizeof(LbAxis) * (size_t)(cfg->max_in_w + cfg->max_in_h);
-  for (size_t l = 0; l < L.size(); ++l) b += layer_weight_bytes(L[l], bf16, (int)l);
+  for (size_t l = 0; l < L.size(); ++l) b += layer_weight_bytes(L[l], cfg->precision, (int)l);
   std::vector<TensorDesc> td;
   tensor_desc_table(&tmp, in_w, in_h, td);
   for (int t = 0; t < T_COUNT; ++t) {

@@ -19,7 +19,7 @@ if not os.path.exists(_LIB_PATH):
 lib = C.CDLL(_LIB_PATH)
 
 JDE_OK = 0
-JDE_FP32, JDE_BF16 = 0, 1
+JDE_FP32, JDE_BF16, JDE_FP8_E4M3 = 0, 1, 2
 JDE_TRACK_TRACKED, JDE_TRACK_LOST = 1, 2
 JDE_ROW, JDE_EMB, JDE_NUM_LAYERS = 518, 512, 78
 STATUS = {0: "JDE_OK", 1: "JDE_ERR_INVALID_ARG", 2: "JDE_ERR_OOM", 3: "JDE_ERR_CUDA", 4: "JDE_ERR_CAPACITY",
@@ -65,6 +65,8 @@ _sig = {
     "jde_stream_reset": (C.c_int, [_P, C.c_int, _P]),
     "jde_get_tensor": (C.c_int, [_P, C.c_int, _P, C.c_size_t, C.POINTER(C.c_int), C.POINTER(C.c_int), _P]),
     "jde_kernel_errors": (C.c_int, [_P, C.POINTER(C.c_int), _P]),
+    "jde_set_act_amax": (C.c_int, [_P, C.POINTER(C.c_float), C.c_int]),
+    "jde_act_amax": (C.c_int, [_P, C.POINTER(C.c_float), _P]),
     "jde_device_bytes": (C.c_int, [_P, C.POINTER(C.c_size_t)]),
     "jde_estimate_device_bytes": (C.c_int, [C.POINTER(jde_config), C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
     "jde_launch_count": (C.c_ulonglong, []),
@@ -194,6 +196,18 @@ def jde_kernel_errors(h, stream=None) -> int:
     w = C.c_int()
     _check(h, lib.jde_kernel_errors(h, C.byref(w), stream_ptr(stream)))
     return w.value
+
+
+def jde_set_act_amax(h, amax) -> None:
+    arr = (C.c_float * len(amax))(*[float(v) for v in amax])
+    _check(h, lib.jde_set_act_amax(h, arr, len(amax)))
+
+
+def jde_act_amax(h, stream=None):
+    n = lib.jde_layer_table(None, 0)
+    arr = (C.c_float * n)()
+    _check(h, lib.jde_act_amax(h, arr, stream_ptr(stream)))
+    return [float(v) for v in arr]
 
 
 def jde_device_bytes(h) -> int:

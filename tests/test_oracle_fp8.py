@@ -106,3 +106,28 @@ def test_fake_quant_stores_fp8_values_and_keeps_heads_float():
             np.testing.assert_array_equal(fp8.e4m3(a / s[l]) * s[l], a)   # on the tensor's FP8 grid
     for l in range(fp8.FIRST_FP8_OUTPUT):
         assert not np.array_equal(fp8.e4m3(acts[l] / (amax[l] / 448)) * (amax[l] / 448), acts[l])
+
+
+def test_layer_io_replays_the_forward_layer_by_layer():
+    """The wiring table drives a layer-by-layer replay that reproduces forward(keep_all) exactly."""
+    layers = synth.parse_blob(synth.weights_blob(net.layer_specs()))
+    x = net.letterbox(synth.frames_uniform(8, 1, 1080, 1920), 64, 64)
+    _, _, acts = net.forward(x, layers, keep_all=True)
+    io = net.layer_io()
+    assert len(io) == 78
+    outs = []
+    for l, (inp, res) in enumerate(io):
+        if inp == -1:
+            xin = x
+        elif isinstance(inp, tuple):
+            xin = np.concatenate([net.upsample2(outs[inp[1]]), outs[inp[2]]], axis=3)
+        else:
+            xin = outs[inp]
+        w, b = net.fold_bn(layers[l])
+        y = net.conv2d(xin, w, b, layers[l]["stride"])
+        if layers[l]["flags"] & 1:
+            y = net.leaky(y)
+        if res is not None:
+            y = outs[res] + y
+        outs.append(y)
+        np.testing.assert_array_equal(y, acts[l])
