@@ -35,6 +35,9 @@ SRC_W, SRC_H = 1920, 1080
 IN_W, IN_H = 1088, 608
 STRIDES = (32, 16, 8)
 METRIC = "JDE FPS at 1088x608: BF16/FP8 batched vs FP32 plain on one GB300; p99 latency"
+# DRAM bytes of the 78 conv launches of one BF16 batch-16 step, from one ncu capture of this build
+# (profiles/dram_bf16_b16_1088x608.md); must be re-taken (or set to None) when the conv kernels change
+CONV_DRAM_BYTES_PER_STEP = 10.119e9
 
 
 def parse():
@@ -51,6 +54,7 @@ def parse():
     p.add_argument("--serve-seconds", type=float, default=20.0,
                    help="serving run: seconds of Poisson arrivals measured after a 2 s warm-up (0: skip)")
     p.add_argument("--serve-budget-gb", type=float, default=64.0, help="serving run: device memory budget")
+    p.add_argument("--no-fp8", action="store_true", help="skip the E4M3 batch-32 line")
     return p.parse_args()
 
 
@@ -187,6 +191,78 @@ def build_heads_device(torch, clips, t, device):
                 xs = torch.tensor([e[2] for e in ee], device=device)
                 embs[s][b][ys, xs] = torch.from_numpy(np.stack([e[3] for e in ee])).to(device)
     return dets + embs
+
+
+def run_fp8(torch, jde, dev, blob, h_bf16, stream, table, B=32, K=20):
+    """E4M3 network at 1088x608, batch 32: activation amax from 64 seeded calibration frames run through
+    the BF16 handle (jde_act_amax, elementwise max over 4 batches of 16), then letterbox + forward +
+    decode + confidence filter + NMS (jde_detect_batch) captured in one CUDA graph and replayed."""
+    import synth
+    amax = None
+    for i in range(4):
+        cal = torch.from_numpy(synth.frames_uniform(1000 + i, 16, SRC_H, SRC_W)).to(dev)
+        jde.jde_forward(h_bf16, cal, 16, SRC_W, SRC_H, IN_W, IN_H, True, stream)
+        a = jde.jde_act_amax(h_bf16, stream)
+        amax = a if amax is None else [max(u, v) for u, v in zip(amax, a)]
+        del cal
+    cfg = jde.jde_default_config()
+    cfg.precision = jde.JDE_FP8_E4M3
+    cfg.max_batch = B
+    cfg.max_streams = 1
+    cfg.device = dev.index or 0
+    h8 = jde.jde_create(cfg, blob)
+    jde.jde_set_act_amax(h8, amax)
+    frames = [torch.from_numpy(synth.frames_uniform(2000 + i, B, SRC_H, SRC_W)).to(dev) for i in range(2)]
+    cap = 256
+    rows = torch.zeros((B, cap, 518), dtype=torch.float32, device=dev)
+    count = torch.zeros(B, dtype=torch.int32, device=dev)
+    dets = jde.make_dets(rows, count, None, cap=cap)
+    gs = torch.cuda.Stream(device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for e in ev:
+        e.record(gs)
+    with torch.cuda.stream(gs):
+        for t in range(3):           # first calls allocate; the captured calls then allocate nothing
+            jde.jde_detect_batch(h8, frames[t % 2], B, SRC_W, SRC_H, IN_W, IN_H, dets, True, gs)
+        # conv phase, eager, for the roofline
+        jde.jde_set_profile_events(h8, *ev)
+        jde.jde_forward(h8, frames[0], B, SRC_W, SRC_H, IN_W, IN_H, True, gs)
+        jde.jde_set_profile_events(h8, None, None, None)
+    torch.cuda.synchronize()
+    conv_ms = ev[1].elapsed_time(ev[2])
+    graphs = []
+    for i in range(2):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=gs):
+            jde.jde_detect_batch(h8, frames[i], B, SRC_W, SRC_H, IN_W, IN_H, dets, True, gs)
+        graphs.append(g)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(gs):
+        for i in range(3):
+            graphs[i % 2].replay()
+        torch.cuda.synchronize()
+        l0 = jde.jde_launch_count()
+        e0.record(gs)
+        for i in range(K):
+            graphs[i % 2].replay()
+        e1.record(gs)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    assert jde.jde_kernel_errors(h8) == 0
+    n_dets = int(count.sum())
+    jde.jde_destroy(h8)
+    flops = conv_flops(table, IN_W, IN_H) * B
+    peaks, kind = measured_peaks()
+    peak8 = 2.0 * peaks["bf16_tflops_sustained"]
+    achieved = flops / (conv_ms * 1e-3) / 1e12
+    return {"fps": B * 1000.0 / ms, "ms_per_batch": ms, "batch": B, "steps": K, "graph": True,
+            "what": "letterbox + E4M3 forward + decode + confidence filter + NMS + embedding L2, one CUDA graph "
+                    "per batch (two graphs over two resident frame batches)",
+            "calibration": "amax per layer output: 64 seeded 1920x1080 uniform frames through the BF16 handle",
+            "conv_ms": conv_ms, "conv_tflops": achieved,
+            "fp8_peak_tflops": peak8, "conv_frac_of_fp8_peak": achieved / peak8 if peak8 else None,
+            "peak_note": "E4M3 peak = 2 x measured BF16 sustained (nominal dense ratio 4.5/2.25)",
+            "detections_last_batch": n_dets, "launch_count_note": "graph replays; library launches are inside graphs"}
 
 
 def run_serving(torch, jde, dev, blob, seconds, budget_gb, n_streams=16, warm_s=2.0):
@@ -457,7 +533,9 @@ def main():
     achieved = flops_frame * B * K / (conv_ms / 1000.0) / 1e12
     peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "conv_tc_kernel (78 launches per step, aggregated)",
+                "traffic": CONV_DRAM_BYTES_PER_STEP if B == 16 else None,
+                "traffic_unit": "bytes per step (78 launches), ncu dram__bytes_read.sum + dram__bytes_write.sum",
+                "kernel": "conv_tc_kernel (78 launches per step, aggregated)",
                 "peak_kind": f"{peak_kind} bf16 sustained"}
 
     # e2e: host frames in (pinned), tracks out to host, through the same C ABI
@@ -521,6 +599,10 @@ def main():
         fp32 = {"fps": 1000.0 / ms32, "ms_per_frame": ms32, "steps": n32, "batch": 1, "graph": False}
         jde.jde_destroy(h32)
 
+    fp8 = None
+    if not args.no_fp8 and rank == 0:
+        fp8 = run_fp8(torch, jde, dev, blob, h, F, table)
+
     serving = None
     if args.serve_seconds > 0 and rank == 0:
         serving = run_serving(torch, jde, dev, blob, args.serve_seconds, args.serve_budget_gb)
@@ -547,6 +629,7 @@ def main():
             "stages_ms_per_step": {"forward": fwd_ms / K, "convs": conv_ms / K},
             "fp32_plain_batch1": fp32,
             "batch_sweep": sweep,
+            "fp8_batch32": fp8,
             "serving": serving,
             "roofline": roofline,
             "cpu_baseline": cpu,
