@@ -35,8 +35,8 @@ SRC_W, SRC_H = 1920, 1080
 IN_W, IN_H = 1088, 608
 STRIDES = (32, 16, 8)
 METRIC = "JDE FPS at 1088x608: BF16/FP8 batched vs FP32 plain on one GB300; p99 latency"
-# DRAM bytes of the 78 conv launches of one BF16 batch-16 step, from one ncu capture of this build
-# (profiles/dram_bf16_b16_1088x608.md); must be re-taken (or set to None) when the conv kernels change
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the 78 conv launches of one BF16
+# batch-16 step, from one ncu capture of this build; re-take it (or set None) when the conv kernels change
 CONV_DRAM_BYTES_PER_STEP = 10.119e9
 
 
