@@ -55,6 +55,7 @@ def parse():
                    help="serving run: seconds of Poisson arrivals measured after a 2 s warm-up (0: skip)")
     p.add_argument("--serve-budget-gb", type=float, default=64.0, help="serving run: device memory budget")
     p.add_argument("--no-fp8", action="store_true", help="skip the E4M3 batch-32 line")
+    p.add_argument("--no-autotune", action="store_true", help="default tile rule instead of jde_autotune")
     return p.parse_args()
 
 
@@ -193,7 +194,7 @@ def build_heads_device(torch, clips, t, device):
     return dets + embs
 
 
-def run_fp8(torch, jde, dev, blob, h_bf16, stream, table, B=32, K=20):
+def run_fp8(torch, jde, dev, blob, h_bf16, stream, table, B=32, K=20, autotune=True):
     """E4M3 network at 1088x608, batch 32: activation amax from 64 seeded calibration frames run through
     the BF16 handle (jde_act_amax, elementwise max over 4 batches of 16), then letterbox + forward +
     decode + confidence filter + NMS (jde_detect_batch) captured in one CUDA graph and replayed."""
@@ -212,6 +213,11 @@ def run_fp8(torch, jde, dev, blob, h_bf16, stream, table, B=32, K=20):
     cfg.device = dev.index or 0
     h8 = jde.jde_create(cfg, blob)
     jde.jde_set_act_amax(h8, amax)
+    changed = None
+    if autotune:
+        d0 = jde.jde_tile_choice(h8, B, IN_W, IN_H)
+        jde.jde_autotune(h8, B, IN_W, IN_H, stream)
+        changed = sum(a != b for a, b in zip(d0, jde.jde_tile_choice(h8, B, IN_W, IN_H)))
     frames = [torch.from_numpy(synth.frames_uniform(2000 + i, B, SRC_H, SRC_W)).to(dev) for i in range(2)]
     cap = 256
     rows = torch.zeros((B, cap, 518), dtype=torch.float32, device=dev)
@@ -256,6 +262,7 @@ def run_fp8(torch, jde, dev, blob, h_bf16, stream, table, B=32, K=20):
     peak8 = 2.0 * peaks["bf16_tflops_sustained"]
     achieved = flops / (conv_ms * 1e-3) / 1e12
     return {"fps": B * 1000.0 / ms, "ms_per_batch": ms, "batch": B, "steps": K, "graph": True,
+            "autotuned_tiles_changed": changed,
             "what": "letterbox + E4M3 forward + decode + confidence filter + NMS + embedding L2, one CUDA graph "
                     "per batch (two graphs over two resident frame batches)",
             "calibration": "amax per layer output: 64 seeded 1920x1080 uniform frames through the BF16 handle",
@@ -376,6 +383,13 @@ def main():
     cfg.device = local
     h = jde.jde_create(cfg, blob)
     st = torch.cuda.current_stream()
+    tiles = None
+    if not args.no_autotune:
+        default_bn = jde.jde_tile_choice(h, B, IN_W, IN_H)
+        jde.jde_autotune(h, B, IN_W, IN_H, st)
+        tuned_bn = jde.jde_tile_choice(h, B, IN_W, IN_H)
+        tiles = {"autotuned": True, "changed_layers": sum(a != b for a, b in zip(default_bn, tuned_bn)),
+                 "bn": tuned_bn}
 
     # inputs resident in HBM: 4 distinct batches of frames, planted heads for every step
     NF = 4
@@ -601,7 +615,7 @@ def main():
 
     fp8 = None
     if not args.no_fp8 and rank == 0:
-        fp8 = run_fp8(torch, jde, dev, blob, h, F, table)
+        fp8 = run_fp8(torch, jde, dev, blob, h, F, table, autotune=not args.no_autotune)
 
     serving = None
     if args.serve_seconds > 0 and rank == 0:
@@ -630,6 +644,7 @@ def main():
             "fp32_plain_batch1": fp32,
             "batch_sweep": sweep,
             "fp8_batch32": fp8,
+            "tiles": tiles,
             "serving": serving,
             "roofline": roofline,
             "cpu_baseline": cpu,

@@ -208,6 +208,19 @@ jde_status jde_set_act_amax(jde_handle* h, const float* amax, int n);
  * E4M3 tensors as code times scale. */
 jde_status jde_act_amax(jde_handle* h, float* amax, void* stream);
 
+/* Tile autotuner (tensor-core handles): for batches of n frames at in_w x in_h, times every
+ * built tile width (64/128/256 output channels, 32 where that is the default; 256 runs on CTA
+ * pairs) of every convolution that has more than one, on `stream` with CUDA events over three launches on the handle's
+ * activation buffers, and keeps the fastest for later forwards of that shape.  Results do not
+ * change: every tile computes each output with the same K order.  Synchronises `stream`;
+ * overwrites intermediate activations (the next forward recomputes them).  E4M3 handles need
+ * their scales first. */
+jde_status jde_autotune(jde_handle* h, int n, int in_w, int in_h, void* stream);
+
+/* Tile width used per layer (bn[JDE_NUM_LAYERS]) for batches of n at in_w x in_h: the tuned
+ * choice if jde_autotune ran for that shape, else the default rule. */
+jde_status jde_tile_choice(jde_handle* h, int n, int in_w, int in_h, int* bn);
+
 /* Device memory the handle holds now (weights, activation buffers of every
  * input size used so far, post-processing and tracker state, staging), in bytes. */
 jde_status jde_device_bytes(jde_handle* h, size_t* out);

@@ -165,6 +165,8 @@ struct jde_handle {
   std::vector<float> act_scale = std::vector<float>(T_COUNT, 1.0f);
   bool scales_set = false;
   float* d_amax = nullptr;   // jde_act_amax scratch [JDE_NUM_LAYERS]
+  // jde_autotune: tile width per layer for (in_w, in_h, n); 0 = the default rule
+  std::map<std::tuple<int, int, int>, std::vector<int>> tuned_bn;
 };
 
 namespace {
@@ -405,7 +407,10 @@ jde_status get_plan(jde_handle* h, ResBuffers* rb, int n, Plan** out) {
     if (bf16) {
       char msg[256];
       const void* w = c.q ? static_cast<const void*>(h->w[l].w_q) : static_cast<const void*>(h->w[l].w_nk);
-      if (!conv_tc_plan(p.tc[l], c, w, h->w[l].cout_pad_tc, h->w[l].bn, msg, sizeof(msg)))
+      int bn = h->w[l].bn;
+      auto tb = h->tuned_bn.find(key);
+      if (tb != h->tuned_bn.end() && tb->second[l] > 0) bn = tb->second[l];
+      if (!conv_tc_plan(p.tc[l], c, w, h->w[l].cout_pad_tc, bn, msg, sizeof(msg)))
         return fail(h, JDE_ERR_UNSUPPORTED, "layer %zu: %s", l, msg);
     }
   }
@@ -1041,6 +1046,71 @@ jde_status jde_act_amax(jde_handle* h, float* amax, void* stream) {
   }
   CUDA_OR(h, cudaMemcpyAsync(amax, h->d_amax, sizeof(float) * JDE_NUM_LAYERS, cudaMemcpyDeviceToHost, st));
   CUDA_OR(h, cudaStreamSynchronize(st));
+  return JDE_OK;
+}
+
+jde_status jde_autotune(jde_handle* h, int n, int in_w, int in_h, void* stream) {
+  if (!h) return fail(nullptr, JDE_ERR_INVALID_ARG, "handle is NULL");
+  if (h->cfg.precision == JDE_FP32) return fail(h, JDE_ERR_UNSUPPORTED, "jde_autotune: tensor-core handles only");
+  if (n < 1 || n > h->cfg.max_batch || in_w % 32 || in_h % 32 || in_w < 32 || in_h < 32 || in_w > h->cfg.max_in_w ||
+      in_h > h->cfg.max_in_h)
+    return fail(h, JDE_ERR_INVALID_ARG, "jde_autotune: bad arguments");
+  if (h->cfg.precision == JDE_FP8_E4M3 && !h->scales_set)
+    return fail(h, JDE_ERR_INVALID_ARG, "jde_autotune: E4M3 handle has no activation scales");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ResBuffers* rb;
+  jde_status s = get_res(h, in_w, in_h, &rb);
+  if (s != JDE_OK) return s;
+  const auto key = std::make_tuple(in_w, in_h, n);
+  h->tuned_bn.erase(key);
+  h->plans.erase(key);
+  Plan* plan;
+  s = get_plan(h, rb, n, &plan);
+  if (s != JDE_OK) return s;
+  std::vector<int> best(JDE_NUM_LAYERS, 0);
+  cudaEvent_t e0, e1;
+  CUDA_OR(h, cudaEventCreate(&e0));
+  CUDA_OR(h, cudaEventCreate(&e1));
+  for (int l = 0; l < JDE_NUM_LAYERS; ++l) {
+    const TcPlan& def = plan->tc[l];
+    if (def.mode == 2 || def.mode == 3) continue;    // stem and window convs have one tile shape
+    const LayerW& lw = h->w[l];
+    const void* w = lw.q ? static_cast<const void*>(lw.w_q) : static_cast<const void*>(lw.w_nk);
+    float best_ms = 1e30f;
+    for (int bn : {32, 64, 128, 256}) {
+      // 32-wide tiles only where they are the default (the 24-channel heads, 32-channel outputs)
+      if (lw.cout_pad_tc % bn || (bn == 32 && lw.bn != 32)) continue;
+      TcPlan cand;
+      char msg[256];
+      if (!conv_tc_plan(cand, plan->specs[l], w, lw.cout_pad_tc, bn, msg, sizeof(msg))) continue;
+      if (conv_tc_launch(cand, st) != cudaSuccess) {   // shape without a built configuration
+        cudaGetLastError();
+        continue;
+      }
+      CUDA_OR(h, cudaEventRecord(e0, st));
+      for (int r = 0; r < 3; ++r) CUDA_OR(h, conv_tc_launch(cand, st));
+      CUDA_OR(h, cudaEventRecord(e1, st));
+      CUDA_OR(h, cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CUDA_OR(h, cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best_ms) {
+        best_ms = ms;
+        best[l] = bn;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->tuned_bn[key] = best;
+  h->plans.erase(key);   // rebuilt with the chosen tiles on the next forward
+  return JDE_OK;
+}
+
+jde_status jde_tile_choice(jde_handle* h, int n, int in_w, int in_h, int* bn) {
+  if (!h || !bn) return fail(h, JDE_ERR_INVALID_ARG, "jde_tile_choice: NULL argument");
+  auto tb = h->tuned_bn.find(std::make_tuple(in_w, in_h, n));
+  for (int l = 0; l < JDE_NUM_LAYERS; ++l)
+    bn[l] = (tb != h->tuned_bn.end() && tb->second[l] > 0) ? tb->second[l] : h->w[l].bn;
   return JDE_OK;
 }
 

@@ -65,6 +65,8 @@ _sig = {
     "jde_stream_reset": (C.c_int, [_P, C.c_int, _P]),
     "jde_get_tensor": (C.c_int, [_P, C.c_int, _P, C.c_size_t, C.POINTER(C.c_int), C.POINTER(C.c_int), _P]),
     "jde_kernel_errors": (C.c_int, [_P, C.POINTER(C.c_int), _P]),
+    "jde_autotune": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P]),
+    "jde_tile_choice": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]),
     "jde_set_act_amax": (C.c_int, [_P, C.POINTER(C.c_float), C.c_int]),
     "jde_act_amax": (C.c_int, [_P, C.POINTER(C.c_float), _P]),
     "jde_device_bytes": (C.c_int, [_P, C.POINTER(C.c_size_t)]),
@@ -196,6 +198,17 @@ def jde_kernel_errors(h, stream=None) -> int:
     w = C.c_int()
     _check(h, lib.jde_kernel_errors(h, C.byref(w), stream_ptr(stream)))
     return w.value
+
+
+def jde_autotune(h, n, in_w, in_h, stream=None) -> None:
+    _check(h, lib.jde_autotune(h, n, in_w, in_h, stream_ptr(stream)))
+
+
+def jde_tile_choice(h, n, in_w, in_h):
+    k = lib.jde_layer_table(None, 0)
+    arr = (C.c_int * k)()
+    _check(h, lib.jde_tile_choice(h, n, in_w, in_h, arr))
+    return list(arr)
 
 
 def jde_set_act_amax(h, amax) -> None:
