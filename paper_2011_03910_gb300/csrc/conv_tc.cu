@@ -34,8 +34,8 @@ struct TcArgs {
   int TW, TH, tiles_x, tiles_y, n_tiles, total_tiles;
   int tma_out, tma_res;
   int stride, WW, WH, win_bytes;   // mode 3: window (or parity sub-window) size in pixels, bytes per buffer
-  int plane;                       // mode 3: stride between 8-channel planes (128-byte aligned: TMA destinations)
-  int plane_tx;                    // mode 3: bytes one plane load delivers (WW * WH * 16)
+  int plane;                       // mode 3: bytes between (parity) windows of one buffer (1024-aligned)
+  int plane_tx;                    // mode 3: bytes one window load delivers (WW * WH * 64)
   int nwin;                        // mode 3: window buffers in the ring (2 .. MAX_WIN)
   int total_units;                 // work units: tiles, or (CTA pairs) pairs of M tiles x N tiles
   int kel;                         // elements of one k-block along K (E4M3: twice the bf16 count, same bytes)
@@ -44,8 +44,9 @@ struct TcArgs {
 
 // Modes: 0 flat stride-1 (TMA per tap), 1 stride-2 patch (TMA per tap from parity maps),
 // 2 stem (im2col gathered from the letterbox), 3 32-channel 3x3: the input window of an
-// 8x16 output patch is loaded once as four 8-channel planes, which is the no-swizzle K-major
-// operand layout, so each tap is the same window at another descriptor start; weights resident.
+// 8x16 output patch (stride 2: its four parity sub-windows) is loaded once, 64 bytes per pixel
+// with the 64-byte swizzle; the MMAs apply the swizzle to absolute shared-memory addresses, so
+// each tap is the same window at another descriptor start (pixel offset); weights resident.
 __device__ __forceinline__ bool patch_mode(int mode) { return mode == 1 || mode == 3; }
 
 // warp 0: TMA producer; warp 1: MMA issuer + TMEM owner; warps 2..9: epilogue in two
@@ -342,16 +343,14 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
           break;
         }
         const TileCoord tc = tile_coord(a, tile, BN);
-        if ((smem_u32(sWin + wb * a.win_bytes) | (uint32_t)a.plane) & 127u) {   // TMA destinations: 128-B aligned
+        if ((smem_u32(sWin + wb * a.win_bytes) | (uint32_t)a.plane) & 1023u) {   // swizzled TMA destinations
           flag_error(c.err, KERR_TIMEOUT);
           atomicExch(&s_abort, 1);
           break;
         }
-        mbar_expect_tx(&win_full[wb], (uint32_t)(npar * 4 * a.plane_tx));
+        mbar_expect_tx(&win_full[wb], (uint32_t)(npar * a.plane_tx));
         for (int par = 0; par < npar; ++par)
-          for (int j = 0; j < 4; ++j)
-            tma_load_5d(sWin + wb * a.win_bytes + (par * 4 + j) * a.plane, &plan.a[par], &win_full[wb], 0, j, tc.ox0,
-                        tc.oy0, tc.img);
+          tma_load_4d(sWin + wb * a.win_bytes + par * a.plane, &plan.a[par], &win_full[wb], 0, tc.ox0, tc.oy0, tc.img);
       }
     }
   } else if (warp == 0 && GW == 1) {
@@ -430,7 +429,7 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
           }
           tc_fence_after();
           const uint32_t win = smem_u32(sWin + wb * a.win_bytes);
-          const uint32_t row_bytes = (uint32_t)a.WW * 16u;
+          const uint32_t row_bytes = (uint32_t)a.WW * 64u;      // 8-row groups: one window row apart
 #pragma unroll 1
           for (int tap = 0; tap < 9; ++tap) {
             const int ky = tap / 3, kx = tap % 3;
@@ -438,8 +437,8 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
             const int pix = a.stride == 2 ? (ky >> 1) * a.WW + (kx >> 1) : ky * a.WW + kx;
 #pragma unroll
             for (int kk = 0; kk < 2; ++kk) {
-              const uint32_t a_addr = win + (uint32_t)((par * 4 + 2 * kk) * a.plane + pix * 16);
-              const uint64_t ad = smem_desc_noswz(a_addr, (uint32_t)a.plane, row_bytes);
+              const uint32_t a_addr = win + (uint32_t)(par * a.plane + pix * 64 + kk * 32);
+              const uint64_t ad = smem_desc(a_addr, row_bytes, 4u);   // 64-byte swizzle
               const int kidx = tap * 32 + kk * 16;          // K index of this MMA's first element
               const uint32_t b_addr = smem_u32(sB + (kidx >> 6) * Cfg::B_BYTES) + (uint32_t)((kidx & 63) * 2);
               const uint64_t bd = smem_desc(b_addr, Cfg::SBO, Cfg::LAYOUT);
@@ -904,8 +903,8 @@ bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const void* w_any, int cout_p
     plan.WW = st == 1 ? plan.TW + 2 : plan.TW + 1;   // (sub-)window width in pixels
     plan.WH = st == 1 ? plan.TH + 2 : plan.TH + 1;
     // every plane is a TMA destination: its shared-memory address must be 128-byte aligned
-    plan.plane = (plan.WW * plan.WH * 16 + 127) / 128 * 128;
-    plan.win_bytes = ((st == 1 ? 4 : 16) * plan.plane + 1023) / 1024 * 1024;
+    plan.plane = (plan.WW * plan.WH * 64 + 1023) / 1024 * 1024;
+    plan.win_bytes = (st == 1 ? 1 : 4) * plan.plane;
     {
       // as many window buffers as shared memory holds next to the resident weights and the two
       // staging tiles (at most MAX_WIN)
@@ -917,7 +916,7 @@ bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const void* w_any, int cout_p
       snprintf(msg, msg_len, "window ring does not fit in shared memory");
       return false;
     }
-    if (plan.plane % 128 || plan.win_bytes % 1024) {
+    if (plan.plane % 1024 || plan.win_bytes % 1024) {
       snprintf(msg, msg_len, "window planes not 128-byte aligned");
       return false;
     }
@@ -927,14 +926,14 @@ bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const void* w_any, int cout_p
     bool ok = true;
     const size_t ps = (size_t)c.in.pixstride;
     for (int par = 0; par < (st == 2 ? 4 : 1); ++par) {
-      // 5-D view (8 channels, 4 channel chunks, x, y, image); stride 2: parity sub-lattice (py, px)
+      // 4-D view (32 channels, x, y, image), 64-byte swizzle; stride 2: parity sub-lattice (py, px)
       const int py = par >> 1, px = par & 1;
       void* base = static_cast<__nv_bfloat16*>(c.in.ptr) + (st == 2 ? ((size_t)py * Wp + px) * ps : 0);
-      cuuint64_t dims[5] = {8, 4, (cuuint64_t)(st == 2 ? Wp / 2 : Wp), (cuuint64_t)(st == 2 ? Hp / 2 : Hp),
+      cuuint64_t dims[4] = {32, (cuuint64_t)(st == 2 ? Wp / 2 : Wp), (cuuint64_t)(st == 2 ? Hp / 2 : Hp),
                             (cuuint64_t)c.in.n};
-      cuuint64_t strides[4] = {16, (cuuint64_t)st * ps * 2, (cuuint64_t)st * Wp * ps * 2, (cuuint64_t)Hp * Wp * ps * 2};
-      cuuint32_t box[5] = {8, 1, (cuuint32_t)plan.WW, (cuuint32_t)plan.WH, 1};
-      ok &= encode(&plan.a[par], 5, base, dims, strides, box, 0);
+      cuuint64_t strides[3] = {(cuuint64_t)st * ps * 2, (cuuint64_t)st * Wp * ps * 2, (cuuint64_t)Hp * Wp * ps * 2};
+      cuuint32_t box[4] = {32, (cuuint32_t)plan.WW, (cuuint32_t)plan.WH, 1};
+      ok &= encode(&plan.a[par], 4, base, dims, strides, box, 32);
     }
     {
       cuuint64_t dims[2] = {320, 64};
@@ -1097,7 +1096,7 @@ cudaError_t conv_tc_launch(const TcPlan& p, cudaStream_t st) {
   a.nwin = p.nwin;
   a.kel = p.kel ? p.kel : p.bkc;
   a.plane = p.plane;
-  a.plane_tx = p.WW * p.WH * 16;
+  a.plane_tx = p.WW * p.WH * 64;
   a.c = p.spec;
   if (p.mode == 2) {
     if (p.bn == 32) return launch_cfg<32, 32, 16, 4>(p, a, st);
