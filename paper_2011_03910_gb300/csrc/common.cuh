@@ -293,6 +293,10 @@ JDE_DEV uint64_t smem_desc(uint32_t saddr, uint32_t sbo_bytes, uint32_t layout) 
   return d;
 }
 
+// Descriptor `d` with its start address (16-byte units, 14-bit field) advanced by `off` units,
+// modulo the field like the masked address smem_desc encodes (no carry into the other fields).
+JDE_DEV uint64_t desc_add(uint64_t d, uint32_t off) { return (d & ~0x3FFFull) | ((d + off) & 0x3FFFull); }
+
 // Descriptor of a K-major tile without swizzle: core matrices of 8 rows x 16 bytes (rows 16 B
 // apart), `lbo` bytes between core matrices adjacent along K, `sbo` bytes between 8-row groups.
 JDE_DEV uint64_t smem_desc_noswz(uint32_t saddr, uint32_t lbo, uint32_t sbo) {

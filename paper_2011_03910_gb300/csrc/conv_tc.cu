@@ -405,7 +405,29 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
     if (lane == 0 && rank == 0) {
       // ---------------- MMA issuer (CG = 2: the leader CTA, for both CTAs of the pair)
       constexpr uint32_t idesc = Q ? idesc_e4m3(128 * CG, BN) : idesc_bf16(128 * CG, BN);
-      uint32_t it = 0, local = 0;
+      uint32_t local = 0;
+      uint32_t s = 0, ph = 0;   // ring slot and its phase parity
+      // Descriptors are built once: the start address (16-byte units, bits 0..13) of every
+      // operand tile is the base descriptor plus a constant offset, so issuing an MMA costs one add.
+      const uint64_t a_desc0 = smem_desc(smem_u32(sA), Cfg::SBO, Cfg::LAYOUT);
+      const uint64_t b_desc0 = smem_desc(smem_u32(sB), Cfg::SBO, Cfg::LAYOUT);
+      constexpr int NW = 18;                      // mode 3: 9 taps x two K=16 MMAs per tile
+      uint32_t w_aoff[NW], w_boff[NW];
+      uint64_t w_desc0 = 0;
+      if (CG == 1 && !Q && a.mode == 3) {
+        // 64-byte-swizzled window, 8-row groups one window row (WW pixels x 64 bytes) apart
+        w_desc0 = smem_desc(smem_u32(sWin), (uint32_t)(a.WW * 64), 4u);
+#pragma unroll
+        for (int i = 0; i < NW; ++i) {
+          const int tap = i / 2, kk = i % 2;
+          const int ky = tap / 3, kx = tap % 3;
+          const int par = a.stride == 2 ? (ky & 1) * 2 + (kx & 1) : 0;
+          const int pix = a.stride == 2 ? (ky >> 1) * a.WW + (kx >> 1) : ky * a.WW + kx;
+          const int kidx = tap * 32 + kk * 16;   // K index of this MMA's first element
+          w_aoff[i] = (uint32_t)(par * a.plane + pix * 64 + kk * 32) >> 4;
+          w_boff[i] = (uint32_t)((kidx >> 6) * Cfg::B_BYTES + (kidx & 63) * 2) >> 4;
+        }
+      }
       for (int u = u0; u < nunits; u += ustep, ++local) {
         const uint32_t buf = local % Cfg::NBUF, use = local / Cfg::NBUF;
         if (local >= (uint32_t)Cfg::NBUF && !mbar_wait(&acc_empty[buf], (use - 1) & 1u)) {
@@ -428,31 +450,17 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
             break;
           }
           tc_fence_after();
-          const uint32_t win = smem_u32(sWin + wb * a.win_bytes);
-          const uint32_t row_bytes = (uint32_t)a.WW * 64u;      // 8-row groups: one window row apart
-#pragma unroll 1
-          for (int tap = 0; tap < 9; ++tap) {
-            const int ky = tap / 3, kx = tap % 3;
-            const int par = a.stride == 2 ? (ky & 1) * 2 + (kx & 1) : 0;
-            const int pix = a.stride == 2 ? (ky >> 1) * a.WW + (kx >> 1) : ky * a.WW + kx;
+          // window buffer wb, each tap at its pixel offset in the swizzled window
+          const uint64_t ad0 = desc_add(w_desc0, (wb * (uint32_t)a.win_bytes) >> 4);
 #pragma unroll
-            for (int kk = 0; kk < 2; ++kk) {
-              const uint32_t a_addr = win + (uint32_t)(par * a.plane + pix * 64 + kk * 32);
-              const uint64_t ad = smem_desc(a_addr, row_bytes, 4u);   // 64-byte swizzle
-              const int kidx = tap * 32 + kk * 16;          // K index of this MMA's first element
-              const uint32_t b_addr = smem_u32(sB + (kidx >> 6) * Cfg::B_BYTES) + (uint32_t)((kidx & 63) * 2);
-              const uint64_t bd = smem_desc(b_addr, Cfg::SBO, Cfg::LAYOUT);
-              umma_bf16(d, ad, bd, idesc, (tap | kk) != 0 ? 1u : 0u);
-            }
-          }
+          for (int i = 0; i < NW; ++i)
+            umma_bf16(d, desc_add(ad0, w_aoff[i]), desc_add(b_desc0, w_boff[i]), idesc, i != 0 ? 1u : 0u);
           umma_commit(&acc_full[buf]);
           umma_commit(&win_empty[wb]);
           continue;
         }
         bool ok = true;
-        for (int kt = 0; kt < a.kt_total; ++kt, ++it) {
-          const uint32_t s = it % STAGES;
-          const uint32_t ph = (it / STAGES) & 1u;
+        for (int kt = 0; kt < a.kt_total; ++kt) {
           if (!mbar_wait(&full[s], ph)) {
             flag_error(c.err, KERR_TIMEOUT);
             atomicExch(&s_abort, 1);
@@ -460,12 +468,12 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
             break;
           }
           tc_fence_after();
-          const uint32_t a_base = smem_u32(sA + s * Cfg::A_BYTES);
-          const uint32_t b_base = smem_u32(sB + (a.mode == 3 ? kt : (int)s) * Cfg::B_BYTES);
+          const uint64_t ad_s = desc_add(a_desc0, (s * (uint32_t)Cfg::A_BYTES) >> 4);
+          const uint64_t bd_s = desc_add(b_desc0, (s * (uint32_t)Cfg::B_BYTES) >> 4);
 #pragma unroll
           for (int kk = 0; kk < BKC / 16; ++kk) {
-            const uint64_t ad = smem_desc(a_base + kk * 32, Cfg::SBO, Cfg::LAYOUT);
-            const uint64_t bd = smem_desc(b_base + kk * 32, Cfg::SBO, Cfg::LAYOUT);
+            const uint64_t ad = desc_add(ad_s, 2 * kk);     // +32 bytes per K=16 (bf16) / K=32 (E4M3) step
+            const uint64_t bd = desc_add(bd_s, 2 * kk);
             const uint32_t accum = (kt | kk) != 0 ? 1u : 0u;
             if constexpr (CG == 2 && Q)
               umma_e4m3_pair(d, ad, bd, idesc, accum);
@@ -480,6 +488,10 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
             umma_commit_pair(&empty[s], 3);      // the stage is free in both CTAs
           else
             umma_commit(&empty[s]);
+          if (++s == (uint32_t)STAGES) {
+            s = 0;
+            ph ^= 1u;
+          }
         }
         if constexpr (CG == 2)
           umma_commit_pair(&acc_full[buf], 3);
@@ -770,7 +782,7 @@ EncodeTiledFn encode_fn() {
 }
 
 // bkc: elements of the innermost box dimension; its bytes (2 per bf16, 1 per E4M3 code when u8)
-// choose the swizzle: 128 -> 128-byte, 64 -> 64-byte, otherwise none.
+// choose the swizzle: 128 -> 128-byte, 64 -> 64-byte, 32 -> 32-byte, otherwise none.
 bool encode(CUtensorMap* m, int rank, void* base, const cuuint64_t* dims, const cuuint64_t* strides_bytes,
             const cuuint32_t* box, int bkc, bool u8 = false) {
   EncodeTiledFn fn = encode_fn();
@@ -779,6 +791,7 @@ bool encode(CUtensorMap* m, int rank, void* base, const cuuint64_t* dims, const 
   const int row_bytes = bkc * (u8 ? 1 : 2);
   const CUtensorMapSwizzle swz = row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
                                  : row_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                 : row_bytes == 32 ? CU_TENSOR_MAP_SWIZZLE_32B
                                                    : CU_TENSOR_MAP_SWIZZLE_NONE;
   CUresult r = fn(m, u8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, base,
                   dims, strides_bytes, box, es,
@@ -885,14 +898,15 @@ bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const void* w_any, int cout_p
     if (!ok) snprintf(msg, msg_len, "cuTensorMapEncodeTiled failed (stem)");
     return ok;
   }
-  if (c.cin == 32 && c.k == 3 && bn == 64 && cout_pad == 64 && c.in.dtype == 1 && c.in.pad == 1 &&
-      c.out.dtype == 1 && c.out.pad == 1 && !c.upsample && c.cout == 64) {
-    // 32-channel 3x3 (stride 1 or 2): the input window of each 8-wide, 16-high output patch
+  // window mode: 32-channel 3x3 convs (64-byte pixels, two K=16 MMAs per tap)
+  if (c.cin == 32 && bn == 64 && c.cout == 64 && c.k == 3 && cout_pad == bn && c.in.dtype == 1 && c.in.pad == 1 &&
+      c.out.dtype == 1 && c.out.pad == 1 && !c.upsample) {
+    // the input window of each 8-wide, 16-high output patch
     plan.mode = 3;
-    plan.bn = 64;
+    plan.bn = bn;
     plan.bkc = 64;
     plan.cin_blocks = 1;
-    plan.kt_total = 5;                       // resident weights: K = 9 taps x 32 ch, padded to 320
+    plan.kt_total = 5;                          // resident weights: 9 taps x 32 channels, padded to 320
     plan.n_tiles = 1;
     plan.TW = 8;
     plan.TH = 16;
@@ -907,8 +921,8 @@ bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const void* w_any, int cout_p
     plan.win_bytes = (st == 1 ? 1 : 4) * plan.plane;
     {
       // as many window buffers as shared memory holds next to the resident weights and the two
-      // staging tiles (at most MAX_WIN)
-      const int fixed = plan.kt_total * 64 * 64 * 2 + 2 * 2 * 128 * 64 * 2 + 1024 + 768 + 2 * 64 * 4;
+      // staging tiles per epilogue group (at most MAX_WIN)
+      const int fixed = plan.kt_total * bn * 64 * 2 + 2 * 2 * 128 * bn * 2 + 1024 + 768 + 2 * bn * 4;
       plan.nwin = (227 * 1024 - 64 - fixed) / plan.win_bytes;
       if (plan.nwin > MAX_WIN) plan.nwin = MAX_WIN;
     }
@@ -928,34 +942,36 @@ bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const void* w_any, int cout_p
     for (int par = 0; par < (st == 2 ? 4 : 1); ++par) {
       // 4-D view (32 channels, x, y, image), 64-byte swizzle; stride 2: parity sub-lattice (py, px)
       const int py = par >> 1, px = par & 1;
+      const int ch = 32;
       void* base = static_cast<__nv_bfloat16*>(c.in.ptr) + (st == 2 ? ((size_t)py * Wp + px) * ps : 0);
-      cuuint64_t dims[4] = {32, (cuuint64_t)(st == 2 ? Wp / 2 : Wp), (cuuint64_t)(st == 2 ? Hp / 2 : Hp),
+      cuuint64_t dims[4] = {(cuuint64_t)ch, (cuuint64_t)(st == 2 ? Wp / 2 : Wp), (cuuint64_t)(st == 2 ? Hp / 2 : Hp),
                             (cuuint64_t)c.in.n};
       cuuint64_t strides[3] = {(cuuint64_t)st * ps * 2, (cuuint64_t)st * Wp * ps * 2, (cuuint64_t)Hp * Wp * ps * 2};
-      cuuint32_t box[4] = {32, (cuuint32_t)plan.WW, (cuuint32_t)plan.WH, 1};
-      ok &= encode(&plan.a[par], 4, base, dims, strides, box, 32);
+      cuuint32_t box[4] = {(cuuint32_t)ch, (cuuint32_t)plan.WW, (cuuint32_t)plan.WH, 1};
+      ok &= encode(&plan.a[par], 4, base, dims, strides, box, ch);
     }
     {
-      cuuint64_t dims[2] = {320, 64};
-      cuuint64_t strides[1] = {320 * 2};
-      cuuint32_t box[2] = {64, 64};
+      const int Kt = plan.kt_total * 64;
+      cuuint64_t dims[2] = {(cuuint64_t)Kt, (cuuint64_t)bn};
+      cuuint64_t strides[1] = {(cuuint64_t)Kt * 2};
+      cuuint32_t box[2] = {64, (cuuint32_t)bn};
       ok &= encode(&plan.b, 2, const_cast<__nv_bfloat16*>(w), dims, strides, box, 64);
     }
     plan.tma_out = 1;
     {
-      cuuint64_t dims[4] = {64, (cuuint64_t)(c.Wo + 2), (cuuint64_t)(c.Ho + 2), (cuuint64_t)c.out.n};
+      cuuint64_t dims[4] = {(cuuint64_t)c.cout, (cuuint64_t)(c.Wo + 2), (cuuint64_t)(c.Ho + 2), (cuuint64_t)c.out.n};
       cuuint64_t strides[3] = {(cuuint64_t)c.out.pixstride * 2, (cuuint64_t)(c.Wo + 2) * c.out.pixstride * 2,
                                (cuuint64_t)(c.Ho + 2) * (c.Wo + 2) * c.out.pixstride * 2};
-      cuuint32_t box[4] = {64, (cuuint32_t)plan.TW, (cuuint32_t)plan.TH, 1};
-      ok &= encode(&plan.o, 4, c.out.ptr, dims, strides, box, 64);
+      cuuint32_t box[4] = {(cuuint32_t)bn, (cuuint32_t)plan.TW, (cuuint32_t)plan.TH, 1};
+      ok &= encode(&plan.o, 4, c.out.ptr, dims, strides, box, bn);
     }
     plan.tma_res = c.res.ptr != nullptr && c.res.dtype == 1 && c.res.pad == 1;
     if (plan.tma_res) {
-      cuuint64_t dims[4] = {64, (cuuint64_t)(c.Wo + 2), (cuuint64_t)(c.Ho + 2), (cuuint64_t)c.res.n};
+      cuuint64_t dims[4] = {(cuuint64_t)c.cout, (cuuint64_t)(c.Wo + 2), (cuuint64_t)(c.Ho + 2), (cuuint64_t)c.res.n};
       cuuint64_t strides[3] = {(cuuint64_t)c.res.pixstride * 2, (cuuint64_t)(c.Wo + 2) * c.res.pixstride * 2,
                                (cuuint64_t)(c.Ho + 2) * (c.Wo + 2) * c.res.pixstride * 2};
-      cuuint32_t box[4] = {64, (cuuint32_t)plan.TW, (cuuint32_t)plan.TH, 1};
-      ok &= encode(&plan.r, 4, c.res.ptr, dims, strides, box, 64);
+      cuuint32_t box[4] = {(cuuint32_t)bn, (cuuint32_t)plan.TW, (cuuint32_t)plan.TH, 1};
+      ok &= encode(&plan.r, 4, c.res.ptr, dims, strides, box, bn);
     }
     if (!ok) snprintf(msg, msg_len, "cuTensorMapEncodeTiled failed (32-channel window conv)");
     return ok;
@@ -1104,11 +1120,14 @@ cudaError_t conv_tc_launch(const TcPlan& p, cudaStream_t st) {
     return cudaErrorInvalidValue;
   }
   if (p.mode == 3) {
-    using Cfg8 = TcCfg<64, 64, 6>;
-    const int smem = p.nwin * p.win_bytes + p.kt_total * Cfg8::B_BYTES + 2 * Cfg8::SDEPTH * Cfg8::C_BYTES + 1024 +
-                     Cfg8::BAR_BYTES + Cfg8::BIAS_BYTES;
-    if (p.bn != 64 || smem > 227 * 1024 - 64) return cudaErrorInvalidValue;
-    return launch_cfg<64, 64, 6, 1>(p, a, st, smem);
+    if (p.bn == 64) {
+      using Cfg8 = TcCfg<64, 64, 6>;
+      const int smem = p.nwin * p.win_bytes + p.kt_total * Cfg8::B_BYTES + 2 * Cfg8::SDEPTH * Cfg8::C_BYTES + 1024 +
+                       Cfg8::BAR_BYTES + Cfg8::BIAS_BYTES;
+      if (smem > 227 * 1024 - 64) return cudaErrorInvalidValue;
+      return launch_cfg<64, 64, 6, 1>(p, a, st, smem);
+    }
+    return cudaErrorInvalidValue;
   }
   if (p.q) {
     // E4M3 operands: 64-bf16-unit rows hold 128 codes, 32-unit rows 64 codes

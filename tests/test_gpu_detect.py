@@ -28,7 +28,7 @@ def per_layer_report(h, acts, tol):
         if g.shape != o.shape:        # laterals are stored upsampled inside the concat
             o = net.upsample2(o)
         e = rel_maxabs(g, o)
-        if e > tol:
+        if not e <= tol:              # NaN counts as a failure
             bad.append((l, e))
     return bad
 
