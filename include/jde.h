@@ -82,6 +82,11 @@ typedef struct {
   int max_tracks;       /* tracks per stream, default 1024 */
   int max_track_dets;   /* detections per frame entering the tracker, default 1024 */
   int device;           /* CUDA device ordinal */
+  int keep_layer_outputs; /* 0 (default): in BF16-stored residual stages each block's 3x3 conv adds
+                             its output into the block input's storage in place (the residual add
+                             of Sec. 3 done by a TMA reduce-add), so the blocks' inputs are not kept
+                             and jde_get_tensor / jde_act_amax refuse them; 1: every conv layer keeps
+                             its own output tensor (per-layer inspection, calibration) */
 } jde_config;
 
 /* One layer of the network as this library builds it (for the weights blob). */
@@ -187,7 +192,8 @@ jde_status jde_stream_reset(jde_handle* h, int stream_id, void* stream);
  * bias, leaky-ReLU, residual add), 100 = letterboxed input.  dims receives {n, h, w, c} of the unpadded tensor, *dtype
  * 0 = f32, 1 = bf16, 2 = E4M3 codes (value = code * amax / 448 of its tensor); the copy is
  * the unpadded tensor in NHWC order.  dst NULL
- * only reports dims and dtype. */
+ * only reports dims and dtype.  JDE_ERR_NOT_FOUND for the input of an in-place residual block
+ * (its storage holds the block's output; see keep_layer_outputs). */
 jde_status jde_get_tensor(jde_handle* h, int id, void* dst, size_t dst_bytes, int* dims, int* dtype,
                           void* stream);
 
@@ -205,7 +211,8 @@ jde_status jde_set_act_amax(jde_handle* h, const float* amax, int n);
 
 /* max |value| of every layer output of the handle's last jde_forward (all its frames), into
  * amax[JDE_NUM_LAYERS] (host); synchronises `stream`.  Heads and BF16/f32 tensors as stored;
- * E4M3 tensors as code times scale. */
+ * E4M3 tensors as code times scale.  Needs every layer output: JDE_ERR_UNSUPPORTED unless the
+ * handle keeps them (keep_layer_outputs = 1, or an FP32 handle). */
 jde_status jde_act_amax(jde_handle* h, float* amax, void* stream);
 
 /* Tile autotuner (tensor-core handles): for batches of n frames at in_w x in_h, times every

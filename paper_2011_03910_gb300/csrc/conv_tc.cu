@@ -33,12 +33,14 @@ struct TcArgs {
   int M_total, Hp, Wp;
   int TW, TH, tiles_x, tiles_y, n_tiles, total_tiles;
   int tma_out, tma_res;
+  int red_res;                     // output aliases the residual: stores are TMA reduce-adds
   int stride, WW, WH, win_bytes;   // mode 3: window (or parity sub-window) size in pixels, bytes per buffer
   int plane;                       // mode 3: bytes between (parity) windows of one buffer (1024-aligned)
   int plane_tx;                    // mode 3: bytes one window load delivers (WW * WH * 64)
   int nwin;                        // mode 3: window buffers in the ring (2 .. MAX_WIN)
   int total_units;                 // work units: tiles, or (CTA pairs) pairs of M tiles x N tiles
   int kel;                         // elements of one k-block along K (E4M3: twice the bf16 count, same bytes)
+  int wnb, whb;                    // mode 4: TMA boxes per window, pixel rows per box
   ConvSpec c;
 };
 
@@ -47,6 +49,10 @@ struct TcArgs {
 // 8x16 output patch (stride 2: its four parity sub-windows) is loaded once, 64 bytes per pixel
 // with the 64-byte swizzle; the MMAs apply the swizzle to absolute shared-memory addresses, so
 // each tap is the same window at another descriptor start (pixel offset); weights resident.
+// 4 stride-1 3x3 with 64-byte k-blocks (32 bf16 / 64 E4M3 channels): per k-block the flat input
+// rows m0 - Wp - 1 .. m0 + 128 + Wp (the nine taps' rows of the tile) are loaded once into a
+// 64-byte-swizzled window; tap (ky, kx) is the window at row offset ky * Wp + kx; the weights
+// stream through the ring, one (tap, k-block) tile per stage.
 __device__ __forceinline__ bool patch_mode(int mode) { return mode == 1 || mode == 3; }
 
 // warp 0: TMA producer; warp 1: MMA issuer + TMEM owner; warps 2..9: epilogue in two
@@ -59,11 +65,12 @@ __host__ __device__ constexpr int tc_threads(int gw) { return 32 * (gw + 1 + EPI
 // 128 rows of A and half (BN/2 rows) of B.
 // Q = 1: E4M3 operands (one byte per element; a k-block row holds 2 * BKC elements, the same
 // bytes as BKC bf16 ones) and E4M3 staged outputs.
-template <int BN, int BKC, int STAGES, int CG = 1, int Q = 0>
+// WM = 1: mode 4 (flat window); the ring holds weight tiles only, the windows are sized at launch.
+template <int BN, int BKC, int STAGES, int CG = 1, int Q = 0, int WM = 0>
 struct TcCfg {
   static constexpr int A_BYTES = 128 * BKC * 2;
   static constexpr int B_BYTES = (BN / CG) * BKC * 2;
-  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int STAGE_BYTES = WM ? B_BYTES : A_BYTES + B_BYTES;
   static constexpr int SWC = BN < 64 ? BN : 64;         // columns staged per epilogue pass
   static constexpr int PASSES = BN / SWC;
   static constexpr int SUB = SWC < 64 ? SWC : 64;       // channels per TMA store box (64 or 128-byte rows)
@@ -177,6 +184,19 @@ __device__ __forceinline__ TileCoord tile_coord(const TcArgs& a, int tile, int b
 
 __device__ __forceinline__ bool aborted(const int* flag) { return *((volatile const int*)flag) != 0; }
 
+// One K step of the tile's MMA: M = 128 (CG = 2: 256 over the CTA pair), N = BN, bf16 or E4M3.
+template <int CG, int Q>
+__device__ __forceinline__ void mma_step(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accum) {
+  if constexpr (CG == 2 && Q)
+    umma_e4m3_pair(d, ad, bd, idesc, accum);
+  else if constexpr (CG == 2)
+    umma_bf16_pair(d, ad, bd, idesc, accum);
+  else if constexpr (Q)
+    umma_e4m3(d, ad, bd, idesc, accum);
+  else
+    umma_bf16(d, ad, bd, idesc, accum);
+}
+
 // Tile of work unit u for this CTA.  CG = 1: unit = tile.  CG = 2: unit = (M-tile pair, N tile);
 // CTA `rank` of the pair takes M tile 2 * pair + rank.
 template <int CG>
@@ -196,9 +216,9 @@ __device__ __forceinline__ bool tile_live(const TcArgs& a, const TileCoord& t) {
 // per CTA pair of a 2-CTA cluster, the leader CTA of the pair issuing the M=256 MMAs).
 // Warps 0..GW-1 produce (GW = 1: lane 0 of warp 0 issues TMA; the stem uses GW gather
 // warps), warp GW issues the MMAs and owns TMEM, the last 8 warps run the epilogue.
-template <int BN, int BKC, int STAGES, int GW, int CG, int Q>
+template <int BN, int BKC, int STAGES, int GW, int CG, int Q, int WM>
 __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid_constant__ TcPlan plan, const TcArgs a) {
-  using Cfg = TcCfg<BN, BKC, STAGES, CG, Q>;
+  using Cfg = TcCfg<BN, BKC, STAGES, CG, Q, WM>;
   const uint32_t rank = CG == 2 ? cluster_rank() : 0u;
   const int u0 = CG == 2 ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
   const int ustep = CG == 2 ? (int)(gridDim.x >> 1) : (int)gridDim.x;
@@ -206,10 +226,11 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
   extern __shared__ uint8_t smem_raw[];
   __shared__ int s_abort;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  // mode 3: [2 windows][resident B][staging]; otherwise [A ring][B ring][staging]
+  // mode 3: [windows][resident B][staging]; mode 4: [windows][B ring][staging];
+  // otherwise [A ring][B ring][staging]
   uint8_t* sWin = smem;
   uint8_t* sA = smem;
-  uint8_t* sB = a.mode == 3 ? smem + a.nwin * a.win_bytes : smem + STAGES * Cfg::A_BYTES;
+  uint8_t* sB = a.mode >= 3 ? smem + a.nwin * a.win_bytes : smem + STAGES * Cfg::A_BYTES;
   const int b_region = a.mode == 3 ? a.kt_total * Cfg::B_BYTES : STAGES * Cfg::B_BYTES;
   uint8_t* sC = sB + b_region;                           // 2 staging tiles
   uint64_t* full = reinterpret_cast<uint64_t*>(sC + 2 * Cfg::SDEPTH * Cfg::C_BYTES);
@@ -353,6 +374,70 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
           tma_load_4d(sWin + wb * a.win_bytes + par * a.plane, &plan.a[par], &win_full[wb], 0, tc.ox0, tc.oy0, tc.img);
       }
     }
+  } else if (WM && warp == 0) {
+    if (lane == 0) {
+      // ---------------- flat-window producer: per k-block the tile's window rows, then its nine
+      // weight tiles (tap-major); CG = 2: both CTAs' bytes are counted on the leader's barriers
+      tma_prefetch(&plan.a[0]);
+      tma_prefetch(&plan.b);
+      uint32_t s = 0, ph = 0, nb = 0, w = 0, wph = 0, nw = 0;   // ring slots, phases, loads issued
+      const uint32_t full_leader0 = CG == 2 ? mapa_rank(smem_u32(&full[0]), 0) : 0u;
+      const uint32_t wfull_leader0 = CG == 2 ? mapa_rank(smem_u32(&win_full[0]), 0) : 0u;
+      const uint32_t box_bytes = (uint32_t)a.whb * 64u;
+      bool ok = true;
+      for (int u = u0; ok && u < nunits && !aborted(&s_abort); u += ustep) {
+        const TileCoord tc = tile_coord(a, unit_tile<CG>(a, u, rank), BN);
+        const int row0 = tc.m0 - a.Wp - 1;   // input row of the window's first pixel (may be < 0: zero fill)
+        for (int cb = 0; ok && cb < a.cin_blocks; ++cb) {
+          if (nw >= (uint32_t)a.nwin && !mbar_wait(&win_empty[w], wph ^ 1u)) {
+            ok = false;
+            break;
+          }
+          uint8_t* dW = sWin + w * a.win_bytes;
+          if ((smem_u32(dW) | box_bytes) & 1023u) {   // swizzled TMA destinations
+            ok = false;
+            break;
+          }
+          if constexpr (CG == 2) {
+            if (rank == 0) mbar_expect_tx(&win_full[w], 2u * (uint32_t)a.wnb * box_bytes);
+            for (int j = 0; j < a.wnb; ++j)
+              tma_load_2d_pair(dW + j * box_bytes, &plan.a[0], wfull_leader0 + w * 8u, cb * a.kel, row0 + j * a.whb);
+          } else {
+            mbar_expect_tx(&win_full[w], (uint32_t)a.wnb * box_bytes);
+            for (int j = 0; j < a.wnb; ++j)
+              tma_load_2d(dW + j * box_bytes, &plan.a[0], &win_full[w], cb * a.kel, row0 + j * a.whb);
+          }
+          ++nw;
+          if (++w == (uint32_t)a.nwin) {
+            w = 0;
+            wph ^= 1u;
+          }
+          for (int tap = 0; tap < 9; ++tap) {
+            if (nb >= (uint32_t)STAGES && !mbar_wait(&empty[s], ph ^ 1u)) {
+              ok = false;
+              break;
+            }
+            ++nb;
+            const int kcol = tap * a.c.cin + cb * a.kel;   // weights: K = (tap, channel)
+            if constexpr (CG == 2) {
+              if (rank == 0) mbar_expect_tx(&full[s], 2u * (uint32_t)Cfg::B_BYTES);
+              tma_load_2d_pair(sB + s * Cfg::B_BYTES, &plan.b, full_leader0 + s * 8u, kcol, tc.n0 + (int)rank * (BN / 2));
+            } else {
+              mbar_expect_tx(&full[s], (uint32_t)Cfg::B_BYTES);
+              tma_load_2d(sB + s * Cfg::B_BYTES, &plan.b, &full[s], kcol, tc.n0);
+            }
+            if (++s == (uint32_t)STAGES) {
+              s = 0;
+              ph ^= 1u;
+            }
+          }
+        }
+      }
+      if (!ok) {
+        flag_error(c.err, KERR_TIMEOUT);
+        atomicExch(&s_abort, 1);
+      }
+    }
   } else if (warp == 0 && GW == 1) {
     if (lane == 0) {
       // ---------------- TMA producer
@@ -407,6 +492,7 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
       constexpr uint32_t idesc = Q ? idesc_e4m3(128 * CG, BN) : idesc_bf16(128 * CG, BN);
       uint32_t local = 0;
       uint32_t s = 0, ph = 0;   // ring slot and its phase parity
+      uint32_t w4 = 0, w4ph = 0;   // mode 4: window slot and its phase parity
       // Descriptors are built once: the start address (16-byte units, bits 0..13) of every
       // operand tile is the base descriptor plus a constant offset, so issuing an MMA costs one add.
       const uint64_t a_desc0 = smem_desc(smem_u32(sA), Cfg::SBO, Cfg::LAYOUT);
@@ -457,6 +543,60 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
             umma_bf16(d, desc_add(ad0, w_aoff[i]), desc_add(b_desc0, w_boff[i]), idesc, i != 0 ? 1u : 0u);
           umma_commit(&acc_full[buf]);
           umma_commit(&win_empty[wb]);
+          continue;
+        }
+        if constexpr (WM != 0) {
+          // mode 4: per k-block one window; tap (ky, kx) starts ky * Wp + kx rows into it
+          const uint64_t w_base = smem_desc(smem_u32(sWin), 8u * 64u, 4u);   // 64-byte rows, 64-byte swizzle
+          bool wok = true;
+          for (int cb = 0; cb < a.cin_blocks; ++cb) {
+            if (!mbar_wait(&win_full[w4], w4ph)) {
+              wok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint64_t wd = desc_add(w_base, (w4 * (uint32_t)a.win_bytes) >> 4);
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap) {
+              if (!mbar_wait(&full[s], ph)) {
+                wok = false;
+                break;
+              }
+              tc_fence_after();
+              const uint64_t ad_t = desc_add(wd, (uint32_t)((tap / 3) * a.Wp + tap % 3) * 4u);
+              const uint64_t bd_s = desc_add(b_desc0, (s * (uint32_t)Cfg::B_BYTES) >> 4);
+#pragma unroll
+              for (int kk = 0; kk < BKC / 16; ++kk)
+                mma_step<CG, Q>(d, desc_add(ad_t, 2 * kk), desc_add(bd_s, 2 * kk), idesc,
+                                (cb | tap | kk) != 0 ? 1u : 0u);
+              if constexpr (CG == 2)
+                umma_commit_pair(&empty[s], 3);
+              else
+                umma_commit(&empty[s]);
+              if (++s == (uint32_t)STAGES) {
+                s = 0;
+                ph ^= 1u;
+              }
+            }
+            if (!wok) break;
+            if constexpr (CG == 2)
+              umma_commit_pair(&win_empty[w4], 3);   // the window is free in both CTAs
+            else
+              umma_commit(&win_empty[w4]);
+            if (++w4 == (uint32_t)a.nwin) {
+              w4 = 0;
+              w4ph ^= 1u;
+            }
+          }
+          if constexpr (CG == 2)
+            umma_commit_pair(&acc_full[buf], 3);
+          else
+            umma_commit(&acc_full[buf]);
+          if (!wok) {
+            flag_error(c.err, KERR_TIMEOUT);
+            atomicExch(&s_abort, 1);
+            break;
+          }
           continue;
         }
         bool ok = true;
@@ -594,40 +734,59 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
           for (int c0 = 0; c0 < Cfg::SWC; c0 += 32) {
             uint32_t r[32];
             tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + buf * BN + (uint32_t)(p * Cfg::SWC + c0), r);
-            tmem_ld_wait();
+            // the chunk's shared-memory operands (bias, scale, residual) are all read before any of
+            // its stores, so the loads overlap each other and the TMEM read
+            const int nu = o8 ? 2 : 4;               // 16-byte staging units of the chunk's 32 columns
+            uint8_t* qa[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int col = o8 ? c0 + 16 * u : c0 + 8 * u;   // first column of unit u inside the pass
+              qa[u] = o8 ? stg + stage_off<32>(row, col >> 4)
+                         : stg + (col / Cfg::SUB) * Cfg::SUB_BYTES + stage_off<Cfg::SUB>(row, (col % Cfg::SUB) >> 3);
+            }
             const float4* b4 = reinterpret_cast<const float4*>(sBias + p * Cfg::SWC + c0);
+            float4 bb[8], mm[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) bb[i] = b4[i];
             if (Q) {
               const float4* m4 = reinterpret_cast<const float4*>(sMult + p * Cfg::SWC + c0);
 #pragma unroll
-              for (int i = 0; i < 8; ++i) {
-                const float4 m = m4[i];
-                r[4 * i] = __float_as_uint(__uint_as_float(r[4 * i]) * m.x);
-                r[4 * i + 1] = __float_as_uint(__uint_as_float(r[4 * i + 1]) * m.y);
-                r[4 * i + 2] = __float_as_uint(__uint_as_float(r[4 * i + 2]) * m.z);
-                r[4 * i + 3] = __float_as_uint(__uint_as_float(r[4 * i + 3]) * m.w);
-              }
+              for (int i = 0; i < 8; ++i) mm[i] = m4[i];
             }
+            uint4 rq[4];
+            if (use_res) {
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                if (u < nu) rq[u] = *reinterpret_cast<const uint4*>(qa[u]);
+            }
+            tmem_ld_wait();
+            float v[32];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              float a4[4] = {__uint_as_float(r[4 * i]), __uint_as_float(r[4 * i + 1]), __uint_as_float(r[4 * i + 2]),
+                             __uint_as_float(r[4 * i + 3])};
+              if (Q) {
+                a4[0] *= mm[i].x;
+                a4[1] *= mm[i].y;
+                a4[2] *= mm[i].z;
+                a4[3] *= mm[i].w;
+              }
+              v[4 * i] = a4[0] + bb[i].x;
+              v[4 * i + 1] = a4[1] + bb[i].y;
+              v[4 * i + 2] = a4[2] + bb[i].z;
+              v[4 * i + 3] = a4[3] + bb[i].w;
+            }
+            if (c.act) {
+#pragma unroll
+              for (int e = 0; e < 32; ++e) v[e] = leaky01(v[e]);
+            }
+            uint4 outv[4];
             if (o8) {
               // 32 columns = two 16-byte units of the 64-byte E4M3 row
-              float v[32];
-#pragma unroll
-              for (int i = 0; i < 8; ++i) {
-                const float4 b = b4[i];
-                v[4 * i] = __uint_as_float(r[4 * i]) + b.x;
-                v[4 * i + 1] = __uint_as_float(r[4 * i + 1]) + b.y;
-                v[4 * i + 2] = __uint_as_float(r[4 * i + 2]) + b.z;
-                v[4 * i + 3] = __uint_as_float(r[4 * i + 3]) + b.w;
-              }
-              if (c.act) {
-#pragma unroll
-                for (int e = 0; e < 32; ++e) v[e] = leaky01(v[e]);
-              }
 #pragma unroll
               for (int h = 0; h < 2; ++h) {
-                uint8_t* q = stg + stage_off<32>(row, (c0 >> 4) + h);
                 if (use_res) {
-                  const uint4 rq = *reinterpret_cast<const uint4*>(q);
-                  const uint32_t rv[4] = {rq.x, rq.y, rq.z, rq.w};
+                  const uint32_t rv[4] = {rq[h].x, rq[h].y, rq[h].z, rq[h].w};
 #pragma unroll
                   for (int e = 0; e < 4; ++e) {
                     const float2 lo = e4m3x2_to_float2(rv[e] & 0xFFFFu), hi = e4m3x2_to_float2(rv[e] >> 16);
@@ -645,41 +804,33 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
                                    (e4m3x2(w[2] * c.out_inv_scale, w[3] * c.out_inv_scale) << 16))
                                 : 0u;
                 }
-                *reinterpret_cast<uint4*>(q) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                outv[h] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
               }
-              continue;
-            }
+            } else {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const int col = c0 + 8 * u;                       // column inside this pass
-              uint8_t* q = stg + (col / Cfg::SUB) * Cfg::SUB_BYTES + stage_off<Cfg::SUB>(row, (col % Cfg::SUB) >> 3);
-              const float4 b0 = b4[2 * u], b1 = b4[2 * u + 1];
-              float t[8] = {__uint_as_float(r[8 * u]) + b0.x,     __uint_as_float(r[8 * u + 1]) + b0.y,
-                            __uint_as_float(r[8 * u + 2]) + b0.z, __uint_as_float(r[8 * u + 3]) + b0.w,
-                            __uint_as_float(r[8 * u + 4]) + b1.x, __uint_as_float(r[8 * u + 5]) + b1.y,
-                            __uint_as_float(r[8 * u + 6]) + b1.z, __uint_as_float(r[8 * u + 7]) + b1.w};
-              if (c.act) {
+              for (int u = 0; u < 4; ++u) {
+                float* t = v + 8 * u;
+                if (use_res) {
+                  const uint32_t rv[4] = {rq[u].x, rq[u].y, rq[u].z, rq[u].w};
 #pragma unroll
-                for (int e = 0; e < 8; ++e) t[e] = leaky01(t[e]);
-              }
-              if (use_res) {
-                const uint4 rq = *reinterpret_cast<const uint4*>(q);
-                const uint32_t rv[4] = {rq.x, rq.y, rq.z, rq.w};
+                  for (int e = 0; e < 4; ++e) {
+                    const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&rv[e]));
+                    t[2 * e] += f.x;
+                    t[2 * e + 1] += f.y;
+                  }
+                }
+                uint32_t pk[4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                  const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&rv[e]));
-                  t[2 * e] += f.x;
-                  t[2 * e + 1] += f.y;
+                  __nv_bfloat162 h2 = valid ? __floats2bfloat162_rn(t[2 * e], t[2 * e + 1]) : __floats2bfloat162_rn(0.f, 0.f);
+                  pk[e] = *reinterpret_cast<uint32_t*>(&h2);
                 }
+                outv[u] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
               }
-              uint32_t pk[4];
-#pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                __nv_bfloat162 h2 = valid ? __floats2bfloat162_rn(t[2 * e], t[2 * e + 1]) : __floats2bfloat162_rn(0.f, 0.f);
-                pk[e] = *reinterpret_cast<uint32_t*>(&h2);
-              }
-              *reinterpret_cast<uint4*>(q) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
             }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (u < nu) *reinterpret_cast<uint4*>(qa[u]) = outv[u];
           }
           if (p == Cfg::PASSES - 1) {
             tc_fence_before();
@@ -696,10 +847,18 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
           if (elected && ok && live && !aborted(&s_abort)) {
             for (int j = 0; j < nsub; ++j) {
               const int ch = tc.n0 + p * Cfg::SWC + j * sub_ch;
-              if (!patch_mode(a.mode))
-                tma_store_2d(&plan.o, stg + j * sub_bytes, ch, tc.m0);
-              else
-                tma_store_4d(&plan.o, stg + j * sub_bytes, ch, tc.ox0 + 1, tc.oy0 + 1, tc.img);
+              // in place over the residual: the tile is added to it (the residual add of the block)
+              if (!patch_mode(a.mode)) {
+                if (a.red_res)
+                  tma_reduce_add_2d(&plan.o, stg + j * sub_bytes, ch, tc.m0);
+                else
+                  tma_store_2d(&plan.o, stg + j * sub_bytes, ch, tc.m0);
+              } else {
+                if (a.red_res)
+                  tma_reduce_add_4d(&plan.o, stg + j * sub_bytes, ch, tc.ox0 + 1, tc.oy0 + 1, tc.img);
+                else
+                  tma_store_4d(&plan.o, stg + j * sub_bytes, ch, tc.ox0 + 1, tc.oy0 + 1, tc.img);
+              }
             }
             bulk_commit();
           }
@@ -764,6 +923,17 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
 }
 
 // ----------------------------------------------------------------------------- host side
+// mode 4: weight-ring depth, and the shared memory of an instantiation besides its windows
+constexpr int W4_STAGES = 8;
+template <int BN, int CG, int Q>
+constexpr int w4_fixed() {
+  using C = TcCfg<BN, 32, W4_STAGES, CG, Q, 1>;
+  return W4_STAGES * C::B_BYTES + 2 * C::SDEPTH * C::C_BYTES + 1024 + C::BAR_BYTES + C::BIAS_BYTES;
+}
+int w4_fixed_bytes(int bn, int q) {
+  if (bn == 128) return q ? w4_fixed<128, 1, 1>() : w4_fixed<128, 1, 0>();
+  return q ? w4_fixed<256, 2, 1>() : w4_fixed<256, 2, 0>();
+}
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -810,10 +980,10 @@ int sm_count() {
   return n;
 }
 
-template <int BN, int BKC, int STAGES, int GW = 1, int CG = 1, int Q = 0>
+template <int BN, int BKC, int STAGES, int GW = 1, int CG = 1, int Q = 0, int WM = 0>
 cudaError_t launch_cfg(const TcPlan& p, const TcArgs& a, cudaStream_t st, int smem = 0) {
-  using Cfg = TcCfg<BN, BKC, STAGES, CG, Q>;
-  auto kernel = conv_tc_kernel<BN, BKC, STAGES, GW, CG, Q>;
+  using Cfg = TcCfg<BN, BKC, STAGES, CG, Q, WM>;
+  auto kernel = conv_tc_kernel<BN, BKC, STAGES, GW, CG, Q, WM>;
   if (!smem) smem = Cfg::SMEM;
   static int attr_set = 0;
   if (attr_set < smem) {
@@ -965,7 +1135,9 @@ bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const void* w_any, int cout_p
       cuuint32_t box[4] = {(cuuint32_t)bn, (cuuint32_t)plan.TW, (cuuint32_t)plan.TH, 1};
       ok &= encode(&plan.o, 4, c.out.ptr, dims, strides, box, bn);
     }
-    plan.tma_res = c.res.ptr != nullptr && c.res.dtype == 1 && c.res.pad == 1;
+    plan.red_res = c.res.ptr != nullptr && c.res.ptr == c.out.ptr && c.res.dtype == 1 &&
+                   c.res.pixstride == c.out.pixstride && c.res.pad == 1;
+    plan.tma_res = !plan.red_res && c.res.ptr != nullptr && c.res.dtype == 1 && c.res.pad == 1;
     if (plan.tma_res) {
       cuuint64_t dims[4] = {(cuuint64_t)c.cout, (cuuint64_t)(c.Wo + 2), (cuuint64_t)(c.Ho + 2), (cuuint64_t)c.res.n};
       cuuint64_t strides[3] = {(cuuint64_t)c.res.pixstride * 2, (cuuint64_t)(c.Wo + 2) * c.res.pixstride * 2,
@@ -1008,10 +1180,31 @@ bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const void* w_any, int cout_p
     plan.mode = 0;
     plan.M_total = c.in.n * Hp * Wp;
     plan.m_tiles = (plan.M_total + 127) / 128;
+    // 3x3 with 128- or 256-wide tiles: flat windows (mode 4) when at least two fit in shared memory
+    const int kel4 = q ? 64 : 32;           // 64-byte k-blocks
+    if (c.k == 3 && (bn == 128 || bn == 256) && c.cin % kel4 == 0) {
+      const int npx = 128 + 2 * Wp + 2;      // rows m0 - Wp - 1 .. m0 + 128 + Wp
+      const int wnb = (npx + 255) / 256;     // a TMA box spans at most 256 rows
+      const int whb = ((npx + wnb - 1) / wnb + 15) / 16 * 16;   // rows per box: 1024-byte multiples
+      const int win_bytes = wnb * whb * 64;
+      int nwin = (227 * 1024 - 64 - w4_fixed_bytes(bn, q)) / win_bytes;
+      if (nwin > MAX_WIN) nwin = MAX_WIN;
+      if (nwin >= 2) {
+        plan.mode = 4;
+        plan.wnb = wnb;
+        plan.whb = whb;
+        plan.win_bytes = win_bytes;
+        plan.nwin = nwin;
+        plan.kel = kel4;
+        plan.bkc = 32;
+        plan.cin_blocks = c.cin / kel4;
+        plan.kt_total = 9 * plan.cin_blocks;
+      }
+    }
     cuuint64_t dims[2] = {(cuuint64_t)c.cin, (cuuint64_t)plan.M_total};
     cuuint64_t strides[1] = {(cuuint64_t)c.in.pixstride * ie};
-    cuuint32_t box[2] = {(cuuint32_t)kel, 128};
-    ok &= encode(&plan.a[0], 2, base, dims, strides, box, kel, q);
+    cuuint32_t box[2] = {(cuuint32_t)plan.kel, plan.mode == 4 ? (cuuint32_t)plan.whb : 128u};
+    ok &= encode(&plan.a[0], 2, base, dims, strides, box, plan.kel, q);
   } else {
     plan.mode = 1;
     if ((c.in.h & 1) || (c.in.w & 1)) {
@@ -1041,27 +1234,30 @@ bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const void* w_any, int cout_p
       }
   }
   // 256-wide tiles run on CTA pairs (M = 256 per MMA, each CTA loads half of B)
-  plan.cg = bn == 256 && bkc == 64 ? 2 : 1;
+  plan.cg = bn == 256 && (bkc == 64 || plan.mode == 4) ? 2 : 1;
   {
     cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)cout_pad};
     cuuint64_t strides[1] = {(cuuint64_t)K * ie};
-    cuuint32_t box[2] = {(cuuint32_t)kel, (cuuint32_t)(bn / plan.cg)};
-    ok &= encode(&plan.b, 2, const_cast<void*>(w_any), dims, strides, box, kel, q);
+    cuuint32_t box[2] = {(cuuint32_t)plan.kel, (cuuint32_t)(bn / plan.cg)};
+    ok &= encode(&plan.b, 2, const_cast<void*>(w_any), dims, strides, box, plan.kel, q);
   }
   // TMA-stored epilogue: bf16 or E4M3 padded outputs written in place (no upsample), channel
   // count a multiple of the store box (64 channels, or 32 for 32-wide bf16 tiles)
   const int sub = o8 ? 64 : (bn < 64 ? bn : 64);
   const int oe = o8 ? 1 : 2;
   plan.tma_out = (c.out.dtype == 1 || o8) && !c.upsample && c.out.pad == 1 && c.cout % sub == 0;
-  plan.tma_res = plan.tma_out && c.res.ptr != nullptr && c.stride == 1 && c.res.dtype == c.out.dtype &&
-                 c.res.pad == 1;
+  // residual stored in place under the output (bf16): added by the store itself (TMA reduce-add)
+  plan.red_res = plan.tma_out && c.res.ptr != nullptr && c.res.ptr == c.out.ptr && c.out.dtype == 1 &&
+                 c.res.dtype == 1 && c.res.pixstride == c.out.pixstride && c.res.pad == 1;
+  plan.tma_res = !plan.red_res && plan.tma_out && c.res.ptr != nullptr && c.stride == 1 &&
+                 c.res.dtype == c.out.dtype && c.res.pad == 1;
   if (q && !o8 && plan.tma_out) {
     snprintf(msg, msg_len, "E4M3 conv: staged outputs must be E4M3");
     return false;
   }
   if (plan.tma_out) {
     const int Ho = c.Ho, Wo = c.Wo;
-    if (plan.mode == 0) {
+    if (plan.mode == 0 || plan.mode == 4) {
       cuuint64_t dims[2] = {(cuuint64_t)c.cout, (cuuint64_t)plan.M_total};
       cuuint64_t strides[1] = {(cuuint64_t)c.out.pixstride * oe};
       cuuint32_t box[2] = {(cuuint32_t)sub, 128};
@@ -1105,6 +1301,7 @@ cudaError_t conv_tc_launch(const TcPlan& p, cudaStream_t st) {
   a.total_units = p.cg == 2 ? (p.m_tiles + 1) / 2 * p.n_tiles : a.total_tiles;
   a.tma_out = p.tma_out;
   a.tma_res = p.tma_res;
+  a.red_res = p.red_res;
   a.stride = p.spec.stride;
   a.WW = p.WW;
   a.WH = p.WH;
@@ -1113,10 +1310,23 @@ cudaError_t conv_tc_launch(const TcPlan& p, cudaStream_t st) {
   a.kel = p.kel ? p.kel : p.bkc;
   a.plane = p.plane;
   a.plane_tx = p.WW * p.WH * 64;
+  a.wnb = p.wnb;
+  a.whb = p.whb;
   a.c = p.spec;
   if (p.mode == 2) {
     if (p.bn == 32) return launch_cfg<32, 32, 16, 4>(p, a, st);
     if (p.bn == 64) return launch_cfg<64, 32, 12, 4>(p, a, st);
+    return cudaErrorInvalidValue;
+  }
+  if (p.mode == 4) {
+    const int smem = p.nwin * p.win_bytes + w4_fixed_bytes(p.bn, p.q);
+    if (smem > 227 * 1024 - 64) return cudaErrorInvalidValue;
+    if (p.bn == 128 && p.cg == 1)
+      return p.q ? launch_cfg<128, 32, W4_STAGES, 1, 1, 1, 1>(p, a, st, smem)
+                 : launch_cfg<128, 32, W4_STAGES, 1, 1, 0, 1>(p, a, st, smem);
+    if (p.bn == 256 && p.cg == 2)
+      return p.q ? launch_cfg<256, 32, W4_STAGES, 1, 2, 1, 1>(p, a, st, smem)
+                 : launch_cfg<256, 32, W4_STAGES, 1, 2, 0, 1>(p, a, st, smem);
     return cudaErrorInvalidValue;
   }
   if (p.mode == 3) {

@@ -34,14 +34,17 @@ struct TcPlan {
   alignas(64) CUtensorMap o;     // output (TMA-stored epilogue), valid when tma_out
   alignas(64) CUtensorMap r;     // residual (TMA-loaded into the staging tile), valid when tma_res
   int tma_out, tma_res;
-  int mode;                      // 0 flat (stride 1 over the padded pixel array), 1 patch (stride 2)
+  int red_res;                   // output aliases the residual: the epilogue reduce-adds into it
+  int mode;                      // 0 flat (stride 1 over the padded pixel array), 1 patch (stride 2),
+                                 // 2 stem gather, 3 32-channel window, 4 flat window (stride-1 3x3)
   int bn, bkc;
   int kt_total, cin_blocks;
   int m_tiles, n_tiles;
   int M_total, Hp, Wp;
   int TW, TH, tiles_x, tiles_y;
   int WW, WH, win_bytes, plane;  // mode 3: (sub-)window pixels, bytes per buffer, bytes per 8-channel plane
-  int nwin;                      // mode 3: window buffers in the ring
+  int nwin;                      // modes 3, 4: window buffers in the ring
+  int wnb, whb;                  // mode 4: TMA boxes per window, pixel rows per box
   int cg;                        // 2: 256-wide tiles on CTA pairs (cta_group::2), else 1
   int q;                         // 1: E4M3 operands (kind::f8f6f4)
   int kel;                       // elements of one k-block along K (bf16: bkc, E4M3: 2 * bkc)

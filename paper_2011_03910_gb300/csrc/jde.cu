@@ -200,7 +200,16 @@ bool dmalloc(void** p, size_t bytes) {
 }
 
 // ----------------------------------------------------------------------------- network wiring
-std::vector<LayerIO> build_io() {
+// In-place residual stages: every block's 3x3 adds its output into the storage of the block's
+// input (TMA reduce-add), so a stage's chain lives in one buffer.  Tensor-core handles whose
+// stage outputs are stored in BF16 (all stages of a BF16 handle; the first stride-2 stage of an
+// E4M3 handle), unless the handle keeps every layer output.
+bool inplace_stage(const jde_config& cfg, int first_layer) {
+  if (cfg.keep_layer_outputs || cfg.precision == JDE_FP32) return false;
+  return cfg.precision == JDE_BF16 || first_layer < FP8_FIRST_OUT;
+}
+
+std::vector<LayerIO> build_io(const jde_config& cfg) {
   const auto& L = layers();
   std::vector<LayerIO> io(L.size());
   int l = 0;
@@ -213,9 +222,20 @@ std::vector<LayerIO> build_io() {
   int c3 = -1, c4 = -1;
   for (int s = 0; s < 5; ++s) {
     x = set(x, -1, 1);
+    const bool chain = inplace_stage(cfg, x);
+    // the skips of stages 3 and 4 end in a concat slice: an in-place chain lives there from its start
+    if (chain && (s == 2 || s == 3)) {
+      io[x].out = s == 2 ? T_CAT8 : T_CAT16;
+      io[x].out_slice = s == 2 ? 128 : 256;
+    }
     for (int b = 0; b < stage_n[s]; ++b) {
+      const int r = x;
       const int t = set(x, -1, 1);
-      x = set(t, x, 1);
+      x = set(t, r, 1);
+      if (chain) {
+        io[x].out = io[r].out;               // the block output overwrites its input
+        io[x].out_slice = io[r].out_slice;
+      }
     }
     if (s == 2) c3 = x;
     if (s == 3) c4 = x;
@@ -360,6 +380,15 @@ TView view_of(const ResBuffers& rb, int tid, int n) {
   }
   if (tid == T_LB && d.c == 4) v.c = 3;   // bf16 letterbox stores RGB + one zero channel
   return v;
+}
+
+// True for a layer output that a later layer overwrites in place (the input of an in-place block).
+bool overwritten(const jde_handle* h, int tid) {
+  for (int l = tid + 1; l < JDE_NUM_LAYERS; ++l)
+    if (h->io[l].res == tid && h->io[l].out == h->io[tid].out && h->io[l].out_slice == h->io[tid].out_slice &&
+        h->io[l].out != l)
+      return true;
+  return false;
 }
 
 // Storage tensor of tensor id `tid` (a concat buffer for the layers writing into one).
@@ -780,7 +809,7 @@ jde_status jde_create(const jde_config* cfg, const void* weights, size_t nbytes,
   if (cudaSetDevice(c.device) != cudaSuccess) return fail(nullptr, JDE_ERR_CUDA, "cudaSetDevice(%d)", c.device);
   jde_handle* h = new jde_handle();
   h->cfg = c;
-  h->io = build_io();
+  h->io = build_io(h->cfg);
   jde_status s = JDE_OK;
   if (!dmalloc((void**)&h->d_err, sizeof(int))) s = fail(h, JDE_ERR_OOM, "error word");
   if (s == JDE_OK) cudaMemset(h->d_err, 0, sizeof(int));
@@ -976,6 +1005,8 @@ jde_status jde_get_tensor(jde_handle* h, int id, void* dst, size_t dst_bytes, in
   if (!h) return fail(nullptr, JDE_ERR_INVALID_ARG, "handle is NULL");
   if (!h->cur) return fail(h, JDE_ERR_NOT_FOUND, "no forward has run");
   int tid;
+  if (id >= 0 && id < JDE_NUM_LAYERS && overwritten(h, id))
+    return fail(h, JDE_ERR_NOT_FOUND, "tensor %d is overwritten in place by its residual block (keep_layer_outputs)", id);
   if (id >= 0 && id < JDE_NUM_LAYERS)
     tid = id;
   else if (id == 100)
@@ -1034,6 +1065,9 @@ jde_status jde_act_amax(jde_handle* h, float* amax, void* stream) {
   if (!h) return fail(nullptr, JDE_ERR_INVALID_ARG, "handle is NULL");
   if (!amax) return fail(h, JDE_ERR_INVALID_ARG, "jde_act_amax: amax is NULL");
   if (!h->cur) return fail(h, JDE_ERR_INVALID_ARG, "jde_act_amax: no forward has run");
+  for (int l = 0; l < JDE_NUM_LAYERS; ++l)
+    if (overwritten(h, l))
+      return fail(h, JDE_ERR_UNSUPPORTED, "jde_act_amax: layer outputs are not kept (keep_layer_outputs = 0)");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (!h->d_amax && !dmalloc((void**)&h->d_amax, sizeof(float) * JDE_NUM_LAYERS))
     return fail(h, JDE_ERR_OOM, "amax scratch");
@@ -1083,6 +1117,7 @@ jde_status jde_autotune(jde_handle* h, int n, int in_w, int in_h, void* stream) 
       TcPlan cand;
       char msg[256];
       if (!conv_tc_plan(cand, plan->specs[l], w, lw.cout_pad_tc, bn, msg, sizeof(msg))) continue;
+      if (cand.mode != def.mode) continue;   // same addressing mode: the same order of the K sum, same bits
       if (conv_tc_launch(cand, st) != cudaSuccess) {   // shape without a built configuration
         cudaGetLastError();
         continue;
@@ -1134,7 +1169,7 @@ jde_status jde_estimate_device_bytes(const jde_config* cfg, int in_w, int in_h, 
     return fail(nullptr, JDE_ERR_INVALID_ARG, "jde_estimate_device_bytes: bad arguments");
   jde_handle tmp;
   tmp.cfg = *cfg;
-  tmp.io = build_io();
+  tmp.io = build_io(tmp.cfg);
   const bool bf16 = cfg->precision != JDE_FP32;
   const auto& L = layers();
   size_t b = sizeof(int) + sizeof(LbAxis) * (size_t)(cfg->max_in_w + cfg->max_in_h);

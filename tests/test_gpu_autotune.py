@@ -32,7 +32,7 @@ def _layer_outputs(j, h, frames):
 @pytest.mark.parametrize("fp8", [False, True])
 def test_autotuned_forward_is_bit_identical(fp8):
     j = jde()
-    h = make_handle(j.JDE_FP8_E4M3 if fp8 else j.JDE_BF16, max_batch=2, src_w=320, src_h=192)
+    h = make_handle(j.JDE_FP8_E4M3 if fp8 else j.JDE_BF16, max_batch=2, src_w=320, src_h=192, keep_layer_outputs=1)
     try:
         if fp8:
             j.jde_set_act_amax(h, json.load(open(GOLDEN))["amax"])

@@ -135,7 +135,7 @@ def test_head_error_of_the_e4m3_network_is_the_scheme_s():
 def test_bf16_calibration_amax_matches_the_oracle_s():
     """jde_act_amax of a BF16 handle on the calibration frames reproduces the golden (oracle) amax."""
     j = jde()
-    h = make_handle(j.JDE_BF16, max_batch=2, src_w=1920, src_h=1080)
+    h = make_handle(j.JDE_BF16, max_batch=2, src_w=1920, src_h=1080, keep_layer_outputs=1)
     try:
         f = torch.from_numpy(synth.frames_uniform(1000, 2, 1080, 1920)).cuda()
         j.jde_forward(h, f, 2, 1920, 1080, 320, 192, True, torch.cuda.current_stream())
