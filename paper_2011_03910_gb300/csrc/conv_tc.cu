@@ -85,6 +85,9 @@ struct TcCfg {
   static constexpr uint32_t LAYOUT = BKC == 64 ? 2u : 4u;     // SW128 : SW64 (MMA operand tiles)
   static constexpr uint32_t SBO = 8 * BKC * 2;                 // bytes per 8-row group
   static constexpr int NBUF = BN <= 128 ? 4 : 2;               // TMEM accumulator buffers
+  // 256-wide tiles (two TMEM buffers): both epilogue groups drain every tile, each half of its
+  // columns, so a buffer is free again in half the time; narrower tiles alternate between groups
+  static constexpr bool SPLIT = BN == 256;
   static constexpr uint32_t TMEM_COLS = NBUF * BN;
   static_assert(SMEM <= 227 * 1024 - 64, "shared memory budget (64 bytes left for static shared variables)");
   static_assert((2 * STAGES + 2 * NBUF + 2 + 2 * MAX_WIN + 1) * 8 + 4 <= BAR_BYTES, "barrier region");
@@ -256,7 +259,7 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
     }
     for (int b = 0; b < Cfg::NBUF; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], CG * EPI_WARPS / 2);   // CG = 2: both CTAs' epilogue groups
+      mbar_init(&acc_empty[b], CG * (Cfg::SPLIT ? EPI_WARPS : EPI_WARPS / 2));   // CG = 2: both CTAs' warps
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&res_full[b], 1);
@@ -641,7 +644,8 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
       }
     }
   } else if (warp > GW) {
-    // ---------------- epilogue: group g takes the tiles whose local index has parity g
+    // ---------------- epilogue: group g takes the tiles whose local index has parity g (256-wide
+    // tiles: every tile, its half g of the columns)
     const int ew = warp - GW - 1;
     const int g = ew >> 2;
     const int quarter = warp & 3;           // TMEM lanes a warp may read: 32 * (warp % 4) ...
@@ -661,7 +665,7 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
     // CG = 2: the accumulator buffer is released on the leader's barrier
     const uint32_t acc_empty_leader0 = CG == 2 ? mapa_rank(smem_u32(&acc_empty[0]), 0) : 0u;
     for (int u = u0; u < nunits; u += ustep, ++local) {
-      if ((local & 1u) != (uint32_t)g) continue;
+      if (!Cfg::SPLIT && (local & 1u) != (uint32_t)g) continue;
       const int tile = unit_tile<CG>(a, u, rank);
       const uint32_t buf = local % Cfg::NBUF, use = local / Cfg::NBUF;
       bool ok = mbar_wait(&acc_full[buf], use & 1u);
@@ -705,7 +709,9 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
         const int nsub = o8 ? 1 : Cfg::NSUB;
         const int sub_ch = o8 ? Cfg::SWC : Cfg::SUB;
         const int sub_bytes = o8 ? 128 * Cfg::SWC : Cfg::SUB_BYTES;
-        for (int p = 0; p < Cfg::PASSES; ++p) {
+        const int p_begin = Cfg::SPLIT ? g * (Cfg::PASSES / 2) : 0;
+        const int p_end = Cfg::SPLIT ? p_begin + Cfg::PASSES / 2 : Cfg::PASSES;
+        for (int p = p_begin; p < p_end; ++p) {
           stg = stg_base + (npass++ % Cfg::SDEPTH) * Cfg::C_BYTES;
           const bool live = tile_live(a, tc);
           const bool use_res = a.tma_res && ok && live;
@@ -832,7 +838,7 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
             for (int u = 0; u < 4; ++u)
               if (u < nu) *reinterpret_cast<uint4*>(qa[u]) = outv[u];
           }
-          if (p == Cfg::PASSES - 1) {
+          if (p == p_end - 1) {
             tc_fence_before();
             __syncwarp();
             if (lane == 0) {                   // accumulator buffer free for the MMA
@@ -867,7 +873,7 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
         // direct: one pixel row per thread (f32 heads, upsampled laterals)
         if (!ok || aborted(&s_abort)) valid = false;
 #pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 32) {
+        for (int c0 = Cfg::SPLIT ? g * (BN / 2) : 0; c0 < (Cfg::SPLIT ? (g + 1) * (BN / 2) : BN); c0 += 32) {
           uint32_t r[32];
           tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + buf * BN + (uint32_t)c0, r);
           tmem_ld_wait();
