@@ -320,6 +320,15 @@ JDE_DEV uint64_t smem_desc_noswz(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   return d;   // layout type 0: no swizzle
 }
 
+// 32 lanes x 16 consecutive 32-bit TMEM columns -> registers r[0..15] per thread.
+JDE_DEV void tmem_ld16(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
 // 32 lanes x 32 consecutive 32-bit TMEM columns -> 32 registers per thread.
 JDE_DEV void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(

@@ -701,7 +701,70 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
         x = tc.ox0 + row % a.TW;
         valid = y < c.Ho && x < c.Wo && tile_live(a, tc);
       }
-      if (a.tma_out) {
+      if (a.tma_out && c.out.dtype == 0) {
+        // staged f32 (the embedding heads): sub-passes of FW columns, each one staging tile
+        // (128-byte rows with the 128-byte swizzle, or 64-byte rows with the 64-byte one) and one
+        // TMA store box; rows on the halo are written as zeros
+        constexpr int FW = Cfg::C_BYTES / (128 * 4);
+        constexpr int NSP = BN / FW;
+        const int sp_begin = Cfg::SPLIT ? g * (NSP / 2) : 0;
+        const int sp_end = Cfg::SPLIT ? sp_begin + NSP / 2 : NSP;
+        for (int sp = sp_begin; sp < sp_end; ++sp) {
+          stg = stg_base + (npass++ % Cfg::SDEPTH) * Cfg::C_BYTES;
+          const bool live = tile_live(a, tc);
+          const int c0 = sp * FW;
+          uint32_t r[32];
+          const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + buf * BN + (uint32_t)c0;
+          if (FW == 32)
+            tmem_ld32(taddr, r);
+          else
+            tmem_ld16(taddr, r);
+          if (elected) bulk_wait_read<Cfg::SDEPTH - 1>();   // the store that last used this staging tile has read it
+          named_bar(bar_id, 128);
+          float v[FW];
+#pragma unroll
+          for (int j = 0; j < FW; ++j) v[j] = sBias[c0 + j];
+          float m[FW];
+          if (Q) {
+#pragma unroll
+            for (int j = 0; j < FW; ++j) m[j] = sMult[c0 + j];
+          }
+          tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < FW; ++j) {
+            const float acc = Q ? __uint_as_float(r[j]) * m[j] : __uint_as_float(r[j]);
+            const float t = acc + v[j];
+            v[j] = c.act ? leaky01(t) : t;
+          }
+#pragma unroll
+          for (int u = 0; u < FW / 4; ++u) {
+            uint8_t* q = stg + (FW == 32 ? stage_off<64>(row, u) : stage_off<32>(row, u));
+            *reinterpret_cast<uint4*>(q) =
+                valid ? make_uint4(__float_as_uint(v[4 * u]), __float_as_uint(v[4 * u + 1]),
+                                   __float_as_uint(v[4 * u + 2]), __float_as_uint(v[4 * u + 3]))
+                      : make_uint4(0u, 0u, 0u, 0u);
+          }
+          if (sp == sp_end - 1) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {                   // accumulator buffer free for the MMA
+              if (CG == 2)
+                mbar_arrive_cluster(acc_empty_leader0 + buf * 8u);
+              else
+                mbar_arrive(&acc_empty[buf]);
+            }
+          }
+          fence_proxy_async();               // staging writes visible to the TMA store
+          named_bar(bar_id, 128);
+          if (elected && ok && live && !aborted(&s_abort)) {
+            if (!patch_mode(a.mode))
+              tma_store_2d(&plan.o, stg, tc.n0 + c0, tc.m0);
+            else
+              tma_store_4d(&plan.o, stg, tc.n0 + c0, tc.ox0 + 1, tc.oy0 + 1, tc.img);
+            bulk_commit();
+          }
+        }
+      } else if (a.tma_out) {
         // staged: TMEM -> (scale, bias, leaky, + residual) -> bf16 or E4M3 staging tile -> TMA store.
         // Rows on the halo are written as zeros, which keeps the halo zero.  E4M3 rows are SWC
         // bytes (64-byte swizzle), one box per pass.
@@ -959,17 +1022,21 @@ EncodeTiledFn encode_fn() {
 
 // bkc: elements of the innermost box dimension; its bytes (2 per bf16, 1 per E4M3 code when u8)
 // choose the swizzle: 128 -> 128-byte, 64 -> 64-byte, 32 -> 32-byte, otherwise none.
+// f32: the box's inner extent `bkc` counts f32 elements (4 bytes each).
 bool encode(CUtensorMap* m, int rank, void* base, const cuuint64_t* dims, const cuuint64_t* strides_bytes,
-            const cuuint32_t* box, int bkc, bool u8 = false) {
+            const cuuint32_t* box, int bkc, bool u8 = false, bool f32 = false) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   cuuint32_t es[5] = {1, 1, 1, 1, 1};
-  const int row_bytes = bkc * (u8 ? 1 : 2);
+  const int row_bytes = bkc * (f32 ? 4 : (u8 ? 1 : 2));
   const CUtensorMapSwizzle swz = row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
                                  : row_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
                                  : row_bytes == 32 ? CU_TENSOR_MAP_SWIZZLE_32B
                                                    : CU_TENSOR_MAP_SWIZZLE_NONE;
-  CUresult r = fn(m, u8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, base,
+  const CUtensorMapDataType dt = f32  ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : u8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                      : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  CUresult r = fn(m, dt, (cuuint32_t)rank, base,
                   dims, strides_bytes, box, es,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -1252,18 +1319,28 @@ bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const void* w_any, int cout_p
   const int sub = o8 ? 64 : (bn < 64 ? bn : 64);
   const int oe = o8 ? 1 : 2;
   plan.tma_out = (c.out.dtype == 1 || o8) && !c.upsample && c.out.pad == 1 && c.cout % sub == 0;
+  // f32 outputs (padded embedding heads) of flat tiles: boxes of fw channels (64- or 128-byte rows)
+  const int fw = q ? 16 : 32;
+  const bool o32 = c.out.dtype == 0 && !c.upsample && c.out.pad == 1 && bn >= 64 && c.cout % fw == 0 &&
+                   (plan.mode == 0 || plan.mode == 4);
+  if (o32) plan.tma_out = 1;
   // residual stored in place under the output (bf16): added by the store itself (TMA reduce-add)
   plan.red_res = plan.tma_out && c.res.ptr != nullptr && c.res.ptr == c.out.ptr && c.out.dtype == 1 &&
                  c.res.dtype == 1 && c.res.pixstride == c.out.pixstride && c.res.pad == 1;
   plan.tma_res = !plan.red_res && plan.tma_out && c.res.ptr != nullptr && c.stride == 1 &&
                  c.res.dtype == c.out.dtype && c.res.pad == 1;
-  if (q && !o8 && plan.tma_out) {
+  if (q && !o8 && !o32 && plan.tma_out) {
     snprintf(msg, msg_len, "E4M3 conv: staged outputs must be E4M3");
     return false;
   }
   if (plan.tma_out) {
     const int Ho = c.Ho, Wo = c.Wo;
-    if (plan.mode == 0 || plan.mode == 4) {
+    if (o32) {
+      cuuint64_t dims[2] = {(cuuint64_t)c.cout, (cuuint64_t)plan.M_total};
+      cuuint64_t strides[1] = {(cuuint64_t)c.out.pixstride * 4};
+      cuuint32_t box[2] = {(cuuint32_t)fw, 128};
+      ok &= encode(&plan.o, 2, c.out.ptr, dims, strides, box, fw, false, true);
+    } else if (plan.mode == 0 || plan.mode == 4) {
       cuuint64_t dims[2] = {(cuuint64_t)c.cout, (cuuint64_t)plan.M_total};
       cuuint64_t strides[1] = {(cuuint64_t)c.out.pixstride * oe};
       cuuint32_t box[2] = {(cuuint32_t)sub, 128};
@@ -1287,6 +1364,17 @@ bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const void* w_any, int cout_p
     return false;
   }
   return true;
+}
+
+bool conv_tc_retarget(TcPlan& p, void* out) {
+  p.spec.out.ptr = out;
+  if (!p.tma_out) return true;
+  if (p.spec.out.dtype != 0 || !(p.mode == 0 || p.mode == 4)) return false;   // only f32 heads move
+  const int fw = p.q ? 16 : 32;
+  cuuint64_t dims[2] = {(cuuint64_t)p.spec.cout, (cuuint64_t)p.M_total};
+  cuuint64_t strides[1] = {(cuuint64_t)p.spec.out.pixstride * 4};
+  cuuint32_t box[2] = {(cuuint32_t)fw, 128};
+  return encode(&p.o, 2, out, dims, strides, box, fw, false, true);
 }
 
 cudaError_t conv_tc_launch(const TcPlan& p, cudaStream_t st) {

@@ -57,6 +57,9 @@ struct TcPlan {
 bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const void* w, int cout_pad, int bn, char* msg,
                   size_t msg_len);
 cudaError_t conv_tc_launch(const TcPlan& plan, cudaStream_t st);
+// Point a planned conv at another output buffer of the same shape (the double-buffered heads);
+// re-encodes the output tensor map of a TMA-stored f32 head.  False if the map cannot be built.
+bool conv_tc_retarget(TcPlan& plan, void* out);
 int conv_tc_pick_bn(int cout);
 
 // Letterbox geometry tables (per output column / row): source index pair and weight.
@@ -80,6 +83,7 @@ struct HeadGeom {
   float anchor_w[12], anchor_h[12];
   int stride[3];
   float ratio, pad_x, pad_y;
+  int epad;              // embedding maps carry a zero halo of this width (0 or 1)
 };
 struct PostBufs {
   uint64_t* cand_keys;   // [n][cand_cap]

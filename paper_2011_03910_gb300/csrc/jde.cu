@@ -297,7 +297,9 @@ void tensor_desc_table(const jde_handle* h, int in_w, int in_h, std::vector<Tens
     const int dt = (prec == JDE_FP32 || h->io[l].head >= 0) ? 0
                    : (prec == JDE_FP8_E4M3 && (int)l >= FP8_FIRST_OUT) ? 2 : 1;
     TensorDesc d{oh[l], ow[l], L[l].cout, 1, dt, -1, 0};
-    if (h->io[l].head >= 0) d.pad = 0;
+    // heads are unpadded f32, except the tensor-core path's embedding maps, which keep the zero
+    // halo so that their convs store whole flat tiles with TMA
+    if (h->io[l].head >= 0) d.pad = (bf16 && h->io[l].head >= 3) ? 1 : 0;
     if (h->io[l].out != (int)l) {
       d.alias = h->io[l].out;
       d.alias_off = h->io[l].out_slice;
@@ -877,7 +879,8 @@ jde_status jde_forward(jde_handle* h, const uint8_t* frames, int n, int src_w, i
     if (h->io[l].head < 0) continue;
     void* p = static_cast<char*>(rb->mem[l]) + (size_t)set * rb->set_bytes[l];
     plan->specs[l].out.ptr = p;
-    if (bf16) plan->tc[l].spec.out.ptr = p;
+    if (bf16 && !conv_tc_retarget(plan->tc[l], p))
+      return fail(h, JDE_ERR_CUDA, "layer %zu: output tensor map for head set %d", l, set);
   }
   if (h->prof[1]) cudaEventRecord(h->prof[1], st);
   for (size_t l = 0; l < L.size(); ++l) {
@@ -928,6 +931,9 @@ jde_status jde_postprocess(jde_handle* h, const float* const* heads, int n, int 
   HeadGeom g;
   memset(&g, 0, sizeof(g));
   g.n = n;
+  if (!heads)   // the handle's own embedding maps (padded on the tensor-core path)
+    for (size_t l = 0; l < layers().size(); ++l)
+      if (h->io[l].head == 3) g.epad = h->cur->td[l].pad;
   const int strides[3] = {32, 16, 8};
   const float base[3] = {128.f, 32.f, 8.f};
   g.off[0] = 0;

@@ -259,7 +259,9 @@ __global__ void emit_kernel(const float* e0, const float* e1, const float* e2, H
   const int gi = (int)(sorted[o] & 0xFFFFFFFFu);
   int s, a, y, x;
   locate(g, gi, s, a, y, x);
-  const float* e = (s == 0 ? e0 : (s == 1 ? e1 : e2)) + ((size_t)(n * g.gh[s] + y) * g.gw[s] + x) * 512;
+  const int ep = g.epad;
+  const float* e = (s == 0 ? e0 : (s == 1 ? e1 : e2)) +
+                   ((size_t)(n * (g.gh[s] + 2 * ep) + y + ep) * (g.gw[s] + 2 * ep) + x + ep) * 512;
   float v[16];
   float ss = 0.f;
 #pragma unroll
