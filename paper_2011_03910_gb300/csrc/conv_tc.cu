@@ -313,6 +313,10 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
         tma_load_2d(sB + s * Cfg::B_BYTES, &plan.b, &full[s], 0, tc.n0);
       }
       uint8_t* dA = sA + s * Cfg::A_BYTES;
+      // tap (ky, kx) of a pixel is a constant element offset from the pixel itself (the letterbox
+      // and the flat tile share the padded grid); the letterbox halo is zero, so every tap of an
+      // in-image pixel is addressable
+      const int tap_step = a.Wp * c.in.pixstride;
       uint2 q[4][9];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {          // issue all 36 loads before using any
@@ -321,12 +325,13 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
         const int n = m / plane, rem = m % plane;
         const int y = rem / a.Wp - 1, x = rem % a.Wp - 1;
         const bool in = m < a.M_total && y >= 0 && y < c.Ho && x >= 0 && x < c.Wo;
+        const __nv_bfloat16* pix = lb + tview_off(c.in, n, y, x);
 #pragma unroll
         for (int ky = 0; ky < 3; ++ky)
 #pragma unroll
           for (int kx = 0; kx < 3; ++kx)
-            // the letterbox halo is zero: (y + ky - 1, x + kx - 1) is always addressable
-            q[i][ky * 3 + kx] = in ? *reinterpret_cast<const uint2*>(lb + tview_off(c.in, n, y + ky - 1, x + kx - 1))
+            q[i][ky * 3 + kx] = in ? __ldg(reinterpret_cast<const uint2*>(pix + (ky - 1) * tap_step +
+                                                                           (kx - 1) * c.in.pixstride))
                                    : make_uint2(0u, 0u);
       }
 #pragma unroll
@@ -662,6 +667,7 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
     float* const sMult = sBiasAll + 2 * BN + g * BN;       // Q: input scale x weight scale per channel
     const int gtid = (ew & 3) * 32 + lane;
     int bias_n0 = -1;
+    float4 breg[8];                         // 32-wide tiles: the tile's bias in registers
     // CG = 2: the accumulator buffer is released on the leader's barrier
     const uint32_t acc_empty_leader0 = CG == 2 ? mapa_rank(smem_u32(&acc_empty[0]), 0) : 0u;
     for (int u = u0; u < nunits; u += ustep, ++local) {
@@ -684,6 +690,10 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
         }
         named_bar(bar_id, 128);
         bias_n0 = tc.n0;
+        if (BN == 32) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) breg[i] = reinterpret_cast<const float4*>(sBias)[i];
+        }
       }
       int n = 0, y = 0, x = 0;
       bool valid;
@@ -816,7 +826,7 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
             const float4* b4 = reinterpret_cast<const float4*>(sBias + p * Cfg::SWC + c0);
             float4 bb[8], mm[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) bb[i] = b4[i];
+            for (int i = 0; i < 8; ++i) bb[i] = BN == 32 ? breg[i] : b4[i];
             if (Q) {
               const float4* m4 = reinterpret_cast<const float4*>(sMult + p * Cfg::SWC + c0);
 #pragma unroll
