@@ -207,6 +207,7 @@ def run_fp8(torch, jde, dev, blob, stream, table, B=32, K=20, autotune=True):
     ccfg.max_streams = 1
     ccfg.device = dev.index or 0
     ccfg.keep_layer_outputs = 1
+    ccfg.sparse_emb = 0
     hc = jde.jde_create(ccfg, blob)
     for i in range(4):
         cal = torch.from_numpy(synth.frames_uniform(1000 + i, 16, SRC_H, SRC_W)).to(dev)

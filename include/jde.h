@@ -87,6 +87,12 @@ typedef struct {
                              of Sec. 3 done by a TMA reduce-add), so the blocks' inputs are not kept
                              and jde_get_tensor / jde_act_amax refuse them; 1: every conv layer keeps
                              its own output tensor (per-layer inspection, calibration) */
+  int sparse_emb;       /* tensor-core handles, 1 (default): the embedding heads (Sec. 3.1, the linear
+                           3x3 -> 512 of each scale) are evaluated only at the detections kept by NMS,
+                           inside the post-processing of the handle's own forward (jde_detect_batch,
+                           jde_postprocess with heads NULL), from copies of their input maps; their
+                           dense maps are not computed (jde_get_tensor and jde_act_amax refuse them).
+                           0: dense embedding maps */
 } jde_config;
 
 /* One layer of the network as this library builds it (for the weights blob). */

@@ -98,6 +98,22 @@ struct PostBufs {
   int* keep_idx;         // [n][kmax] positions in sorted order
   int* n_keep;           // [n]
   int kmax;
+  int4* emb_list;        // [3][n * kmax] sparse embedding head: (frame, row, y, x) per kept detection
+  int* emb_count;        // [3] kept detections per scale
 };
+// Sparse embedding head (Sec. 3.1, the linear 3x3 -> 512 of each scale) evaluated only at the
+// locations kept by NMS: per scale the head's input feature map, its weights and epilogue constants.
+struct EmbSparse {
+  TView in[3];           // padded NHWC input of the head (bf16 or E4M3 codes)
+  const void* w[3];      // [cout_pad][K] bf16, or E4M3 codes when q[s]
+  const float* bias[3];  // [>= 512]
+  const float* mult[3];  // E4M3: input scale x weight scale per channel, else null
+  int cin[3];
+  int ldw[3];            // elements per weight row (>= 9 cin)
+  int q[3];
+};
+// es != null: the embedding maps heads[3..5] are not read; the kept detections' embeddings are
+// computed from es (sparse head) into their rows, then normalised.
 void post_launch(const float* const* heads, const HeadGeom& g, float conf_thresh, float nms_iou, PostBufs& b,
-                 float* rows, int32_t* count, int32_t* anchor_index, int cap, int* err, cudaStream_t st);
+                 float* rows, int32_t* count, int32_t* anchor_index, int cap, int* err, cudaStream_t st,
+                 const EmbSparse* es = nullptr);

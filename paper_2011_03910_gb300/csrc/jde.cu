@@ -95,6 +95,8 @@ struct LayerW {
 constexpr int FP8_FIRST_OUT = 4;
 bool is_q_layer(int precision, int l) { return precision == JDE_FP8_E4M3 && l > FP8_FIRST_OUT; }
 int el_size(int dt) { return dt == 0 ? 4 : (dt == 1 ? 2 : 1); }
+// Sparse embedding head: tensor-core handles with sparse_emb set.
+bool sparse_emb_cfg(const jde_config& c) { return c.sparse_emb && c.precision != JDE_FP32; }
 
 // Where each conv reads and writes (tensor ids below, -1 = none).
 struct LayerIO {
@@ -105,8 +107,10 @@ struct LayerIO {
   int head;        // output is a head tensor (f32, unpadded): 0..2 det, 3..5 emb, -1 otherwise
 };
 
-// Tensor ids: 0..77 = output of layer l, 78 = cat16, 79 = cat8, 80 = letterbox.
-enum { T_CAT16 = 78, T_CAT8 = 79, T_LB = 80, T_COUNT = 81 };
+// Tensor ids: 0..77 = output of layer l, 78 = cat16, 79 = cat8, 80 = letterbox, 81..83 = copies of
+// the embedding heads' input maps (strides 32, 16, 8) kept for the sparse embedding head of the
+// post-processing (two sets, like the heads).
+enum { T_CAT16 = 78, T_CAT8 = 79, T_LB = 80, T_PF = 81, T_COUNT = 84 };
 
 struct TensorDesc {
   int h, w, c;     // unpadded size at the given input resolution (per frame)
@@ -314,6 +318,23 @@ void tensor_desc_table(const jde_handle* h, int in_w, int in_h, std::vector<Tens
   td[T_CAT16] = TensorDesc{in_h / 16, in_w / 16, 768, 1, cat_dt, -1, 0};
   td[T_CAT8] = TensorDesc{in_h / 8, in_w / 8, 384, 1, cat_dt, -1, 0};
   td[T_LB] = TensorDesc{in_h, in_w, bf16 ? 4 : 3, 1, bf16 ? 1 : 0, -1, 0};
+  // copies of the embedding heads' inputs (sparse head): same shape and storage type as the map
+  for (size_t l = 0; l < L.size(); ++l)
+    if (h->io[l].head >= 3) {
+      const int src = h->io[l].in;
+      td[T_PF + h->io[l].head - 3] = td[src];
+      if (!sparse_emb_cfg(h->cfg)) td[T_PF + h->io[l].head - 3].alias = src;   // not kept
+    }
+}
+
+// Storage of a tensor id in two sets (written by alternate forwards): the heads and, for the
+// sparse embedding head, the copies of its input maps.
+bool two_sets(const jde_handle* h, int t) {
+  return (t < JDE_NUM_LAYERS && h->io[t].head >= 0) || (t >= T_PF && t < T_PF + 3);
+}
+// Tensor not allocated: the embedding heads when they are evaluated sparsely.
+bool not_stored(const jde_handle* h, int t) {
+  return t < JDE_NUM_LAYERS && h->io[t].head >= 3 && sparse_emb_cfg(h->cfg);
 }
 
 size_t tensor_bytes(const TensorDesc& d, int n) {
@@ -338,10 +359,9 @@ jde_status get_res(jde_handle* h, int in_w, int in_h, ResBuffers** out) {
   const int n = h->cfg.max_batch;
   const bool bf16 = h->cfg.precision != JDE_FP32;   // tensor-core path (BF16 / E4M3)
   for (int t = 0; t < T_COUNT; ++t) {
-    if (rb.td[t].alias >= 0) continue;
-    const bool head = t < JDE_NUM_LAYERS && h->io[t].head >= 0;
+    if (rb.td[t].alias >= 0 || not_stored(h, t)) continue;
     rb.set_bytes[t] = tensor_bytes(rb.td[t], n);
-    const size_t b = rb.set_bytes[t] * (head ? 2 : 1);
+    const size_t b = rb.set_bytes[t] * (two_sets(h, t) ? 2 : 1);
     if (!dmalloc(&rb.mem[t], b)) {
       for (void* p : rb.mem)
         if (p) cudaFree(p);
@@ -414,6 +434,7 @@ jde_status get_plan(jde_handle* h, ResBuffers* rb, int n, Plan** out) {
   if (bf16) p.tc.resize(L.size());
   for (size_t l = 0; l < L.size(); ++l) {
     const LayerIO& io = h->io[l];
+    if (not_stored(h, (int)l)) continue;   // sparse embedding head: evaluated in the post-processing
     ConvSpec c;
     memset(&c, 0, sizeof(c));
     c.k = L[l].k;
@@ -558,7 +579,7 @@ size_t post_bytes(int n, int anchors, int kmax) {
   const size_t N = (size_t)n, K = (size_t)kmax;
   return N * anchors * sizeof(uint64_t) + N * sizeof(int) + N * K * sizeof(uint64_t) + N * sizeof(int) +
          N * K * sizeof(float4) + 2 * N * K * sizeof(float) + N * K * (K / 64) * sizeof(unsigned long long) +
-         N * K * sizeof(int) + N * sizeof(int);
+         N * K * sizeof(int) + N * sizeof(int) + 3 * N * K * sizeof(int4) + 3 * sizeof(int);
 }
 
 int anchors_for(int in_w, int in_h) {
@@ -669,7 +690,7 @@ jde_status ensure_post(jde_handle* h, int n) {
   if (h->pb_n >= n && h->pb.cand_keys) return JDE_OK;
   PostBufs& b = h->pb;
   void* ptrs[] = {b.cand_keys, b.cand_count, b.sorted, b.n_sorted, b.boxes, b.conf, b.cls, b.mask, b.keep_idx,
-                  b.n_keep};
+                  b.n_keep, b.emb_list, b.emb_count};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   const int kmax = h->cfg.max_cand;
@@ -683,7 +704,9 @@ jde_status ensure_post(jde_handle* h, int n) {
             dmalloc((void**)&b.conf, sizeof(float) * (size_t)n * kmax) &&
             dmalloc((void**)&b.cls, sizeof(float) * (size_t)n * kmax) &&
             dmalloc((void**)&b.mask, sizeof(unsigned long long) * (size_t)n * kmax * (kmax / 64)) &&
-            dmalloc((void**)&b.keep_idx, sizeof(int) * (size_t)n * kmax) && dmalloc((void**)&b.n_keep, sizeof(int) * n);
+            dmalloc((void**)&b.keep_idx, sizeof(int) * (size_t)n * kmax) && dmalloc((void**)&b.n_keep, sizeof(int) * n) &&
+            dmalloc((void**)&b.emb_list, sizeof(int4) * 3 * (size_t)n * kmax) &&
+            dmalloc((void**)&b.emb_count, sizeof(int) * 3);
   if (!ok) return fail(h, JDE_ERR_OOM, "post-processing buffers for %d frames", n);
   h->pb_n = n;
   return JDE_OK;
@@ -760,6 +783,7 @@ void jde_default_config(jde_config* c) {
   c->max_tracks = 1024;
   c->max_track_dets = 1024;
   c->device = 0;
+  c->sparse_emb = 1;
 }
 
 int jde_layer_table(jde_layer_desc* out, int cap) {
@@ -876,7 +900,7 @@ jde_status jde_forward(jde_handle* h, const uint8_t* frames, int n, int src_w, i
   // head tensors are double-buffered: this forward writes set head_set
   const int set = h->head_set;
   for (size_t l = 0; l < L.size(); ++l) {
-    if (h->io[l].head < 0) continue;
+    if (h->io[l].head < 0 || not_stored(h, (int)l)) continue;
     void* p = static_cast<char*>(rb->mem[l]) + (size_t)set * rb->set_bytes[l];
     plan->specs[l].out.ptr = p;
     if (bf16 && !conv_tc_retarget(plan->tc[l], p))
@@ -884,12 +908,24 @@ jde_status jde_forward(jde_handle* h, const uint8_t* frames, int n, int src_w, i
   }
   if (h->prof[1]) cudaEventRecord(h->prof[1], st);
   for (size_t l = 0; l < L.size(); ++l) {
+    if (not_stored(h, (int)l)) continue;
     if (bf16) {
       cudaError_t e = conv_tc_launch(plan->tc[l], st);
       if (e != cudaSuccess) return fail(h, JDE_ERR_CUDA, "conv layer %zu: %s", l, cudaGetErrorString(e));
     } else {
       conv_simt_launch(plan->specs[l], h->w[l].w_kn, h->w[l].cout_pad64, st);
     }
+  }
+  // sparse embedding head: keep this forward's head inputs for its post-processing (set `set`)
+  for (int s = 0; s < 3; ++s) {
+    const int t = T_PF + s;
+    if (!rb->mem[t]) continue;
+    int src = -1;
+    for (size_t l = 0; l < L.size(); ++l)
+      if (h->io[l].head == 3 + s) src = h->io[l].in;
+    const size_t bytes = tensor_bytes(rb->td[src], n);
+    CUDA_OR(h, cudaMemcpyAsync(static_cast<char*>(rb->mem[t]) + (size_t)set * rb->set_bytes[t], rb->mem[src], bytes,
+                               cudaMemcpyDeviceToDevice, st));
   }
   if (h->prof[2]) cudaEventRecord(h->prof[2], st);
   cudaError_t e = cudaGetLastError();
@@ -976,7 +1012,30 @@ jde_status jde_postprocess(jde_handle* h, const float* const* heads, int n, int 
     count = h->count_stage;
     aidx = out->anchor_index ? h->aidx_stage : nullptr;
   }
-  post_launch(hp, g, h->cfg.conf_thresh, h->cfg.nms_iou, h->pb, rows, count, aidx, out->cap, h->d_err, st);
+  // the handle's own forward with a sparse embedding head: its input maps of the last forward
+  EmbSparse es;
+  memset(&es, 0, sizeof(es));
+  const bool sparse = !heads && sparse_emb_cfg(h->cfg);
+  if (sparse) {
+    const auto& L = layers();
+    for (size_t l = 0; l < L.size(); ++l) {
+      const int hd = h->io[l].head;
+      if (hd < 3) continue;
+      const int s = hd - 3, t = T_PF + s;
+      TView v = view_of(*h->cur, h->io[l].in, n);
+      v.ptr = static_cast<char*>(h->cur->mem[t]) + (size_t)h->cur_set * h->cur->set_bytes[t];
+      const LayerW& lw = h->w[l];
+      es.in[s] = v;
+      es.w[s] = lw.q ? static_cast<const void*>(lw.w_q) : static_cast<const void*>(lw.w_nk);
+      es.bias[s] = lw.bias;
+      es.mult[s] = lw.q ? lw.mult : nullptr;
+      es.cin[s] = L[l].cin;
+      es.ldw[s] = lw.k_tc;
+      es.q[s] = lw.q;
+    }
+  }
+  post_launch(hp, g, h->cfg.conf_thresh, h->cfg.nms_iou, h->pb, rows, count, aidx, out->cap, h->d_err, st,
+              sparse ? &es : nullptr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(h, JDE_ERR_CUDA, "post-processing launch: %s", cudaGetErrorString(e));
   if (!out->on_device) {
@@ -1011,6 +1070,8 @@ jde_status jde_get_tensor(jde_handle* h, int id, void* dst, size_t dst_bytes, in
   if (!h) return fail(nullptr, JDE_ERR_INVALID_ARG, "handle is NULL");
   if (!h->cur) return fail(h, JDE_ERR_NOT_FOUND, "no forward has run");
   int tid;
+  if (id >= 0 && id < JDE_NUM_LAYERS && not_stored(h, id))
+    return fail(h, JDE_ERR_NOT_FOUND, "tensor %d: the embedding head runs only at kept detections (sparse_emb)", id);
   if (id >= 0 && id < JDE_NUM_LAYERS && overwritten(h, id))
     return fail(h, JDE_ERR_NOT_FOUND, "tensor %d is overwritten in place by its residual block (keep_layer_outputs)", id);
   if (id >= 0 && id < JDE_NUM_LAYERS)
@@ -1072,8 +1133,9 @@ jde_status jde_act_amax(jde_handle* h, float* amax, void* stream) {
   if (!amax) return fail(h, JDE_ERR_INVALID_ARG, "jde_act_amax: amax is NULL");
   if (!h->cur) return fail(h, JDE_ERR_INVALID_ARG, "jde_act_amax: no forward has run");
   for (int l = 0; l < JDE_NUM_LAYERS; ++l)
-    if (overwritten(h, l))
-      return fail(h, JDE_ERR_UNSUPPORTED, "jde_act_amax: layer outputs are not kept (keep_layer_outputs = 0)");
+    if (overwritten(h, l) || not_stored(h, l))
+      return fail(h, JDE_ERR_UNSUPPORTED,
+                  "jde_act_amax: layer outputs are not kept (needs keep_layer_outputs = 1, sparse_emb = 0)");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (!h->d_amax && !dmalloc((void**)&h->d_amax, sizeof(float) * JDE_NUM_LAYERS))
     return fail(h, JDE_ERR_OOM, "amax scratch");
@@ -1112,6 +1174,7 @@ jde_status jde_autotune(jde_handle* h, int n, int in_w, int in_h, void* stream) 
   CUDA_OR(h, cudaEventCreate(&e0));
   CUDA_OR(h, cudaEventCreate(&e1));
   for (int l = 0; l < JDE_NUM_LAYERS; ++l) {
+    if (not_stored(h, l)) continue;                  // sparse embedding head: not a conv launch
     const TcPlan& def = plan->tc[l];
     if (def.mode == 2 || def.mode == 3) continue;    // stem and window convs have one tile shape
     const LayerW& lw = h->w[l];
@@ -1183,9 +1246,8 @@ jde_status jde_estimate_device_bytes(const jde_config* cfg, int in_w, int in_h, 
   std::vector<TensorDesc> td;
   tensor_desc_table(&tmp, in_w, in_h, td);
   for (int t = 0; t < T_COUNT; ++t) {
-    if (td[t].alias >= 0) continue;
-    const bool head = t < JDE_NUM_LAYERS && tmp.io[t].head >= 0;
-    b += tensor_bytes(td[t], cfg->max_batch) * (head ? 2 : 1);
+    if (td[t].alias >= 0 || not_stored(&tmp, t)) continue;
+    b += tensor_bytes(td[t], cfg->max_batch) * (two_sets(&tmp, t) ? 2 : 1);
   }
   b += post_bytes(cfg->max_batch, anchors_for(cfg->max_in_w, cfg->max_in_h), cfg->max_cand);
   b += track_bytes(*cfg);

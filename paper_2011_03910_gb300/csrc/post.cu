@@ -259,9 +259,12 @@ __global__ void emit_kernel(const float* e0, const float* e1, const float* e2, H
   const int gi = (int)(sorted[o] & 0xFFFFFFFFu);
   int s, a, y, x;
   locate(g, gi, s, a, y, x);
+  float* row = rows + ((size_t)n * cap + r) * 518;
   const int ep = g.epad;
-  const float* e = (s == 0 ? e0 : (s == 1 ? e1 : e2)) +
-                   ((size_t)(n * (g.gh[s] + 2 * ep) + y + ep) * (g.gw[s] + 2 * ep) + x + ep) * 512;
+  // sparse head (e0 null): the raw embedding was written into the row by emb_gemm_kernel
+  const float* e = e0 == nullptr ? row + 6
+                                 : (s == 0 ? e0 : (s == 1 ? e1 : e2)) +
+                                       ((size_t)(n * (g.gh[s] + 2 * ep) + y + ep) * (g.gw[s] + 2 * ep) + x + ep) * 512;
   float v[16];
   float ss = 0.f;
 #pragma unroll
@@ -275,7 +278,6 @@ __global__ void emit_kernel(const float* e0, const float* e1, const float* e2, H
   for (int off = 16; off > 0; off >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, off);
   const float nrm = sqrtf(ss);
   const float inv = nrm > 0.f ? 1.f / nrm : 0.f;
-  float* row = rows + ((size_t)n * cap + r) * 518;
 #pragma unroll
   for (int q = 0; q < 8; ++q)
     *reinterpret_cast<float2*>(row + 6 + q * 64 + lane * 2) = make_float2(v[2 * q] * inv, v[2 * q + 1] * inv);
@@ -291,10 +293,104 @@ __global__ void emit_kernel(const float* e0, const float* e1, const float* e2, H
   }
 }
 
+// Sparse embedding head, step 1: the kept detections of every frame, listed per scale as
+// (frame, row, y, x).
+__global__ void emb_list_kernel(HeadGeom g, const uint64_t* sorted, const int* keep_idx, const int* n_keep, int kmax,
+                                int cap, int4* list, int* count) {
+  const int n = blockIdx.x;
+  const int nk = min(n_keep[n], cap);
+  for (int r = threadIdx.x; r < nk; r += blockDim.x) {
+    const int p = keep_idx[(size_t)n * kmax + r];
+    const int gi = (int)(sorted[(size_t)n * kmax + p] & 0xFFFFFFFFu);
+    int s, a, y, x;
+    locate(g, gi, s, a, y, x);
+    const int slot = atomicAdd(&count[s], 1);
+    list[(size_t)s * g.n * kmax + slot] = make_int4(n, r, y, x);
+  }
+}
+
+__device__ __forceinline__ float e4m3_value(uint8_t code) { return e4m3x2_to_float2((uint32_t)code).x; }
+
+// Sparse embedding head, step 2: for the listed detections of scale blockIdx.z, out[o] = sum_k
+// W[o][k] x[k] over K = (tap, channel) of the 3x3 input patch around (y, x), times the E4M3
+// dequantisation multiplier, plus the bias; the raw (unnormalised) values go into the detection's
+// row.  Tiles of 32 detections x 128 outputs, fp32 accumulation, K in chunks of 32 (one tap each).
+constexpr int EG_D = 32, EG_O = 128, EG_K = 32;
+__global__ void __launch_bounds__(256) emb_gemm_kernel(EmbSparse es, const int4* list, const int* count, int list_stride,
+                                                       float* rows, int cap) {
+  const int s = blockIdx.z;
+  const int o0 = blockIdx.y * EG_O;
+  const int total = count[s];
+  const TView in = es.in[s];
+  const int cin = es.cin[s], K = 9 * cin, ldw = es.ldw[s], q = es.q[s];
+  __shared__ float As[EG_K][EG_D + 1];
+  __shared__ float Bs[EG_K][EG_O + 4];
+  __shared__ int4 ent[EG_D];
+  const int t = threadIdx.x;
+  const int to = (t % 32) * 4;          // 4 outputs
+  const int td = (t / 32) * 4;          // 4 detections
+  for (int d0 = blockIdx.x * EG_D; d0 < total; d0 += gridDim.x * EG_D) {
+    __syncthreads();
+    if (t < EG_D) ent[t] = d0 + t < total ? list[(size_t)s * list_stride + d0 + t] : make_int4(-1, -1, 0, 0);
+    __syncthreads();
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += EG_K) {
+      const int tap = k0 / cin, c0 = k0 % cin;
+      const int ky = tap / 3, kx = tap % 3;
+      // A: 32 detections x 32 channels of one tap (4 per thread)
+      for (int i = t; i < EG_D * EG_K; i += 256) {
+        const int d = i / EG_K, kk = i % EG_K;
+        const int4 e = ent[d];
+        float v = 0.f;
+        if (e.x >= 0) {
+          const size_t off = tview_off(in, e.x, e.z + ky - 1, e.w + kx - 1) + c0 + kk;
+          v = q ? e4m3_value(static_cast<const uint8_t*>(in.ptr)[off])
+                : __bfloat162float(static_cast<const __nv_bfloat16*>(in.ptr)[off]);
+        }
+        As[kk][d] = v;
+      }
+      // B: 128 outputs x 32 K (16 per thread)
+      for (int i = t; i < EG_O * EG_K; i += 256) {
+        const int o = i / EG_K, kk = i % EG_K;
+        const size_t off = (size_t)(o0 + o) * ldw + k0 + kk;
+        Bs[kk][o] = q ? e4m3_value(static_cast<const uint8_t*>(es.w[s])[off])
+                      : __bfloat162float(static_cast<const __nv_bfloat16*>(es.w[s])[off]);
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int kk = 0; kk < EG_K; ++kk) {
+        float a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = As[kk][td + i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] = Bs[kk][to + j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int4 e = ent[td + i];
+      if (e.x < 0) continue;
+      float* row = rows + ((size_t)e.x * cap + e.y) * 518 + 6;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int o = o0 + to + j;
+        const float m = q ? es.mult[s][o] : 1.f;
+        row[o] = acc[i][j] * m + es.bias[s][o];
+      }
+    }
+  }
+}
+
 }  // namespace
 
 void post_launch(const float* const* heads, const HeadGeom& g, float conf_thresh, float nms_iou, PostBufs& b,
-                 float* rows, int32_t* count, int32_t* anchor_index, int cap, int* err, cudaStream_t st) {
+                 float* rows, int32_t* count, int32_t* anchor_index, int cap, int* err, cudaStream_t st,
+                 const EmbSparse* es) {
   (void)err;
   static bool attr = false;
   if (!attr) {
@@ -322,8 +418,18 @@ void post_launch(const float* const* heads, const HeadGeom& g, float conf_thresh
   jde_count_launch();
   nms_scan_kernel<<<(n + wpb - 1) / wpb, 32 * wpb, wpb * (b.kmax / 64) * sizeof(unsigned long long), st>>>(
       b.mask, b.n_sorted, b.kmax, b.keep_idx, b.n_keep, n);
+  if (es) {
+    cudaMemsetAsync(b.emb_count, 0, sizeof(int) * 3, st);
+    jde_count_launch();
+    emb_list_kernel<<<n, 256, 0, st>>>(g, b.sorted, b.keep_idx, b.n_keep, b.kmax, cap, b.emb_list, b.emb_count);
+    const int per = n * (cap < b.kmax ? cap : b.kmax);   // most detections of one scale
+    int gx = (per + EG_D - 1) / EG_D;
+    if (gx > 64) gx = 64;
+    jde_count_launch();
+    emb_gemm_kernel<<<dim3(gx, 512 / EG_O, 3), 256, 0, st>>>(*es, b.emb_list, b.emb_count, n * b.kmax, rows, cap);
+  }
   dim3 ge((b.kmax + 3) / 4, n);
   jde_count_launch();
-  emit_kernel<<<ge, 128, 0, st>>>(heads[3], heads[4], heads[5], g, b.sorted, b.boxes, b.conf, b.cls, b.keep_idx,
-                                  b.n_keep, b.kmax, rows, count, anchor_index, cap);
+  emit_kernel<<<ge, 128, 0, st>>>(es ? nullptr : heads[3], heads[4], heads[5], g, b.sorted, b.boxes, b.conf, b.cls,
+                                  b.keep_idx, b.n_keep, b.kmax, rows, count, anchor_index, cap);
 }

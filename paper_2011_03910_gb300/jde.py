@@ -33,7 +33,7 @@ class jde_config(C.Structure):
                 ("nms_iou", C.c_float), ("assign_thresh", C.c_float), ("gate_chi2", C.c_double),
                 ("lost_max_frames", C.c_int), ("emb_momentum", C.c_float), ("max_streams", C.c_int),
                 ("max_tracks", C.c_int), ("max_track_dets", C.c_int), ("device", C.c_int),
-                ("keep_layer_outputs", C.c_int)]
+                ("keep_layer_outputs", C.c_int), ("sparse_emb", C.c_int)]
 
 
 class jde_layer_desc(C.Structure):

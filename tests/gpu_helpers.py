@@ -35,6 +35,7 @@ def make_handle(precision, max_batch=2, in_w=320, in_h=192, src_w=1920, src_h=10
     cfg.max_batch = max_batch
     cfg.max_in_w, cfg.max_in_h = in_w, in_h
     cfg.max_src_w, cfg.max_src_h = src_w, src_h
+    kw.setdefault("sparse_emb", 0)     # the tests read the dense embedding maps unless they ask otherwise
     for k, v in kw.items():
         setattr(cfg, k, v)
     return j.jde_create(cfg, blob())

@@ -228,3 +228,54 @@ def test_bf16_other_resolutions_and_batches_on_one_handle(in_w, in_h, n):
         assert max(errs) < 2e-2
     finally:
         j.jde_destroy(h)
+
+
+def _detect_rows(j, h, frames, in_w, in_h, cap=1024):
+    n, sh, sw, _ = frames.shape
+    f = torch.from_numpy(np.ascontiguousarray(frames)).cuda()
+    rows = torch.zeros((n, cap, 518), dtype=torch.float32, device="cuda")
+    count = torch.zeros(n, dtype=torch.int32, device="cuda")
+    aidx = torch.full((n, cap), -1, dtype=torch.int32, device="cuda")
+    d = j.make_dets(rows, count, aidx, cap=cap)
+    j.jde_detect_batch(h, f, n, sw, sh, in_w, in_h, d, on_device=True, stream=torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    assert j.jde_kernel_errors(h) == 0
+    return rows.cpu().numpy(), count.cpu().numpy(), aidx.cpu().numpy()
+
+
+@pytest.mark.parametrize("precision,n,in_w,in_h", [("bf16", 2, 320, 192), ("bf16", 16, 1088, 608),
+                                                    ("fp8", 2, 320, 192)])
+def test_sparse_embedding_head_matches_the_dense_maps(precision, n, in_w, in_h):
+    """sparse_emb=1 (the default) evaluates the 512-channel embedding convs only at the kept detections:
+    the kept set, boxes, scores and anchor indices are bit-identical to the dense handle's (the detection
+    heads do not depend on the embedding convs) and the unit embeddings agree to float32 summation order;
+    the dense embedding maps are refused."""
+    import json
+    import os
+    j = jde()
+    prec = j.JDE_BF16 if precision == "bf16" else j.JDE_FP8_E4M3
+    frames = synth.frames_uniform(5, n, 1080, 1920)
+    out = {}
+    for sparse in (0, 1):
+        h = make_handle(prec, max_batch=n, in_w=in_w, in_h=in_h, sparse_emb=sparse)
+        try:
+            if precision == "fp8":
+                golden = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "fp8_amax_320x192.json")
+                j.jde_set_act_amax(h, json.load(open(golden))["amax"])
+            out[sparse] = _detect_rows(j, h, frames, in_w, in_h)
+            if sparse:
+                with pytest.raises(j.JdeError):
+                    get_tensor(h, 77)
+        finally:
+            j.jde_destroy(h)
+    (r0, c0, a0), (r1, c1, a1) = out[0], out[1]
+    np.testing.assert_array_equal(c0, c1)
+    assert c0.sum() > 0
+    for f in range(n):
+        k = min(int(c0[f]), r0.shape[1])
+        np.testing.assert_array_equal(a0[f, :k], a1[f, :k])
+        np.testing.assert_array_equal(r0[f, :k, :6], r1[f, :k, :6])
+        err = float(np.max(np.abs(r0[f, :k, 6:] - r1[f, :k, 6:]))) if k else 0.0
+        assert err < 1e-4, (f, err)
+        norms = np.linalg.norm(r1[f, :k, 6:], axis=1)
+        np.testing.assert_allclose(norms, 1.0, atol=1e-5)
