@@ -194,7 +194,7 @@ def build_heads_device(torch, clips, t, device):
     return dets + embs
 
 
-def run_fp8(torch, jde, dev, blob, stream, table, B=32, K=20, autotune=True):
+def run_fp8(torch, jde, dev, blob, stream, table, B=32, K=20, autotune=True, sparse_emb=0):
     """E4M3 network at 1088x608, batch 32: activation amax from 64 seeded calibration frames run through
     a BF16 handle that keeps every layer output (jde_act_amax, elementwise max over 4 batches of 16),
     then letterbox + forward + decode + confidence filter + NMS (jde_detect_batch) captured in one
@@ -221,6 +221,9 @@ def run_fp8(torch, jde, dev, blob, stream, table, B=32, K=20, autotune=True):
     cfg.max_batch = B
     cfg.max_streams = 1
     cfg.device = dev.index or 0
+    # synthetic weights on noise frames keep ~1600 detections per frame after NMS (256 rows kept per
+    # frame here); at that count the dense embedding maps cost less than the sparse head
+    cfg.sparse_emb = sparse_emb
     h8 = jde.jde_create(cfg, blob)
     jde.jde_set_act_amax(h8, amax)
     changed = None
@@ -391,6 +394,9 @@ def main():
     cfg.max_batch = B
     cfg.max_streams = B
     cfg.device = local
+    # the timed post-processing reads planted head maps (embeddings included): the forward computes
+    # the network's dense embedding maps too, so no part of the network is skipped
+    cfg.sparse_emb = 0
     h = jde.jde_create(cfg, blob)
     st = torch.cuda.current_stream()
     tiles = None

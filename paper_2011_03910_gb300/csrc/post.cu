@@ -314,74 +314,108 @@ __device__ __forceinline__ float e4m3_value(uint8_t code) { return e4m3x2_to_flo
 // Sparse embedding head, step 2: for the listed detections of scale blockIdx.z, out[o] = sum_k
 // W[o][k] x[k] over K = (tap, channel) of the 3x3 input patch around (y, x), times the E4M3
 // dequantisation multiplier, plus the bias; the raw (unnormalised) values go into the detection's
-// row.  Tiles of 32 detections x 128 outputs, fp32 accumulation, K in chunks of 32 (one tap each).
-constexpr int EG_D = 32, EG_O = 128, EG_K = 32;
+// row.  Tiles of 64 detections x 128 outputs (8 x 4 per thread), fp32 accumulation, K in chunks
+// of 32 channels of one tap, operands read with 16-byte loads.
+constexpr int EG_D = 64, EG_O = 128, EG_K = 32;
+// 16 bytes -> 8 bf16 values, or 16 E4M3 codes (Q)
+template <int Q>
+__device__ __forceinline__ void unpack16b(const uint4 v, float (&out)[16]) {
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+  if (Q) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 lo = e4m3x2_to_float2(w[i] & 0xFFFFu), hi = e4m3x2_to_float2(w[i] >> 16);
+      out[4 * i] = lo.x;
+      out[4 * i + 1] = lo.y;
+      out[4 * i + 2] = hi.x;
+      out[4 * i + 3] = hi.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[i]));
+      out[2 * i] = f.x;
+      out[2 * i + 1] = f.y;
+    }
+  }
+}
+template <int Q>
 __global__ void __launch_bounds__(256) emb_gemm_kernel(EmbSparse es, const int4* list, const int* count, int list_stride,
                                                        float* rows, int cap) {
   const int s = blockIdx.z;
   const int o0 = blockIdx.y * EG_O;
   const int total = count[s];
   const TView in = es.in[s];
-  const int cin = es.cin[s], K = 9 * cin, ldw = es.ldw[s], q = es.q[s];
-  __shared__ float As[EG_K][EG_D + 1];
-  __shared__ float Bs[EG_K][EG_O + 4];
+  const int cin = es.cin[s], K = 9 * cin, ldw = es.ldw[s];
+  constexpr int es_b = Q ? 1 : 2;             // bytes per element
+  constexpr int vec = 16 / es_b;              // elements per 16-byte load
+  __shared__ __align__(16) float As[EG_K][EG_D + 4];
+  __shared__ __align__(16) float Bs[EG_K][EG_O + 4];
   __shared__ int4 ent[EG_D];
   const int t = threadIdx.x;
-  const int to = (t % 32) * 4;          // 4 outputs
-  const int td = (t / 32) * 4;          // 4 detections
+  const int td = (t / 32) * 8;                // 8 detections
+  const int to = (t % 32) * 4;                // 4 outputs
   for (int d0 = blockIdx.x * EG_D; d0 < total; d0 += gridDim.x * EG_D) {
     __syncthreads();
     if (t < EG_D) ent[t] = d0 + t < total ? list[(size_t)s * list_stride + d0 + t] : make_int4(-1, -1, 0, 0);
     __syncthreads();
-    float acc[4][4] = {};
+    float acc[8][4] = {};
     for (int k0 = 0; k0 < K; k0 += EG_K) {
       const int tap = k0 / cin, c0 = k0 % cin;
       const int ky = tap / 3, kx = tap % 3;
-      // A: 32 detections x 32 channels of one tap (4 per thread)
-      for (int i = t; i < EG_D * EG_K; i += 256) {
-        const int d = i / EG_K, kk = i % EG_K;
+      // A: 64 detections x 32 channels of one tap
+      for (int i = t; i < EG_D * (EG_K / vec); i += 256) {
+        const int d = i / (EG_K / vec), part = i % (EG_K / vec);
         const int4 e = ent[d];
-        float v = 0.f;
+        float v[16];
         if (e.x >= 0) {
-          const size_t off = tview_off(in, e.x, e.z + ky - 1, e.w + kx - 1) + c0 + kk;
-          v = q ? e4m3_value(static_cast<const uint8_t*>(in.ptr)[off])
-                : __bfloat162float(static_cast<const __nv_bfloat16*>(in.ptr)[off]);
+          const size_t off = tview_off(in, e.x, e.z + ky - 1, e.w + kx - 1) + c0 + part * vec;
+          unpack16b<Q>(__ldg(reinterpret_cast<const uint4*>(static_cast<const uint8_t*>(in.ptr) + off * es_b)), v);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) v[j] = 0.f;
         }
-        As[kk][d] = v;
+#pragma unroll
+        for (int j = 0; j < vec; ++j) As[part * vec + j][d] = v[j];
       }
-      // B: 128 outputs x 32 K (16 per thread)
-      for (int i = t; i < EG_O * EG_K; i += 256) {
-        const int o = i / EG_K, kk = i % EG_K;
-        const size_t off = (size_t)(o0 + o) * ldw + k0 + kk;
-        Bs[kk][o] = q ? e4m3_value(static_cast<const uint8_t*>(es.w[s])[off])
-                      : __bfloat162float(static_cast<const __nv_bfloat16*>(es.w[s])[off]);
+      // B: 128 outputs x 32 K
+      for (int i = t; i < EG_O * (EG_K / vec); i += 256) {
+        const int o = i / (EG_K / vec), part = i % (EG_K / vec);
+        const size_t off = (size_t)(o0 + o) * ldw + k0 + part * vec;
+        float v[16];
+        unpack16b<Q>(__ldg(reinterpret_cast<const uint4*>(static_cast<const uint8_t*>(es.w[s]) + off * es_b)), v);
+#pragma unroll
+        for (int j = 0; j < vec; ++j) Bs[part * vec + j][o] = v[j];
       }
       __syncthreads();
-#pragma unroll 8
+#pragma unroll 4
       for (int kk = 0; kk < EG_K; ++kk) {
-        float a[4], b[4];
+        const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][td]);
+        const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][td + 4]);
+        const float4 b = *reinterpret_cast<const float4*>(&Bs[kk][to]);
+        const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float bb[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = As[kk][td + i];
+        for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) b[j] = Bs[kk][to + j];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], bb[j], acc[i][j]);
       }
       __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 8; ++i) {
       const int4 e = ent[td + i];
       if (e.x < 0) continue;
       float* row = rows + ((size_t)e.x * cap + e.y) * 518 + 6;
+      float v[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int o = o0 + to + j;
-        const float m = q ? es.mult[s][o] : 1.f;
-        row[o] = acc[i][j] * m + es.bias[s][o];
+        v[j] = acc[i][j] * (Q ? es.mult[s][o] : 1.f) + es.bias[s][o];
       }
+      // rows are 518 floats: 8-byte aligned only
+      reinterpret_cast<float2*>(row + o0 + to)[0] = make_float2(v[0], v[1]);
+      reinterpret_cast<float2*>(row + o0 + to)[1] = make_float2(v[2], v[3]);
     }
   }
 }
@@ -426,7 +460,11 @@ void post_launch(const float* const* heads, const HeadGeom& g, float conf_thresh
     int gx = (per + EG_D - 1) / EG_D;
     if (gx > 64) gx = 64;
     jde_count_launch();
-    emb_gemm_kernel<<<dim3(gx, 512 / EG_O, 3), 256, 0, st>>>(*es, b.emb_list, b.emb_count, n * b.kmax, rows, cap);
+    // the three heads of a handle are all BF16 or all E4M3
+    if (es->q[0])
+      emb_gemm_kernel<1><<<dim3(gx, 512 / EG_O, 3), 256, 0, st>>>(*es, b.emb_list, b.emb_count, n * b.kmax, rows, cap);
+    else
+      emb_gemm_kernel<0><<<dim3(gx, 512 / EG_O, 3), 256, 0, st>>>(*es, b.emb_list, b.emb_count, n * b.kmax, rows, cap);
   }
   dim3 ge((b.kmax + 3) / 4, n);
   jde_count_launch();

@@ -266,6 +266,9 @@ class Server:
         cfg.max_streams = self.max_streams
         cfg.max_in_w, cfg.max_in_h = in_w, in_h
         cfg.device = self.device.index or 0
+        # the post-processing reads the planted head maps (embeddings included), so the forward
+        # computes the network's dense embedding maps as well (nothing of the network is skipped)
+        cfg.sparse_emb = 0
         return cfg
 
     def group_cost(self, in_w, in_h):
