@@ -10,8 +10,8 @@ subnormals m/8 * 2^-6 for e = 0.  Conversion from a wider type rounds to the
 nearest representable value, ties to the even mantissa, and saturates finite
 values beyond the range to +-448.
 
-Quantisation scheme (the spec precision pattern; the paper itself runs
-FP32): every conv whose input tensor is stored in FP8 multiplies E4M3 codes of
+Quantisation scheme (the E4M3 pattern of the library's FP8 path; the paper itself
+runs FP32): every conv whose input tensor is stored in FP8 multiplies E4M3 codes of
 the input (one scale per tensor, s_x = amax_x / 448) with E4M3 codes of the
 folded weights (one scale per output channel, s_w[co] = max|W'[co]| / 448) and
 accumulates exactly; the epilogue applies s_x s_w[co], the bias, leaky-ReLU

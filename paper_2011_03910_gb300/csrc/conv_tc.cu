@@ -37,7 +37,7 @@ struct TcArgs {
   int stride, WW, WH, win_bytes;   // mode 3: window (or parity sub-window) size in pixels, bytes per buffer
   int plane;                       // mode 3: bytes between (parity) windows of one buffer (1024-aligned)
   int plane_tx;                    // mode 3: bytes one window load delivers (WW * WH * 64)
-  int nwin;                        // mode 3: window buffers in the ring (2 .. MAX_WIN)
+  int nwin;                        // modes 3, 4: window buffers in the ring (2 .. MAX_WIN)
   int total_units;                 // work units: tiles, or (CTA pairs) pairs of M tiles x N tiles
   int kel;                         // elements of one k-block along K (E4M3: twice the bf16 count, same bytes)
   int wnb, whb;                    // mode 4: TMA boxes per window, pixel rows per box
@@ -58,7 +58,7 @@ __device__ __forceinline__ bool patch_mode(int mode) { return mode == 1 || mode 
 // warp 0: TMA producer; warp 1: MMA issuer + TMEM owner; warps 2..9: epilogue in two
 // groups of four, group g draining TMEM accumulator buffer g (tiles alternate).
 constexpr int EPI_WARPS = 8;
-constexpr int MAX_WIN = 16;   // mode 3: most window buffers in flight
+constexpr int MAX_WIN = 16;   // modes 3, 4: most window buffers in flight
 __host__ __device__ constexpr int tc_threads(int gw) { return 32 * (gw + 1 + EPI_WARPS); }
 
 // CG = 2: a CTA pair computes a 256 x BN tile with one M=256 MMA; each CTA holds its own
@@ -241,8 +241,8 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
   uint64_t* acc_full = empty + STAGES;   // [NBUF] MMA -> epilogue group
   uint64_t* acc_empty = acc_full + Cfg::NBUF;   // [NBUF] epilogue group -> MMA
   uint64_t* res_full = acc_empty + Cfg::NBUF;   // [2] residual tile landed in staging tile g
-  uint64_t* win_full = res_full + 2;     // [MAX_WIN] mode 3: input window landed
-  uint64_t* win_empty = win_full + MAX_WIN;   // [MAX_WIN] mode 3: window consumed by the MMAs
+  uint64_t* win_full = res_full + 2;     // [MAX_WIN] modes 3, 4: input window landed
+  uint64_t* win_empty = win_full + MAX_WIN;   // [MAX_WIN] modes 3, 4: window consumed by the MMAs
   uint64_t* b_full = win_empty + MAX_WIN;     // mode 3: resident weights landed
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(b_full + 1);
   float* const sBiasAll = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(full) + Cfg::BAR_BYTES);   // [2][BN]
