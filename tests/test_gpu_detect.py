@@ -279,3 +279,49 @@ def test_sparse_embedding_head_matches_the_dense_maps(precision, n, in_w, in_h):
         assert err < 1e-4, (f, err)
         norms = np.linalg.norm(r1[f, :k, 6:], axis=1)
         np.testing.assert_allclose(norms, 1.0, atol=1e-5)
+
+
+def _iou(a, b):
+    ix = max(0.0, min(a[2], b[2]) - max(a[0], b[0]))
+    iy = max(0.0, min(a[3], b[3]) - max(a[1], b[1]))
+    inter = ix * iy
+    ua = (a[2] - a[0]) * (a[3] - a[1]) + (b[2] - b[0]) * (b[3] - b[1]) - inter
+    return inter / ua if ua > 0 else 0.0
+
+
+def test_bf16_detections_end_to_end_match_the_oracle_boxes_and_embeddings():
+    """The BF16 network's own detections (jde_detect_batch, sparse embedding head) against the FP64
+    oracle's forward + post-processing on the same frames, for every detection both keep (same anchor):
+    unit embeddings at cosine >= 0.999.  Boxes: their width and height are exp of head logits, which
+    amplifies the BF16 head error of the random-init model's large logits; measured IoU median 0.98,
+    minimum 0.93 at 320x192, so the test holds them to IoU >= 0.9 (median >= 0.95), not 0.99.  The kept
+    sets agree except for candidates whose confidence or overlap sits at a threshold within the BF16
+    head error."""
+    j = jde()
+    n = 2
+    frames = synth.frames_uniform(11, n, 1080, 1920)
+    h = make_handle(j.JDE_BF16, max_batch=n, sparse_emb=1)
+    try:
+        rows, count, aidx = _detect_rows(j, h, frames, 320, 192, cap=4096)
+    finally:
+        j.jde_destroy(h)
+    r, nw, nh, px, py = net.letterbox_geometry(1920, 1080, 320, 192)
+    x = net.letterbox(frames, 320, 192)
+    dets, embs, _ = net.forward(x, oracle_layers())
+    for f in range(n):
+        out = pp.postprocess_frame([d[f] for d in dets], [e[f] for e in embs], r, px, py)
+        o_rows = {int(i): out["rows"][k] for k, i in enumerate(out["index"])}
+        k = int(count[f])
+        g_rows = {int(aidx[f, q]): rows[f, q] for q in range(k)}
+        common = sorted(set(o_rows) & set(g_rows))
+        assert len(o_rows) > 0
+        assert len(common) >= 0.95 * max(len(o_rows), len(g_rows)), (len(common), len(o_rows), len(g_rows))
+        ious = np.array([_iou(g_rows[i][:4], o_rows[i][:4]) for i in common])
+        coss = np.array([float(np.dot(g_rows[i][6:], o_rows[i][6:]) /
+                               (np.linalg.norm(g_rows[i][6:]) * np.linalg.norm(o_rows[i][6:]))) for i in common])
+        print("frame", f, "kept gpu/oracle/common", len(g_rows), len(o_rows), len(common),
+              "IoU min/median", ious.min(), np.median(ious), "share >= 0.99", float(np.mean(ious >= 0.99)),
+              "cosine min", coss.min())
+        assert coss.min() >= 0.999
+        assert ious.min() >= 0.9
+        assert np.median(ious) >= 0.95
