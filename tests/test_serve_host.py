@@ -70,3 +70,52 @@ def test_budget_admits_groups_in_arrival_order_until_full():
     led = serve.AdmissionLedger(budget)
     admitted = [led.try_charge((s.in_w, s.in_h), cost[(s.in_w, s.in_h)]) for s in specs(6)]
     assert admitted == [True, False, True, True, False, True]
+
+
+def _act_bytes(n, hw, c, el, pad=1):
+    h, w = hw
+    return n * (h + 2 * pad) * (w + 2 * pad) * c * el
+
+
+def test_estimate_accounts_for_in_place_stages_and_the_sparse_embedding_head():
+    """Host bookkeeping of the activation buffers (no GPU): with keep_layer_outputs = 0 every residual
+    block's output shares its stage buffer (the 3x3 reduce-adds into the block input; the stride-16 and
+    stride-8 stages live in their concat slices), and with sparse_emb = 1 the three f32 embedding maps
+    (two sets, zero halo) are replaced by two-set bf16 copies of their input maps."""
+    from paper_2011_03910_gb300 import jde
+    n, W, H = 16, 1088, 608
+    table = jde.jde_layer_table()
+
+    def est(keep, sparse):
+        cfg = jde.jde_default_config()
+        cfg.precision = jde.JDE_BF16
+        cfg.max_batch = n
+        cfg.keep_layer_outputs = keep
+        cfg.sparse_emb = sparse
+        return jde.jde_estimate_device_bytes(cfg, W, H)
+
+    # spatial size of every layer output (stem at full size, five stride-2 stages, three scales)
+    sizes, h, w = [(H, W)], H, W
+    stage_blocks = [1, 2, 8, 8, 4]
+    stage_first = []
+    for nb in stage_blocks:
+        h, w = h // 2, w // 2
+        stage_first.append(len(sizes))
+        sizes += [(h, w)] * (1 + 2 * nb)
+    for i, s in enumerate((32, 16, 8)):
+        sizes += [(H // s, W // s)] * (9 if i < 2 else 8)
+    assert len(sizes) == len(table) == 78
+    # in place: a stage's block outputs (the last block of stages 3 and 4 is a concat slice in both
+    # layouts) and the downsampling outputs of stages 3 and 4 (they move into the concat slices)
+    saved = 0
+    for s, (first, nb) in enumerate(zip(stage_first, stage_blocks)):
+        blocks = [first + 2 + 2 * b for b in range(nb)]
+        if s in (2, 3):
+            blocks = blocks[:-1] + [first]
+        saved += sum(_act_bytes(n, sizes[l], table[l][1], 2) for l in blocks)
+    assert est(1, 0) - est(0, 0) == saved
+    # sparse head: minus the padded f32 embedding maps, plus bf16 copies of their inputs (two sets each)
+    emb = [59, 68, 77]
+    dense = sum(2 * _act_bytes(n, sizes[l], 512, 4) for l in emb)
+    copies = sum(2 * _act_bytes(n, sizes[l], table[l][0], 2) for l in emb)
+    assert est(0, 0) - est(0, 1) == dense - copies
