@@ -517,8 +517,12 @@ def main():
             a1.record(F)
             torch.cuda.synchronize()
             lat = sorted(ev0[i].elapsed_time(ev1[i]) for i in range(ws, ws + ks))
+            # device memory a handle sized for batches of n holds at this input size (the library's exact
+            # allocation rule, evaluated on the host): the peak-HBM-versus-batch study
+            mcfg = jde.jde_default_config()
+            mcfg.precision, mcfg.max_batch, mcfg.max_streams, mcfg.sparse_emb = jde.JDE_BF16, n, n, 0
             sweep[str(n)] = {"fps": n * ks / (a0.elapsed_time(a1) / 1000.0), "p50_ms": lat[len(lat) // 2],
-                             "p99_ms": lat[-1]}
+                             "p99_ms": lat[-1], "hbm_bytes": jde.jde_estimate_device_bytes(mcfg, IN_W, IN_H)}
 
         # batch 1 captured in one CUDA graph (forward + post-processing + tracker step): launch-bound regime
         g1_dets = jde.make_dets(rows[:1], count[:1], None, cap=cap)
