@@ -1013,7 +1013,7 @@ constexpr int w4_fixed() {
   return S * C::B_BYTES + 2 * C::SDEPTH * C::C_BYTES + 1024 + C::BAR_BYTES + C::BIAS_BYTES;
 }
 int w4_fixed_bytes(int bn, int q) {
-  if (bn == 128) return q ? w4_fixed<128, 1, 1>() : w4_fixed<128, 1, 0>();
+  if (bn == 128) return q ? w4_fixed<128, 2, 1>() : w4_fixed<128, 2, 0>();
   return q ? w4_fixed<256, 2, 1>() : w4_fixed<256, 2, 0>();
 }
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -1321,7 +1321,8 @@ bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const void* w_any, int cout_p
       }
   }
   // 256-wide tiles run on CTA pairs (M = 256 per MMA, each CTA loads half of B)
-  plan.cg = bn == 256 && (bkc == 64 || plan.mode == 4) ? 2 : 1;
+  // CTA pairs: 256-wide tiles, and every flat-window tile (each CTA holds half of the weight tile)
+  plan.cg = (bn == 256 && (bkc == 64 || plan.mode == 4)) || (bn == 128 && plan.mode == 4) ? 2 : 1;
   {
     cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)cout_pad};
     cuuint64_t strides[1] = {(cuuint64_t)K * ie};
@@ -1429,9 +1430,9 @@ cudaError_t conv_tc_launch(const TcPlan& p, cudaStream_t st) {
   if (p.mode == 4) {
     const int smem = p.nwin * p.win_bytes + w4_fixed_bytes(p.bn, p.q);
     if (smem > 227 * 1024 - 64) return cudaErrorInvalidValue;
-    if (p.bn == 128 && p.cg == 1)
-      return p.q ? launch_cfg<128, 32, W4_STAGES_Q, 1, 1, 1, 1>(p, a, st, smem)
-                 : launch_cfg<128, 32, W4_STAGES, 1, 1, 0, 1>(p, a, st, smem);
+    if (p.bn == 128 && p.cg == 2)
+      return p.q ? launch_cfg<128, 32, W4_STAGES_Q, 1, 2, 1, 1>(p, a, st, smem)
+                 : launch_cfg<128, 32, W4_STAGES, 1, 2, 0, 1>(p, a, st, smem);
     if (p.bn == 256 && p.cg == 2)
       return p.q ? launch_cfg<256, 32, W4_STAGES_Q, 1, 2, 1, 1>(p, a, st, smem)
                  : launch_cfg<256, 32, W4_STAGES, 1, 2, 0, 1>(p, a, st, smem);
