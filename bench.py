@@ -37,7 +37,7 @@ STRIDES = (32, 16, 8)
 METRIC = "JDE FPS at 1088x608: BF16/FP8 batched vs FP32 plain on one GB300; p99 latency"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the 78 conv launches of one BF16
 # batch-16 step, from one ncu capture of this build; re-take it (or set None) when the conv kernels change
-CONV_DRAM_BYTES_PER_STEP = 9.782e9   # ncu dram__bytes_read.sum + dram__bytes_write.sum, 78 launches, default tiles
+CONV_DRAM_BYTES_PER_STEP = 9.783e9   # ncu dram__bytes_read.sum + dram__bytes_write.sum, 78 launches, default tiles
 
 
 def parse():
