@@ -1,16 +1,17 @@
-// BF16 implicit-GEMM convolution on the 5th-generation tensor cores (tcgen05).
+// BF16 / E4M3 implicit-GEMM convolution on the 5th-generation tensor cores (tcgen05).
 //
 // GEMM view: D[M = pixels][N = out channels] = sum_k A[m][k] B[n][k], K = (tap, ci).
-// One CTA computes a 128 x BN tile with the f32 accumulator in TMEM:
-//   * warp 0 / lane 0 streams A and B k-blocks (BKC channels of one tap) into a
-//     STAGES-deep shared-memory ring with TMA (cp.async.bulk.tensor), 128- or
-//     64-byte swizzled, completion tracked by mbarriers;
-//   * warp 1 / lane 0 issues tcgen05.mma (M=128, N=BN, K=16) per k-block and
-//     frees the ring slot with tcgen05.commit;
-//   * all four warps then read the accumulator rows (TMEM lane = tile row)
-//     with tcgen05.ld and run the fused epilogue: + bias (BN folded),
-//     leaky-ReLU, + residual, bf16/f32 store, optional 2x2 upsample write into
-//     a concat slice.
+// A persistent CTA (or CTA pair: M = 256 over two SMs, cta_group::2) computes 128 x BN tiles
+// with the f32 accumulator in TMEM:
+//   * warp 0 / lane 0 streams A and B k-blocks (64-byte or 128-byte rows of one tap) into a
+//     STAGES-deep shared-memory ring with TMA (cp.async.bulk.tensor), swizzled, completion
+//     tracked by mbarriers (the windowed modes load an input window once per k-block instead);
+//   * warp 1 / lane 0 issues tcgen05.mma (M=128 or 256, N=BN, K=16 bf16 / 32 E4M3) per k-block
+//     and frees the ring slot with tcgen05.commit;
+//   * two groups of four epilogue warps read the accumulator rows (TMEM lane = tile row) with
+//     tcgen05.ld and run the fused epilogue: x E4M3 dequantisation, + bias (BN folded),
+//     leaky-ReLU, + residual (or a TMA reduce-add into the residual's own storage), bf16 / E4M3 /
+//     f32 staged TMA stores, or direct stores with the 2x2 upsample into a concat slice.
 // Activation addressing (implicit im2col) needs no gather:
 //   * stride 1 ("flat"): activations keep a 1-pixel zero halo, so for tap
 //     (ky, kx) the A rows of output pixels m0..m0+127 (flattened over the
