@@ -33,6 +33,7 @@ constexpr double SP = 1.0 / 20.0;
 constexpr double SV = 1.0 / 160.0;
 constexpr double INF_COST = 1e5;
 constexpr int MAXB = 64;
+constexpr int ASSIGN_COST_CACHE = 8192;   // doubles of cost matrix the assignment keeps in shared memory
 
 struct Slots {
   int stream[MAXB];
@@ -256,7 +257,9 @@ __global__ void __launch_bounds__(256) assign_kernel(StepArgs a, Slots sl) {
   const int R = trans ? D : nt;   // rows
   const int M = trans ? nt : D;   // cols
   const int MM = T > Dmax ? T : Dmax;
-  double* u = reinterpret_cast<double*>(smem);
+  // the block's cost matrix, read once per Hungarian step, is kept in shared memory when it fits
+  double* const cache = reinterpret_cast<double*>(smem);
+  double* u = cache + ASSIGN_COST_CACHE;
   double* v = u + (MM + 1);
   double* minv = v + (MM + 1);
   int* p = reinterpret_cast<int*>(minv + (MM + 1));
@@ -267,7 +270,10 @@ __global__ void __launch_bounds__(256) assign_kernel(StepArgs a, Slots sl) {
   uint8_t* used = reinterpret_cast<uint8_t*>(new_order + T);
   __shared__ int s_fail, s_nnew, s_births;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const double* A = a.t.cost + (size_t)b * T * Dmax;
+  const double* const Ag = a.t.cost + (size_t)b * T * Dmax;
+  const bool cached = (long long)R * M <= ASSIGN_COST_CACHE;
+  for (int k = tid; cached && k < R * M; k += blockDim.x) cache[k] = Ag[k];
+  const double* A = cached ? cache : Ag;
   const float* rows = a.rows + (size_t)b * a.cap * 518;
   for (int k = tid; k < T; k += blockDim.x) trk_det[k] = -1;
   for (int j = tid; j < Dmax; j += blockDim.x) det_trk[j] = -1;
@@ -530,7 +536,7 @@ __global__ void __launch_bounds__(256) assign_kernel(StepArgs a, Slots sl) {
 
 size_t assign_smem(const TrackState& t) {
   const int MM = t.max_tracks > t.max_dets ? t.max_tracks : t.max_dets;
-  return sizeof(double) * 3 * (MM + 1) + sizeof(int) * 2 * (MM + 1) + sizeof(int) * (2 * t.max_tracks + t.max_dets) +
+  return sizeof(double) * ASSIGN_COST_CACHE + sizeof(double) * 3 * (MM + 1) + sizeof(int) * 2 * (MM + 1) + sizeof(int) * (2 * t.max_tracks + t.max_dets) +
          (MM + 1) + 16;
 }
 
