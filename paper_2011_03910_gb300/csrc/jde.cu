@@ -813,7 +813,8 @@ void jde_destroy(jde_handle* h) {
       if (p) cudaFree(p);
   PostBufs& b = h->pb;
   void* ptrs[] = {b.cand_keys, b.cand_count, b.sorted, b.n_sorted, b.boxes, b.conf, b.cls, b.mask, b.keep_idx,
-                  b.n_keep, h->lb_x, h->lb_y, h->frames_dev, h->rows_stage, h->count_stage, h->aidx_stage, h->d_err};
+                  b.n_keep, b.emb_list, b.emb_count, h->lb_x, h->lb_y, h->frames_dev, h->rows_stage,
+                  h->count_stage, h->aidx_stage, h->d_err};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   track_free(h->trk);

@@ -135,7 +135,7 @@ extern "C" jde_status jde_postprocess_noalloc(const float* const* heads, int n, 
     base_ptr = g_scratch_addr[dev];
   }
   unsigned char* s = static_cast<unsigned char*>(base_ptr);
-  PostBufs b;
+  PostBufs b{};   // the sparse-embedding scratch stays null: caller heads carry dense embedding maps
   b.cand_keys = reinterpret_cast<uint64_t*>(s + o_keys);
   b.cand_count = reinterpret_cast<int*>(s + o_cnt);   // zeroed by post_launch before the filter runs
   b.cand_cap = (int)A;
