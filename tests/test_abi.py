@@ -51,3 +51,35 @@ def test_create_rejects_bad_config_without_gpu(jde):
         jde.jde_create(c, b"JDEW")
     assert e.value.status == 1
     jde.jde_destroy(None)      # NULL is a no-op
+
+
+def test_binding_structs_match_the_header_layout(jde, tmp_path):
+    """The ctypes structures of the binding have the sizes and field offsets the C compiler gives the
+    header's structs (compiled here with gcc against include/jde.h)."""
+    import ctypes as C
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    structs = {"jde_config": jde.jde_config, "jde_layer_desc": jde.jde_layer_desc, "jde_dets": jde.jde_dets,
+               "jde_tracks": jde.jde_tracks}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "jde.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            parts = line.split()
+            got[(parts[0], parts[1])] = int(parts[2])
+    for name, cls in structs.items():
+        assert got[(name, "size")] == C.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
