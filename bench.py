@@ -570,7 +570,9 @@ def main():
                 "traffic": CONV_DRAM_BYTES_PER_STEP if B == 16 else None,
                 "traffic_unit": "bytes per step (78 launches), ncu dram__bytes_read.sum + dram__bytes_write.sum",
                 "kernel": "conv_tc_kernel (78 launches per step, aggregated)",
-                "peak_kind": f"{peak_kind} bf16 sustained"}
+                "peak_kind": f"{peak_kind} bf16 sustained",
+                # the same conv rate against the burst figure (a GEMM timed alone)
+                "peak_burst": peaks.get("bf16_tflops", peak), "frac_burst": achieved / peaks.get("bf16_tflops", peak)}
 
     # e2e: host frames in (pinned), tracks out to host, through the same C ABI
     pinned = [f.cpu().pin_memory() for f in frames]
