@@ -168,14 +168,16 @@ jde_status jde_forward(jde_handle* h, const uint8_t* frames, int n, int src_w, i
  * strides 32, 16, 8 ([n][H_s][W_s][24] f32, channels 6a..6a+5 = tx, ty, tw, th,
  * t_obj, t_cls of anchor a), heads[3..5] the embedding maps
  * ([n][H_s][W_s][512] f32), all device pointers; NULL heads means the
- * handle's own heads from the last jde_forward.  Boxes are mapped back to
- * src_w x src_h frame pixels. */
+ * handle's own heads from the last jde_forward (with sparse_emb, its embedding
+ * head is then evaluated at the kept detections only, from the input maps that
+ * forward kept).  Boxes are mapped back to src_w x src_h frame pixels. */
 jde_status jde_postprocess(jde_handle* h, const float* const* heads, int n, int in_w, int in_h,
                            int src_w, int src_h, jde_dets* out, void* stream);
 
 /* Head tensors are double-buffered: the k-th jde_forward on a handle writes
  * set k mod 2 and jde_postprocess(heads = NULL) reads the set of the last
- * forward.  So the post-processing of batch k, enqueued on a second stream
+ * forward (the copies of the embedding head's input maps kept for sparse_emb
+ * follow the same two sets).  So the post-processing of batch k, enqueued on a second stream
  * after an event recorded behind forward k, may run while forward k+1 runs;
  * forward k+2 overwrites the set of batch k and must be ordered after that
  * post-processing by the caller (e.g. cudaStreamWaitEvent). */
