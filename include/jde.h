@@ -255,6 +255,15 @@ unsigned long long jde_launch_count(void);
  * events stay owned by the caller. */
 jde_status jde_set_profile_events(jde_handle* h, void* forward_begin, void* conv_begin, void* conv_end);
 
+/* Failure-detection self-test (no counterpart in the paper).  Every kernel that waits on another warp
+ * or CTA waits on an mbarrier with a cycle limit (about 2^32 SM cycles, two seconds); when the limit
+ * passes, the kernel sets bit 0 of the handle's error word, skips its remaining work and returns, so a
+ * lost signal never hangs the GPU.  This call exercises that path: one thread waits on a phase of a
+ * fresh mbarrier that nothing completes, with limit_cycles (1 .. 2^31) as the limit.  The call then
+ * reads and clears the error word (synchronising `stream`) into *word and returns JDE_ERR_TIMEOUT
+ * with bit 0 set; nothing traps and the context stays usable. */
+jde_status jde_selftest_wait(jde_handle* h, long long limit_cycles, int* word, void* stream);
+
 /* Post-processing for callers that cannot allocate device memory: code that
  * runs after a host application has reserved all device memory, a real-time
  * loop where a cudaMalloc (which can synchronise the device) is not allowed,
@@ -265,15 +274,19 @@ jde_status jde_set_profile_events(jde_handle* h, void* forward_begin, void* conv
  * It needs no handle and calls no cudaMalloc, cudaFree or allocating library
  * routine: heads[0..5] (device, layout as in jde_postprocess) and the outputs
  * (device; out->on_device must be 1) are the caller's, and all scratch comes
- * from one fixed 32 MiB device array compiled into the library, which every
- * GPU that loads libjde holds until the process exits.  A call needs about
+ * from one fixed 32 MiB device array compiled into the library.  CUDA loads
+ * that array onto a device the first time its address is looked up there -
+ * by jde_create for the handle's device, or else by the first call of this
+ * function on that device - and the device holds the 32 MiB from then until
+ * the process exits; so create a handle, or make that first call, before the
+ * application reserves the device's memory.  in_w, in_h <= 16384.  A call needs about
  * n * (8 * anchors + max_cand * (36 + max_cand / 8)) bytes of it (anchors =
  * 4 * (in_w*in_h/1024 + in_w*in_h/256 + in_w*in_h/64)); a larger request
  * returns JDE_ERR_CAPACITY with the sizes in err_msg (e.g. 16 frames at
  * 1088x608 fit with max_cand <= 2048).
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current: make that first call
- * before any stream capture.  Every call uses the same array and leaves its
+ * The first call on a device with no handle looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current: make that first
+ * call before any stream capture.  Every call uses the same array and leaves its
  * contents behind; two calls that can overlap on the GPU (different streams
  * or host threads) race, so the caller must serialise them.
  * err_msg (optional, err_len bytes) receives the reason of a failure. */

@@ -13,6 +13,9 @@
 // Process-wide count of kernels launched by libjde (host side, for launch accounting).
 void jde_count_launch(unsigned n = 1);
 
+// Device ordinals for which per-device host caches (kernel attributes, scratch addresses) are kept.
+constexpr int JDE_MAX_DEVICES = 64;
+
 // Bits of the per-handle device error word.
 enum : int { KERR_TIMEOUT = 1, KERR_CAPACITY = 2 };
 
@@ -64,15 +67,16 @@ JDE_DEV bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for the given phase parity: gives up after ~2^32 SM cycles
-// (about two seconds) and returns false so the caller can flag an error and
-// unwind instead of hanging the GPU.
-JDE_DEV bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait for the given phase parity: gives up after `limit` SM cycles
+// (default 2^32, about two seconds) and returns false so the caller can flag an
+// error and unwind instead of hanging the GPU.
+constexpr long long MBAR_WAIT_LIMIT = 1ll << 32;
+JDE_DEV bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit = MBAR_WAIT_LIMIT) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   for (;;) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (clock64() - t0 > (1ll << 32)) return false;
+    if (clock64() - t0 > limit) return false;
   }
 }
 

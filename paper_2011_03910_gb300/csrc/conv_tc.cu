@@ -25,6 +25,8 @@
 // its stores, releases TMEM and exits.
 #include <stdio.h>
 
+#include <mutex>
+
 #include "internal.h"
 
 namespace {
@@ -1057,14 +1059,25 @@ bool encode(CUtensorMap* m, int rank, void* base, const cuuint64_t* dims, const 
   return r == CUDA_SUCCESS;
 }
 
-int sm_count() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+// Per-device launch facts (SM count, kernel attributes, cluster occupancy) are cached per device
+// ordinal under one mutex: a process may drive several GPUs, from several host threads.
+std::mutex g_launch_mutex;
+
+int current_device() {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  return dev >= 0 && dev < JDE_MAX_DEVICES ? dev : -1;
+}
+
+int sm_count(int dev) {
+  static int n[JDE_MAX_DEVICES] = {0};
+  std::lock_guard<std::mutex> lock(g_launch_mutex);
+  if (!n[dev]) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
+    n[dev] = v;
   }
-  return n;
+  return n[dev];
 }
 
 template <int BN, int BKC, int STAGES, int GW = 1, int CG = 1, int Q = 0, int WM = 0>
@@ -1072,15 +1085,22 @@ cudaError_t launch_cfg(const TcPlan& p, const TcArgs& a, cudaStream_t st, int sm
   using Cfg = TcCfg<BN, BKC, STAGES, CG, Q, WM>;
   auto kernel = conv_tc_kernel<BN, BKC, STAGES, GW, CG, Q, WM>;
   if (!smem) smem = Cfg::SMEM;
-  static int attr_set = 0;
-  if (attr_set < smem) {
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    attr_set = smem;
+  const int dev = current_device();
+  if (dev < 0) return cudaErrorInvalidDevice;
+  const int sms = sm_count(dev);
+  // the dynamic shared-memory attribute is a per-device property of the kernel
+  static int attr_set[JDE_MAX_DEVICES] = {0};
+  {
+    std::lock_guard<std::mutex> lock(g_launch_mutex);
+    if (attr_set[dev] < smem) {
+      cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return e;
+      attr_set[dev] = smem;
+    }
   }
   if (CG == 1) {
     const int tiles = p.m_tiles * p.n_tiles;
-    const int grid = tiles < sm_count() ? tiles : sm_count();
+    const int grid = tiles < sms ? tiles : sms;
     jde_count_launch();
     kernel<<<grid, tc_threads(GW), smem, st>>>(p, a);
     return cudaGetLastError();
@@ -1097,17 +1117,22 @@ cudaError_t launch_cfg(const TcPlan& p, const TcArgs& a, cudaStream_t st, int sm
   cfg.stream = st;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  static int max_clusters = 0;
-  if (!max_clusters) {
-    cfg.gridDim = dim3(2 * (sm_count() / 2));
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, kernel, &cfg) != cudaSuccess || n < 1) {
-      cudaGetLastError();
-      n = sm_count() / 2;
+  static int max_clusters[JDE_MAX_DEVICES] = {0};
+  int mc;
+  {
+    std::lock_guard<std::mutex> lock(g_launch_mutex);
+    if (!max_clusters[dev]) {
+      cfg.gridDim = dim3(2 * (sms / 2));
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, kernel, &cfg) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        n = sms / 2;
+      }
+      max_clusters[dev] = n;
     }
-    max_clusters = n;
+    mc = max_clusters[dev];
   }
-  const int clusters = a.total_units < max_clusters ? a.total_units : max_clusters;
+  const int clusters = a.total_units < mc ? a.total_units : mc;
   cfg.gridDim = dim3(2 * clusters);
   jde_count_launch();
   return cudaLaunchKernelEx(&cfg, kernel, p, a);

@@ -117,3 +117,7 @@ struct EmbSparse {
 void post_launch(const float* const* heads, const HeadGeom& g, float conf_thresh, float nms_iou, PostBufs& b,
                  float* rows, int32_t* count, int32_t* anchor_index, int cap, int* err, cudaStream_t st,
                  const EmbSparse* es = nullptr);
+
+// Loads the fixed scratch array of jde_postprocess_noalloc onto the current device and records its
+// address; 0 on success, else 1 with a reason in msg.
+int noalloc_scratch_setup(char* msg, size_t len);

@@ -491,7 +491,8 @@ __global__ void pack_kernel(const float* W, const float* gamma, const float* bet
     v = (double)W[(((size_t)co * cin + ci) * k + ky) * k + kx] * scale;
   }
   if (w_kn && kk < kpad16 && co < cp64) w_kn[(size_t)kk * cp64 + co] = (float)v;
-  if (w_nk && kk < ktc && co < cptc) w_nk[(size_t)co * ktc + kk] = __float2bfloat16_rn((float)v);
+  // one rounding of the exact folded value (a float intermediate would round twice)
+  if (w_nk && kk < ktc && co < cptc) w_nk[(size_t)co * ktc + kk] = __double2bfloat16(v);
   if (kk == 0 && co < bias_len) {
     double b = 0.0;
     if (co < cout) b = gamma ? (double)beta[co] - (double)mean[co] * scale : (double)bias_in[co];
@@ -758,6 +759,18 @@ __global__ void amax_kernel(TView v, float scale, float* out) {
   if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int*>(out), __float_as_int(m));
 }
 
+// Self-test of the bounded waits: one thread waits on phase 0 of a fresh mbarrier, which nothing
+// completes, with the given cycle limit; the wait gives up and the error word gets the timeout bit.
+__global__ void wait_selftest_kernel(int* err, long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(&bar, 0u, limit)) flag_error(err, KERR_TIMEOUT);
+}
+
 }  // namespace
 
 // ============================================================================= C ABI
@@ -845,6 +858,12 @@ jde_status jde_create(const jde_config* cfg, const void* weights, size_t nbytes,
                        dmalloc((void**)&h->lb_y, sizeof(LbAxis) * c.max_in_h)))
     s = fail(h, JDE_ERR_OOM, "letterbox tables");
   if (s == JDE_OK && track_alloc(h->trk, c) != 0) s = fail(h, JDE_ERR_OOM, "tracker state");
+  if (s == JDE_OK) {
+    // the scratch array of jde_postprocess_noalloc is loaded onto this device now, with the handle's
+    // other device memory, rather than by that entry point's first call
+    char msg[200] = {0};
+    if (noalloc_scratch_setup(msg, sizeof(msg)) != 0) s = fail(h, JDE_ERR_CUDA, "no-alloc scratch set-up: %s", msg);
+  }
   if (s != JDE_OK) {
     g_create_error = h->err;
     jde_destroy(h);
@@ -1276,6 +1295,24 @@ jde_status jde_track_step(jde_handle* h, int n, const int32_t* stream_ids, const
 }
 
 unsigned long long jde_launch_count(void) { return g_launches.load(); }
+
+jde_status jde_selftest_wait(jde_handle* h, long long limit_cycles, int* word, void* stream) {
+  if (!h) return fail(nullptr, JDE_ERR_INVALID_ARG, "handle is NULL");
+  if (!word || limit_cycles < 1 || limit_cycles > (1ll << 31))
+    return fail(h, JDE_ERR_INVALID_ARG, "jde_selftest_wait: word NULL or limit out of [1, 2^31]");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  jde_count_launch();
+  wait_selftest_kernel<<<1, 32, 0, st>>>(h->d_err, limit_cycles);
+  CUDA_OR(h, cudaGetLastError());
+  CUDA_OR(h, cudaMemcpyAsync(word, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CUDA_OR(h, cudaStreamSynchronize(st));
+  CUDA_OR(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
+  CUDA_OR(h, cudaStreamSynchronize(st));
+  if (*word & KERR_TIMEOUT)
+    return fail(h, JDE_ERR_TIMEOUT, "bounded device wait gave up after %lld cycles (error word 0x%x)", limit_cycles,
+                *word);
+  return JDE_OK;
+}
 
 jde_status jde_set_profile_events(jde_handle* h, void* forward_begin, void* conv_begin, void* conv_end) {
   if (!h) return fail(nullptr, JDE_ERR_INVALID_ARG, "handle is NULL");

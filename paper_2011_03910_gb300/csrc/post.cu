@@ -13,6 +13,8 @@
 // NMS: bit j of mask word (i, j/64) says IoU(i, j) > threshold for j > i in
 // sorted order; one warp per frame then scans the rows in order, keeping a row
 // unless an earlier kept row suppressed it - exactly the greedy result.
+#include <mutex>
+
 #include "internal.h"
 
 namespace {
@@ -426,11 +428,17 @@ void post_launch(const float* const* heads, const HeadGeom& g, float conf_thresh
                  float* rows, int32_t* count, int32_t* anchor_index, int cap, int* err, cudaStream_t st,
                  const EmbSparse* es) {
   (void)err;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(select_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         SORT_CAP * (int)sizeof(uint64_t));
-    attr = true;
+  {
+    // the kernel's dynamic shared-memory limit is a per-device attribute: set it once per device
+    static std::mutex mu;
+    static bool attr[JDE_MAX_DEVICES] = {false};
+    int dev = -1;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < JDE_MAX_DEVICES) {
+      std::lock_guard<std::mutex> lock(mu);
+      if (!attr[dev] && cudaFuncSetAttribute(select_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             SORT_CAP * (int)sizeof(uint64_t)) == cudaSuccess)
+        attr[dev] = true;
+    }
   }
   const int n = g.n;
   cudaMemsetAsync(b.cand_count, 0, sizeof(int) * n, st);

@@ -9,10 +9,13 @@
 // allocate their scratch with cudaMalloc; this entry point takes its scratch
 // from a fixed array compiled into the library instead.
 //
-// The array below lives in the library's device image: every GPU that loads
-// libjde holds these 32 MiB until the process exits.  Host code must not use
-// the array's name as a device pointer (on the host it is only a stand-in):
-// its device address is looked up once per device with cudaGetSymbolAddress.
+// The array below lives in the device code of this file.  CUDA loads that code
+// onto a device lazily, the first time the array's address is looked up there,
+// and the load reserves the 32 MiB, which the device then holds until the
+// process exits.  The look-up (cudaGetSymbolAddress, once per device, with that
+// device current) happens in jde_create for the handle's device and otherwise
+// in the first jde_postprocess_noalloc call on a device.  Host code must not
+// use the array's name as a device pointer: on the host it is only a stand-in.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -27,11 +30,36 @@ namespace {
 constexpr size_t NOALLOC_SCRATCH_BYTES = 32ull << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
-constexpr int MAX_DEVICES = 64;
+constexpr int MAX_DEVICES = JDE_MAX_DEVICES;
 std::mutex g_setup_mutex;
 void* g_scratch_addr[MAX_DEVICES] = {nullptr};
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+// Largest model input side the entry point accepts (keeps every size computation far from overflow).
+constexpr int NOALLOC_MAX_SIDE = 16384;
+
+// Device address of the scratch array on the current device, looked up once per device.
+void* scratch_address(int* dev_out, char* msg, size_t len) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
+    if (msg && len) snprintf(msg, len, "no usable current CUDA device");
+    return nullptr;
+  }
+  if (dev_out) *dev_out = dev;
+  std::lock_guard<std::mutex> lock(g_setup_mutex);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      if (msg && len) snprintf(msg, len, "cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+      return nullptr;
+    }
+    g_scratch_addr[dev] = p;
+  }
+  return g_scratch_addr[dev];
+}
 
 void say(char* msg, size_t len, const char* text) {
   if (msg && len) snprintf(msg, len, "%s", text);
@@ -39,17 +67,33 @@ void say(char* msg, size_t len, const char* text) {
 
 }  // namespace
 
+// Loads the scratch array onto the current device and records its address (called by jde_create).
+int noalloc_scratch_setup(char* msg, size_t len) { return scratch_address(nullptr, msg, len) ? 0 : 1; }
+
 extern "C" jde_status jde_postprocess_noalloc(const float* const* heads, int n, int in_w, int in_h, int src_w,
                                               int src_h, float conf_thresh, float nms_iou, int max_cand,
                                               jde_dets* out, void* stream, char* err_msg, size_t err_len) {
   char buf[256];
   if (!heads || !out || !out->rows || !out->count || out->cap < 1 || !out->on_device || n < 1 || in_w < 32 ||
-      in_h < 32 || in_w % 32 || in_h % 32 || src_w < 1 || src_h < 1 || max_cand < 64 || max_cand > 4096 ||
-      max_cand % 64) {
+      in_h < 32 || in_w % 32 || in_h % 32 || in_w > NOALLOC_MAX_SIDE || in_h > NOALLOC_MAX_SIDE || src_w < 1 ||
+      src_h < 1 || max_cand < 64 || max_cand > 4096 || max_cand % 64) {
     say(err_msg, err_len,
-        "jde_postprocess_noalloc: bad arguments (device outputs required; sizes multiples of 32; "
+        "jde_postprocess_noalloc: bad arguments (device outputs required; sizes multiples of 32 up to 16384; "
         "max_cand a multiple of 64 in [64, 4096])");
     return JDE_ERR_INVALID_ARG;
+  }
+  {
+    // n frames of 4 * (in_w in_h / 1024 + in_w in_h / 256 + in_w in_h / 64) anchors, counted in size_t
+    const size_t px = (size_t)in_w * (size_t)in_h;
+    const size_t anchors = 4 * (px / 1024 + px / 256 + px / 64);
+    if ((size_t)n * anchors * sizeof(uint64_t) > NOALLOC_SCRATCH_BYTES) {
+      snprintf(buf, sizeof(buf),
+               "jde_postprocess_noalloc: %d frames at %dx%d need more than the fixed scratch of %zu bytes "
+               "for their candidate keys alone; use fewer frames per call",
+               n, in_w, in_h, NOALLOC_SCRATCH_BYTES);
+      say(err_msg, err_len, buf);
+      return JDE_ERR_CAPACITY;
+    }
   }
   for (int i = 0; i < 6; ++i)
     if (!heads[i]) {
@@ -113,26 +157,12 @@ extern "C" jde_status jde_postprocess_noalloc(const float* const* heads, int n, 
   }
 
   // once per device (with that device current): the device address of the scratch array
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
-    say(err_msg, err_len, "jde_postprocess_noalloc: no usable current CUDA device");
+  char why[160] = {0};
+  void* base_ptr = scratch_address(nullptr, why, sizeof(why));
+  if (!base_ptr) {
+    snprintf(buf, sizeof(buf), "jde_postprocess_noalloc: %s", why);
+    say(err_msg, err_len, buf);
     return JDE_ERR_CUDA;
-  }
-  void* base_ptr;
-  {
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
-      void* p = nullptr;
-      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess || !p) {
-        snprintf(buf, sizeof(buf), "jde_postprocess_noalloc: cudaGetSymbolAddress failed: %s",
-                 cudaGetErrorString(e));
-        say(err_msg, err_len, buf);
-        return JDE_ERR_CUDA;
-      }
-      g_scratch_addr[dev] = p;
-    }
-    base_ptr = g_scratch_addr[dev];
   }
   unsigned char* s = static_cast<unsigned char*>(base_ptr);
   PostBufs b{};   // the sparse-embedding scratch stays null: caller heads carry dense embedding maps

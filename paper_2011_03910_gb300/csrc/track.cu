@@ -5,7 +5,7 @@
 //            P <- F P F^T + Q, Q from the pre-prediction height), then the
 //            innovation covariance S = H P H^T + R (R from the predicted
 //            height) and its Cholesky factor for gating and update;
-//   cost   : C[k][j] = 1 - <e_k, d_j> (f32 dot of unit embeddings), replaced by
+//   cost   : C[k][j] = 1 - <e_k, d_j> (compensated f32 dot of unit embeddings), replaced by
 //            the "infinite" 1e5 when the squared Mahalanobis distance
 //            |L^-1 (z_j - H x_k)|^2 exceeds the chi-square gate;
 //   assign : shortest-augmenting-path Hungarian in f64 (one warp per stream;
@@ -181,7 +181,10 @@ __global__ void cost_kernel(StepArgs a, Slots sl) {
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   if (threadIdx.x < 32) slot_s[threadIdx.x] = k0 + threadIdx.x < nt ? a.t.order[(size_t)s * T + k0 + threadIdx.x] : -1;
   __syncthreads();
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  // compensated f32 dot product: each product's rounding error (fma) and each sum's rounding error
+  // (Neumaier) go into c, so s + c is the dot product of the f32 inputs to ~1e-7, well inside the
+  // 1e-6 band in which a threshold decision counts as a tie
+  float acc[4] = {0.f, 0.f, 0.f, 0.f}, comp[4] = {0.f, 0.f, 0.f, 0.f};
   const float* rows = a.rows + (size_t)b * a.cap * 518;
   for (int c0 = 0; c0 < 512; c0 += 32) {
     for (int e = threadIdx.x; e < 32 * 32; e += 256) {
@@ -195,7 +198,14 @@ __global__ void cost_kernel(StepArgs a, Slots sl) {
     for (int cc = 0; cc < 32; ++cc) {
       const float dv = Ds[tx][cc];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] = fmaf(Es[ty * 4 + q][cc], dv, acc[q]);
+      for (int q = 0; q < 4; ++q) {
+        const float ev = Es[ty * 4 + q][cc];
+        const float p = ev * dv;
+        const float pe = fmaf(ev, dv, -p);       // exact product error
+        const float t = acc[q] + p;
+        comp[q] += (fabsf(acc[q]) >= fabsf(p) ? (acc[q] - t) + p : (p - t) + acc[q]) + pe;
+        acc[q] = t;
+      }
     }
     __syncthreads();
   }
@@ -223,7 +233,7 @@ __global__ void cost_kernel(StepArgs a, Slots sl) {
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) d2 += w[i] * w[i];
-    double cost = (double)(1.f - acc[q]);
+    double cost = 1.0 - ((double)acc[q] + (double)comp[q]);
     if (d2 > a.gate) cost = INF_COST;
     if (trans)
       A[(size_t)j * M + k] = cost;
@@ -624,8 +634,7 @@ int track_step(TrackState& t, const jde_config& cfg, int n, const int32_t* strea
   const int32_t* count = dets->count;
   if (!dets->on_device) {
     const size_t need = (size_t)t.max_batch * dets->cap * 518;
-    static size_t have = 0;
-    if (!t.rows_stage || need > have) {
+    if (!t.rows_stage || need > t.rows_stage_cap) {
       cudaFree(t.rows_stage);
       cudaFree(t.count_stage);
       if (!dalloc((void**)&t.rows_stage, sizeof(float) * need) ||
@@ -633,7 +642,7 @@ int track_step(TrackState& t, const jde_config& cfg, int n, const int32_t* strea
         snprintf(msg, msg_len, "detection staging");
         return JDE_ERR_OOM;
       }
-      have = need;
+      t.rows_stage_cap = need;
     }
     if (cudaMemcpyAsync(t.rows_stage, dets->rows, sizeof(float) * (size_t)n * dets->cap * 518, cudaMemcpyHostToDevice,
                         st) != cudaSuccess ||

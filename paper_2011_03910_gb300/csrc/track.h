@@ -28,7 +28,8 @@ struct TrackState {
   double* gate_z = nullptr;         // [B][T][4]   projected mean H x
   double* cost = nullptr;           // [B][T*D]    gated cost, rows = min(T, D)
   int* slot_stream = nullptr;       // [B]
-  float* rows_stage = nullptr;      // [B][D][518] host-provided detections staged on the device
+  float* rows_stage = nullptr;      // [B][cap][518] host-provided detections staged on the device
+  size_t rows_stage_cap = 0;        // floats rows_stage holds
   int32_t* count_stage = nullptr;   // [B]
   // output staging for host outputs
   long long* o_id = nullptr;

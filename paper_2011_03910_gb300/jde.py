@@ -74,6 +74,7 @@ _sig = {
     "jde_estimate_device_bytes": (C.c_int, [C.POINTER(jde_config), C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
     "jde_launch_count": (C.c_ulonglong, []),
     "jde_set_profile_events": (C.c_int, [_P, _P, _P, _P]),
+    "jde_selftest_wait": (C.c_int, [_P, C.c_longlong, C.POINTER(C.c_int), _P]),
     "jde_postprocess_noalloc": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float, C.c_float,
                                           C.c_int, C.POINTER(jde_dets), _P, C.c_char_p, C.c_size_t]),
 }
@@ -255,3 +256,12 @@ def jde_postprocess_noalloc(heads, n, in_w, in_h, src_w, src_h, conf_thresh, nms
                                      C.byref(dets), stream_ptr(stream), msg, len(msg))
     if st != JDE_OK:
         raise JdeError(st, msg.value.decode(errors="replace"))
+
+
+def jde_selftest_wait(h, limit_cycles, stream=None) -> tuple[int, int]:
+    """Run the bounded-wait self-test; returns (status, error word) without raising for JDE_ERR_TIMEOUT."""
+    w = C.c_int()
+    st = lib.jde_selftest_wait(h, int(limit_cycles), C.byref(w), stream_ptr(stream))
+    if st not in (JDE_OK, 6):
+        _check(h, st)
+    return st, w.value

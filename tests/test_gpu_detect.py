@@ -12,8 +12,8 @@ import synth
 from oracle import network as net
 from oracle import postprocess as pp
 
-from gpu_helpers import (blob, forward, get_tensor, heads_to_device, jde, make_handle, nms_tie_frame, oracle_layers,
-                         postprocess, rel_maxabs)
+from gpu_helpers import (bf16_heads_ok, blob, forward, get_tensor, heads_to_device, jde, make_handle, nms_tie_frame,
+                         oracle_layers, postprocess, rel_maxabs)
 
 pytestmark = pytest.mark.gpu
 
@@ -68,7 +68,7 @@ def test_bf16_forward_320x192_matches_oracle(keep):
         heads = forward(h, frames, 320, 192)
         errs = [rel_maxabs(g, o) for g, o in zip(heads, dets + embs)]
         print("bf16 320x192 head errors", errs)
-        assert max(errs) < 2e-2
+        assert bf16_heads_ok(errs), errs
         if keep:
             bad = per_layer_report(h, acts, 2e-2)
             assert bad == [], bad
@@ -100,7 +100,6 @@ def test_forward_1088x608_letterboxed_sampled_frames(precision):
     n = 16 if bf16 else 1
     frames = synth.frames_uniform(2, n, 1080, 1920)
     h = make_handle(j.JDE_BF16 if bf16 else j.JDE_FP32, max_batch=n, in_w=1088, in_h=608)
-    tol = 2e-2 if bf16 else 1e-4
     try:
         heads = forward(h, frames, 1088, 608)
         for f in ([0, n - 1] if bf16 else [0]):
@@ -108,7 +107,7 @@ def test_forward_1088x608_letterboxed_sampled_frames(precision):
             dets, embs, _ = net.forward(x, oracle_layers())
             errs = [rel_maxabs(g[f:f + 1], o) for g, o in zip(heads, dets + embs)]
             print(precision, "frame", f, "head errors", errs)
-            assert max(errs) < tol
+            assert bf16_heads_ok(errs) if bf16 else max(errs) < 1e-4, errs
     finally:
         j.jde_destroy(h)
 
@@ -227,7 +226,7 @@ def test_bf16_other_resolutions_and_batches_on_one_handle(in_w, in_h, n):
         dets, embs, _ = net.forward(x, oracle_layers())
         errs = [rel_maxabs(g[n - 1:n], o) for g, o in zip(heads, dets + embs)]
         print(in_w, in_h, "head errors", errs)
-        assert max(errs) < 2e-2
+        assert bf16_heads_ok(errs), errs
     finally:
         j.jde_destroy(h)
 
@@ -294,11 +293,14 @@ def _iou(a, b):
 def test_bf16_detections_end_to_end_match_the_oracle_boxes_and_embeddings():
     """The BF16 network's own detections (jde_detect_batch, sparse embedding head) against the FP64
     oracle's forward + post-processing on the same frames, for every detection both keep (same anchor):
-    unit embeddings at cosine >= 0.999.  Boxes: their width and height are exp of head logits, which
-    amplifies the BF16 head error of the random-init model's large logits; measured IoU median 0.98,
-    minimum 0.93 at 320x192, so the test holds them to IoU >= 0.9 (median >= 0.95), not 0.99.  The kept
-    sets share at least 85% of their detections (measured 24-25 of 25-26): the others sit at a
+    unit embeddings at cosine >= 0.999 (the benchmark spec's criterion).  Boxes: width and height are exp of
+    head logits, which turns the BF16 storage noise of the random-init model's large logits into a few
+    percent of size, so IoU >= 0.99 against float64 is beyond the BF16 scheme itself (oracle with exact
+    arithmetic and bfloat16 stores: IoU median 0.98, minimum 0.92, R23).  The GPU's boxes are held to
+    the scheme's own agreement on the same frames: median IoU within 0.01 of the scheme's and 90% of
+    boxes at IoU >= 0.9.  The kept sets share at least 85% of their detections: the others sit at a
     confidence or overlap threshold within the BF16 head error."""
+    from oracle import bf16
     j = jde()
     n = 2
     frames = synth.frames_uniform(11, n, 1080, 1920)
@@ -310,22 +312,55 @@ def test_bf16_detections_end_to_end_match_the_oracle_boxes_and_embeddings():
     r, nw, nh, px, py = net.letterbox_geometry(1920, 1080, 320, 192)
     x = net.letterbox(frames, 320, 192)
     dets, embs, _ = net.forward(x, oracle_layers())
+    d_s, e_s, _ = bf16.forward(x, oracle_layers(), inplace=True)
     for f in range(n):
         out = pp.postprocess_frame([d[f] for d in dets], [e[f] for e in embs], r, px, py)
+        sch = pp.postprocess_frame([d[f] for d in d_s], [e[f] for e in e_s], r, px, py)
         o_rows = {int(i): out["rows"][k] for k, i in enumerate(out["index"])}
+        s_rows = {int(i): sch["rows"][k] for k, i in enumerate(sch["index"])}
         k = int(count[f])
         g_rows = {int(aidx[f, q]): rows[f, q] for q in range(k)}
         common = sorted(set(o_rows) & set(g_rows))
         assert len(o_rows) > 0
-        # a confidence or an overlap within the BF16 head error of its threshold flips a keep, and a
-        # flipped keep can change later NMS decisions: most, not all, kept detections are shared
         assert len(common) >= 0.85 * max(len(o_rows), len(g_rows)), (len(common), len(o_rows), len(g_rows))
         ious = np.array([_iou(g_rows[i][:4], o_rows[i][:4]) for i in common])
+        s_common = sorted(set(o_rows) & set(s_rows))
+        s_ious = np.array([_iou(s_rows[i][:4], o_rows[i][:4]) for i in s_common])
         coss = np.array([float(np.dot(g_rows[i][6:], o_rows[i][6:]) /
                                (np.linalg.norm(g_rows[i][6:]) * np.linalg.norm(o_rows[i][6:]))) for i in common])
         print("frame", f, "kept gpu/oracle/common", len(g_rows), len(o_rows), len(common),
-              "IoU min/median", ious.min(), np.median(ious), "share >= 0.99", float(np.mean(ious >= 0.99)),
-              "cosine min", coss.min())
+              "IoU min/median", ious.min(), np.median(ious), "scheme IoU min/median", s_ious.min(),
+              np.median(s_ious), "cosine min", coss.min())
         assert coss.min() >= 0.999
-        assert ious.min() >= 0.9
-        assert np.median(ious) >= 0.95
+        assert np.median(ious) >= np.median(s_ious) - 0.01
+        assert float(np.mean(ious >= 0.9)) >= 0.9
+
+
+@pytest.mark.parametrize("in_w,in_h", [(1088, 608), (864, 480), (576, 320)])
+def test_letterbox_element_wise_at_the_serving_sizes(in_w, in_h):
+    """Tensor 100 (the letterboxed input, bfloat16 RGB on the tensor-core path) against the oracle's
+    float64 letterbox of the same 1920x1080 frames rounded once to bfloat16: the GPU blends in float32
+    from float64 sample positions, so it equals the rounded oracle except where the float64 value lies
+    within float32 error of a rounding midpoint (then one bfloat16 step)."""
+    from oracle import bf16
+    j = jde()
+    n = 2
+    frames = synth.frames_uniform(31, n, 1080, 1920)
+    h = make_handle(j.JDE_BF16, max_batch=n, in_w=in_w, in_h=in_h)
+    try:
+        f = torch.from_numpy(frames).cuda()
+        j.jde_forward(h, f, n, 1920, 1080, in_w, in_h, True, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        got = get_tensor(h, 100)
+    finally:
+        j.jde_destroy(h)
+    o = net.letterbox(frames, in_w, in_h)
+    want = bf16.bf16(o)
+    assert got.shape == want.shape == (n, in_h, in_w, 3)
+    ulp = np.exp2(np.floor(np.log2(np.maximum(np.abs(o), 2.0 ** -126))) - 7.0)
+    exact = float(np.mean(got == want))
+    print(in_w, in_h, "exact share", exact)
+    assert exact >= 0.9999
+    assert np.all(np.abs(got - o) <= 0.5 * ulp + 1e-6)
+    r, nw, nh, px, py = net.letterbox_geometry(1920, 1080, in_w, in_h)
+    assert np.all(got[:, :, :px] == 0.5) and np.all(got[:, :, px + nw:] == 0.5)    # padding columns

@@ -1,0 +1,232 @@
+"""GPU parity of the reduced-precision paths against the oracle of their own storage scheme.
+
+BF16: ``oracle.bf16`` is the float64 network with every stored tensor rounded to bfloat16 (weights,
+letterbox, layer outputs; heads float).  The GPU differs from it only where its float32 accumulation
+puts a sum on the other side of a bfloat16 rounding boundary (one unit in the last place), so each
+layer, fed the GPU's own stored inputs, must agree exactly on almost every element and within one
+bfloat16 step everywhere.  End to end, two evaluations of a reduced-precision network decorrelate
+(every rounding flip moves the next layers' inputs; pinned on the CPU in test_oracle_bf16.py), so the
+GPU's end-to-end error against float64 is compared with the scheme's own (reading R23; for BF16 boxes:
+IoU median 0.98, minimum 0.92 on the random-init model, a property of the scheme, not a kernel error).
+
+E4M3: ``oracle.fp8`` (the fake-quantised network) against the GPU layer by layer in the batch-32
+1088x608 configuration of the E4M3 benchmark line with autotuned tiles, and end to end as for BF16.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from gpu_helpers import HEAD_LAYERS, forward, get_tensor, jde, make_handle, oracle_layers, rel_maxabs
+from oracle import bf16
+from oracle import fp8
+from oracle import network as net
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+LUT = np.array([fp8.e4m3_decode(c) for c in range(256)])
+
+
+def bf16_ulp(v):
+    """Spacing of bfloat16 values at |v| (the binade's step 2^(k-7))."""
+    a = np.maximum(np.abs(v), 2.0 ** -126)
+    return np.exp2(np.floor(np.log2(a)) - 7.0)
+
+
+def layer_input(io_entry, get, lb):
+    inp, res = io_entry
+    if inp == -1:
+        xin = lb
+    elif isinstance(inp, tuple):
+        xin = np.concatenate([get(inp[1]), get(inp[2])], axis=3)   # the lateral is stored upsampled
+    else:
+        xin = get(inp)
+    return xin, (get(res) if res is not None else None)
+
+
+def test_each_bf16_layer_matches_the_bf16_scheme_on_the_gpu_inputs():
+    """keep_layer_outputs = 1: every layer of the BF16 network, fed the GPU's stored input, against the
+    scheme's layer (bfloat16 weights, exact accumulation, bfloat16 store; heads float)."""
+    j = jde()
+    h = make_handle(j.JDE_BF16, max_batch=2, keep_layer_outputs=1)
+    try:
+        frames = synth.frames_uniform(11, 2, 1080, 1920)
+        forward(h, frames, 320, 192)
+        lb = get_tensor(h, 100)
+        # the letterbox itself: the float64 letterbox rounded once to bfloat16
+        want_lb = bf16.bf16(net.letterbox(frames, 320, 192))
+        assert float(np.mean(lb == want_lb)) >= 0.9999
+        assert np.all(np.abs(lb - want_lb) <= bf16_ulp(want_lb))
+        layers = oracle_layers()
+        io = net.layer_io()
+        cache = {}
+
+        def get(t):
+            if t not in cache:
+                cache[t] = get_tensor(h, t)
+            return cache[t]
+
+        report = []
+        for l in range(78):
+            xin, res = layer_input(io[l], get, lb)
+            want = bf16.conv_layer(l, xin, layers, res, inplace=False)
+            got = get(l)
+            if got.shape != want.shape:          # a lateral, stored 2x upsampled in its concat buffer
+                want = net.upsample2(want)
+            if l in HEAD_LAYERS:
+                err = rel_maxabs(got, want)
+                report.append((l, "head", err))
+                assert err < 1e-5, (l, err)
+                continue
+            exact = float(np.mean(got == want))
+            # one bfloat16 step at the larger magnitude, plus the float32 accumulation error of a sum that
+            # cancels to near zero (1e-5 of the layer's range)
+            bound = bf16_ulp(np.maximum(np.abs(got), np.abs(want))) + 1e-5 * np.max(np.abs(want))
+            over = float(np.max(np.abs(got - want) / bound))
+            report.append((l, round(exact, 6), round(over, 3)))
+            assert over <= 1.0, (l, over)
+            assert exact >= 0.98, (l, exact)
+        print("per-layer BF16 scheme parity (layer, exact share, worst diff / bound)", report)
+    finally:
+        j.jde_destroy(h)
+
+
+def test_bf16_end_to_end_error_is_the_scheme_s():
+    """The default BF16 handle's heads against float64, next to the BF16 scheme's own heads against
+    float64 on the same frames.  Two evaluations of the scheme decorrelate through the network (R23,
+    pinned in test_oracle_bf16.py), so the GPU's error is compared with the scheme's as a size: per head
+    at most 1.5 times the scheme's plus 2e-3."""
+    j = jde()
+    n = 2
+    frames = synth.frames_uniform(11, n, 1080, 1920)
+    layers = oracle_layers()
+    x = net.letterbox(frames, 320, 192)
+    d_s, e_s, _ = bf16.forward(x, layers, inplace=True)
+    d_f, e_f, _ = net.forward(x, layers)
+    h = make_handle(j.JDE_BF16, max_batch=n, sparse_emb=0)
+    try:
+        heads = forward(h, frames, 320, 192)
+    finally:
+        j.jde_destroy(h)
+    gpu = [rel_maxabs(g, o) for g, o in zip(heads, d_f + e_f)]
+    scheme = [rel_maxabs(s, o) for s, o in zip(d_s + e_s, d_f + e_f)]
+    between = [rel_maxabs(g, s) for g, s in zip(heads, d_s + e_s)]
+    print("BF16 heads rel max-abs vs float64: GPU", gpu, "scheme", scheme, "GPU vs scheme", between)
+    for g_err, s_err in zip(gpu, scheme):
+        assert g_err <= 1.5 * s_err + 2e-3
+
+
+def test_e4m3_end_to_end_error_is_the_scheme_s():
+    """E4M3 at 320x192, batch 2: the GPU's heads against float64, next to the fake-quantised oracle's
+    (the same scheme and scales) against float64.  As for BF16, two evaluations of the scheme decorrelate
+    end to end, so the sizes are compared: per head at most 1.5 times the scheme's plus 2e-2.  The
+    the benchmark spec's 6e-2 is beyond the scheme itself on this network (0.15-0.29, R21); the layer-by-layer
+    parity is in test_gpu_fp8.py and below."""
+    j = jde()
+    amax = json.load(open(os.path.join(GOLDEN, "fp8_amax_320x192.json")))["amax"]
+    h = make_handle(j.JDE_FP8_E4M3, max_batch=2, src_w=320, src_h=192)
+    try:
+        j.jde_set_act_amax(h, amax)
+        frames = synth.frames_uniform(1, 2, 192, 320)
+        heads = forward(h, frames, 320, 192)
+    finally:
+        j.jde_destroy(h)
+    x = net.letterbox(frames, 320, 192)
+    layers = oracle_layers()
+    d_q, e_q, _ = fp8.forward(x, layers, fp8.tensor_scales(amax))
+    d_f, e_f, _ = net.forward(x, layers)
+    gpu = [rel_maxabs(g, o) for g, o in zip(heads, d_f + e_f)]
+    scheme = [rel_maxabs(q, o) for q, o in zip(d_q + e_q, d_f + e_f)]
+    between = [rel_maxabs(g, q) for g, q in zip(heads, d_q + e_q)]
+    print("E4M3 heads rel max-abs vs float64: GPU", gpu, "fake-quant oracle", scheme, "GPU vs oracle", between)
+    for g_err, s_err in zip(gpu, scheme):
+        assert g_err <= 1.5 * s_err + 2e-2
+
+
+def _raw(j, h, tid, frames_sel):
+    """Tensor tid of the listed frames: (codes or values as float64, dtype id)."""
+    dims, dt = j.jde_get_tensor(h, tid)
+    tdt = {0: torch.float32, 1: torch.bfloat16, 2: torch.uint8}[dt]
+    t = torch.empty(dims, dtype=tdt, device="cuda")
+    j.jde_get_tensor(h, tid, t, t.numel() * t.element_size(), torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    sel = t[frames_sel].cpu()
+    del t
+    if dt == 2:
+        return LUT[sel.numpy()], dt
+    return sel.float().numpy().astype(np.float64), dt
+
+
+def test_e4m3_bench_configuration_each_layer_on_sampled_frames():
+    """The E4M3 benchmark configuration: 1088x608 letterboxed from 1920x1080, batch 32, tiles chosen by
+    jde_autotune (CTA-pair 256-wide E4M3 tiles, the 12-deep flat-window weight ring, the autotuned
+    widths).  Frames 0 and 31 of the batch: every conv from layer 4 on, fed the GPU's own stored inputs,
+    against the oracle's E4M3 layer with the same scales (oracle calibration at 1088x608)."""
+    j = jde()
+    B, W, H = 32, 1088, 608
+    amax = json.load(open(os.path.join(GOLDEN, "fp8_amax_1088x608.json")))["amax"]
+    scales = fp8.tensor_scales(amax)
+    h = make_handle(j.JDE_FP8_E4M3, max_batch=B, in_w=W, in_h=H)
+    st = torch.cuda.current_stream()
+    try:
+        j.jde_set_act_amax(h, amax)
+        default = j.jde_tile_choice(h, B, W, H)
+        j.jde_autotune(h, B, W, H, st)
+        tuned = j.jde_tile_choice(h, B, W, H)
+        frames = synth.frames_uniform(2000, B, 1080, 1920)
+        f = torch.from_numpy(frames).cuda()
+        j.jde_forward(h, f, B, 1920, 1080, W, H, True, st)
+        torch.cuda.synchronize()
+        assert j.jde_kernel_errors(h) == 0
+        del f
+        sel = [0, B - 1]
+        layers = oracle_layers()
+        io = net.layer_io()
+        cache = {}
+
+        def get(t):
+            if t not in cache:
+                v, dt = _raw(j, h, t, sel)
+                cache[t] = v * scales[t] if dt == 2 else v
+            return cache[t]
+
+        last_use = {}                            # last layer reading each tensor (host memory stays bounded)
+        for k, (inp, res) in enumerate(io):
+            for t in (list(inp[1:]) if isinstance(inp, tuple) else [inp]) + ([res] if res is not None else []):
+                last_use[t] = k
+        report = []
+        for l in range(fp8.FIRST_FP8_OUTPUT, 78):
+            xin, res = layer_input(io[l], get, None)
+            want = fp8.conv_layer(l, xin, layers, scales, res)
+            got = get(l)
+            if got.shape != want.shape:
+                want = net.upsample2(want)
+            if l in HEAD_LAYERS:
+                err = rel_maxabs(got, want)
+                report.append((l, "head", err))
+                assert err < 1e-4, (l, err)
+                continue
+            s = scales[l]
+            exact = float(np.mean(got == want))
+            a = np.maximum(np.abs(got), np.abs(want)) / s
+            step = np.exp2(np.floor(np.log2(np.maximum(a, 2.0 ** -6))) - 3.0)
+            steps = float(np.max(np.abs(got - want) / (s * step)))
+            report.append((l, tuned[l], round(exact, 6), round(steps, 3)))
+            if l == fp8.FIRST_FP8_OUTPUT:
+                # BF16 operands (GPU) vs float64 (oracle) before the first E4M3 store
+                assert np.max(np.abs(got - want)) <= 1e-2 * amax[l] + s * step.max()
+                assert exact >= 0.85, (l, exact)
+            else:
+                assert steps <= 1.0 + 1e-9, (l, steps)
+                assert exact >= 0.98, (l, exact)
+            for t in list(cache):
+                if last_use.get(t, -1) <= l:
+                    del cache[t]
+        print("tiles changed by the autotuner:", sum(a != b for a, b in zip(default, tuned)), "tuned", tuned)
+        print("E4M3 1088x608 b32 per-layer parity (layer, tile, exact share, worst steps)", report)
+    finally:
+        j.jde_destroy(h)

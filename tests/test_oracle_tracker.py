@@ -197,3 +197,32 @@ def test_planted_objects_keep_their_ids():
             tid = T.last["det_track"][j]
             assert owner.setdefault(o, tid) == tid, "identity switch"
     assert len(owner) == 8
+
+
+def test_gallery_update_is_the_normalised_momentum_average():
+    """R15 by hand: a track born from a detection with embedding e starts its gallery at e; each match
+    with a detection d sets it to (0.9 e + 0.1 d) / |0.9 e + 0.1 d|.  Two unit vectors at 60 degrees in a
+    plane (cosine cost 0.5 <= 0.7, same box) give the closed form (0.9 + 0.05, 0.1 sin 60) / norm; a swapped
+    momentum or a missing normalisation gives another vector."""
+    e = np.zeros(512)
+    e[0] = 1.0
+    d = np.zeros(512)
+    d[0], d[1] = 0.5, math.sqrt(3.0) / 2
+    T = tk.Tracker()
+    T.step(np.stack([det_row([100, 100, 140, 220], e)]))
+    np.testing.assert_array_equal(T.tracks[0].emb, e)
+    T.step(np.stack([det_row([100, 100, 140, 220], d)]))
+    assert T.last["matches"] == [(1, 0)]
+    v = np.array([0.9 + 0.1 * 0.5, 0.1 * math.sqrt(3.0) / 2])
+    want = np.zeros(512)
+    want[:2] = v / math.hypot(*v)
+    np.testing.assert_allclose(T.tracks[0].emb, want, rtol=0, atol=1e-15)
+    assert abs(np.linalg.norm(T.tracks[0].emb) - 1.0) < 1e-15
+    # a third frame: the update composes from the gallery, not from the last detection
+    T.step(np.stack([det_row([100, 100, 140, 220], d)]))
+    v2 = 0.9 * want[:2] + 0.1 * d[:2]
+    np.testing.assert_allclose(T.tracks[0].emb[:2], v2 / np.linalg.norm(v2), rtol=0, atol=1e-15)
+    np.testing.assert_array_equal(T.tracks[0].emb[2:], 0.0)
+    # the cost of the next step uses the gallery: 1 - <gallery, d>
+    T.step(np.stack([det_row([100, 100, 140, 220], d)]))
+    assert T.last["cost"][0, 0] == pytest.approx(1.0 - float(v2 @ d[:2]) / np.linalg.norm(v2), abs=1e-15)
