@@ -84,9 +84,12 @@ typedef struct {
   int device;           /* CUDA device ordinal */
   int keep_layer_outputs; /* 0 (default): in BF16-stored residual stages each block's 3x3 conv adds
                              its output into the block input's storage in place (the residual add
-                             of Sec. 3 done by a TMA reduce-add), so the blocks' inputs are not kept
-                             and jde_get_tensor / jde_act_amax refuse them; 1: every conv layer keeps
-                             its own output tensor (per-layer inspection, calibration) */
+                             of Sec. 3 done by a TMA reduce-add), so the blocks' inputs are not kept,
+                             and on tensor-core handles the stem runs fused with the first stride-2
+                             conv, so the stem's output (layer 0) is never stored; jde_get_tensor /
+                             jde_act_amax refuse those tensors; 1: every conv layer keeps its own
+                             output tensor (per-layer inspection, calibration); 2: as 1, except that
+                             the stem stays fused (inspection of the fused path; layer 0 refused) */
   int sparse_emb;       /* tensor-core handles, 1 (default): the embedding heads (Sec. 3.1, the linear
                            3x3 -> 512 of each scale) are evaluated only at the detections kept by NMS,
                            inside the post-processing of the handle's own forward (jde_detect_batch,

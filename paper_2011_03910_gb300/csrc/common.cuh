@@ -35,6 +35,14 @@ JDE_DEV size_t tview_off(const TView& t, int n, int y, int x) {
 }
 
 JDE_DEV float leaky01(float v) { return v > 0.f ? v : 0.1f * v; }
+// The same value as leaky01 (0.1 v is above v exactly when v < 0), as a multiply and a max.
+JDE_DEV float leaky01f(float v) { return fmaxf(v, 0.1f * v); }
+// Two floats -> bf16x2 (round to nearest even), lo in the low half.
+JDE_DEV uint32_t pack_bf16x2(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
 
 JDE_DEV void flag_error(int* err, int bit) {
   if (err) atomicOr(err, bit);
@@ -103,6 +111,13 @@ JDE_DEV void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
           smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+      : "memory");
+}
+JDE_DEV void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
       : "memory");
 }
 JDE_DEV void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2, int c3) {

@@ -121,3 +121,17 @@ void post_launch(const float* const* heads, const HeadGeom& g, float conf_thresh
 // Loads the fixed scratch array of jde_postprocess_noalloc onto the current device and records its
 // address; 0 on success, else 1 with a reason in msg.
 int noalloc_scratch_setup(char* msg, size_t len);
+
+// Stem (layer 0) and the first stride-2 conv (layer 1) fused into one tcgen05 kernel: the stem's output
+// stays in shared memory.  lb: the bf16 RGB0 letterbox (haloed); out: layer 1's output (bf16, 64
+// channels, haloed); w0b: the stem's packed bf16 weights [32][32] with its bias in K columns 27..29;
+// w1: layer 1's packed bf16 weights [64][320]; b1b: layer 1's bias parts [64][32] (K columns 0..2).
+// stem_s2_pack writes w0b and b1b (bias = sum of three bf16 parts) from the packed weights and biases.
+struct StemS2Plan;
+constexpr size_t STEM_S2_PACK_BYTES = 32 * 32 * 2 + 64 * 32 * 2;   // w0b + b1b
+cudaError_t stem_s2_pack(const void* w0, const float* bias0, const float* bias1, void* w0b, void* b1b,
+                         cudaStream_t st);
+StemS2Plan* stem_s2_plan_new(const TView& lb, const TView& out, const void* w0b, const void* w1, const void* b1b,
+                             int* err, char* msg, size_t msg_len);
+void stem_s2_plan_free(StemS2Plan* p);
+cudaError_t stem_s2_launch(const StemS2Plan* p, cudaStream_t st);

@@ -22,6 +22,7 @@
 
 #include <atomic>
 #include <map>
+#include <memory>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -97,6 +98,9 @@ bool is_q_layer(int precision, int l) { return precision == JDE_FP8_E4M3 && l > 
 int el_size(int dt) { return dt == 0 ? 4 : (dt == 1 ? 2 : 1); }
 // Sparse embedding head: tensor-core handles with sparse_emb set.
 bool sparse_emb_cfg(const jde_config& c) { return c.sparse_emb && c.precision != JDE_FP32; }
+// Stem and first stride-2 conv fused (the stem's output is never stored): tensor-core handles, unless
+// they keep every layer output (keep_layer_outputs = 1).
+bool fused_stem_cfg(const jde_config& c) { return c.precision != JDE_FP32 && c.keep_layer_outputs != 1; }
 
 // Where each conv reads and writes (tensor ids below, -1 = none).
 struct LayerIO {
@@ -132,6 +136,7 @@ struct Plan {
   int n = 0;
   std::vector<ConvSpec> specs;     // per layer
   std::vector<TcPlan> tc;          // per layer (BF16)
+  std::shared_ptr<StemS2Plan> stem_s2;   // layers 0 and 1 fused (their tc plans unused)
 };
 
 }  // namespace
@@ -169,6 +174,7 @@ struct jde_handle {
   std::vector<float> act_scale = std::vector<float>(T_COUNT, 1.0f);
   bool scales_set = false;
   float* d_amax = nullptr;   // jde_act_amax scratch [JDE_NUM_LAYERS]
+  void* stem_pack = nullptr; // tensor-core handles: fused stem weights with bias parts, then layer 1's bias parts
   // jde_autotune: tile width per layer for (in_w, in_h, n); 0 = the default rule
   std::map<std::tuple<int, int, int>, std::vector<int>> tuned_bn;
 };
@@ -332,9 +338,11 @@ void tensor_desc_table(const jde_handle* h, int in_w, int in_h, std::vector<Tens
 bool two_sets(const jde_handle* h, int t) {
   return (t < JDE_NUM_LAYERS && h->io[t].head >= 0) || (t >= T_PF && t < T_PF + 3);
 }
-// Tensor not allocated: the embedding heads when they are evaluated sparsely.
+// Tensor not allocated: the embedding heads when they are evaluated sparsely, the stem's output when
+// it is fused into the next conv.
 bool not_stored(const jde_handle* h, int t) {
-  return t < JDE_NUM_LAYERS && h->io[t].head >= 3 && sparse_emb_cfg(h->cfg);
+  if (t == 0 && fused_stem_cfg(h->cfg)) return true;
+  return t < JDE_NUM_LAYERS && t >= 0 && h->io[t].head >= 3 && sparse_emb_cfg(h->cfg);
 }
 
 size_t tensor_bytes(const TensorDesc& d, int n) {
@@ -456,6 +464,7 @@ jde_status get_plan(jde_handle* h, ResBuffers* rb, int n, Plan** out) {
     if (c.res.ptr && c.res.dtype == 2) c.res_scale = h->act_scale[buffer_of(h, io.res)];
     if (c.out.dtype == 2) c.out_inv_scale = 1.0f / h->act_scale[buffer_of(h, (int)l)];
     p.specs[l] = c;
+    if (bf16 && l == 1 && fused_stem_cfg(h->cfg)) continue;   // runs inside the fused stem kernel
     if (bf16) {
       char msg[256];
       const void* w = c.q ? static_cast<const void*>(h->w[l].w_q) : static_cast<const void*>(h->w[l].w_nk);
@@ -465,6 +474,13 @@ jde_status get_plan(jde_handle* h, ResBuffers* rb, int n, Plan** out) {
       if (!conv_tc_plan(p.tc[l], c, w, h->w[l].cout_pad_tc, bn, msg, sizeof(msg)))
         return fail(h, JDE_ERR_UNSUPPORTED, "layer %zu: %s", l, msg);
     }
+  }
+  if (bf16 && fused_stem_cfg(h->cfg)) {
+    char msg[256];
+    StemS2Plan* fp = stem_s2_plan_new(view_of(*rb, T_LB, n), view_of(*rb, 1, n), h->stem_pack, h->w[1].w_nk,
+                                      static_cast<char*>(h->stem_pack) + 32 * 32 * 2, h->d_err, msg, sizeof(msg));
+    if (!fp) return fail(h, JDE_ERR_UNSUPPORTED, "layers 0-1: %s", msg);
+    p.stem_s2.reset(fp, stem_s2_plan_free);
   }
   auto res = h->plans.emplace(key, std::move(p));
   *out = &res.first->second;
@@ -672,6 +688,19 @@ jde_status load_weights(jde_handle* h, const void* blob, size_t nbytes) {
       CUDA_OR(h, cudaMemcpy(lw.wscale_host.data(), lw.wscale, sizeof(double) * lw.cout_pad_tc, cudaMemcpyDeviceToHost));
     }
   }
+  if (bf16) {
+    // the fused stem kernel's weights: the stem's with its bias parts, and layer 1's bias parts
+    if (!dmalloc(&h->stem_pack, STEM_S2_PACK_BYTES)) {
+      cudaFree(dblob);
+      return fail(h, JDE_ERR_OOM, "fused stem weights");
+    }
+    h->weight_bytes += STEM_S2_PACK_BYTES;
+    if (stem_s2_pack(h->w[0].w_nk, h->w[0].bias, h->w[1].bias, h->stem_pack,
+                     static_cast<char*>(h->stem_pack) + 32 * 32 * 2, 0) != cudaSuccess) {
+      cudaFree(dblob);
+      return fail(h, JDE_ERR_CUDA, "packing the fused stem weights");
+    }
+  }
   cudaError_t e = cudaDeviceSynchronize();
   cudaFree(dblob);
   if (e != cudaSuccess) return fail(h, JDE_ERR_CUDA, "packing weights: %s", cudaGetErrorString(e));
@@ -821,6 +850,7 @@ void jde_destroy(jde_handle* h) {
     cudaFree(lw.bias);
   }
   cudaFree(h->d_amax);
+  cudaFree(h->stem_pack);
   for (auto& kv : h->res)
     for (void* p : kv.second.mem)
       if (p) cudaFree(p);
@@ -844,7 +874,7 @@ jde_status jde_create(const jde_config* cfg, const void* weights, size_t nbytes,
   if (c.max_batch < 1 || c.max_in_w < 32 || c.max_in_h < 32 || c.max_in_w % 32 || c.max_in_h % 32 ||
       c.max_src_w < 1 || c.max_src_h < 1 || c.max_cand < 64 || c.max_cand > 4096 || c.max_cand % 64 ||
       c.max_streams < 1 || c.max_tracks < 1 || c.max_track_dets < 1 || c.max_track_dets > 4096 ||
-      c.max_tracks > 4096)
+      c.max_tracks > 4096 || c.keep_layer_outputs < 0 || c.keep_layer_outputs > 2)
     return fail(nullptr, JDE_ERR_INVALID_ARG, "config out of range");
   if (cudaSetDevice(c.device) != cudaSuccess) return fail(nullptr, JDE_ERR_CUDA, "cudaSetDevice(%d)", c.device);
   jde_handle* h = new jde_handle();
@@ -930,7 +960,8 @@ jde_status jde_forward(jde_handle* h, const uint8_t* frames, int n, int src_w, i
   for (size_t l = 0; l < L.size(); ++l) {
     if (not_stored(h, (int)l)) continue;
     if (bf16) {
-      cudaError_t e = conv_tc_launch(plan->tc[l], st);
+      const cudaError_t e = (l == 1 && plan->stem_s2) ? stem_s2_launch(plan->stem_s2.get(), st)
+                                                      : conv_tc_launch(plan->tc[l], st);
       if (e != cudaSuccess) return fail(h, JDE_ERR_CUDA, "conv layer %zu: %s", l, cudaGetErrorString(e));
     } else {
       conv_simt_launch(plan->specs[l], h->w[l].w_kn, h->w[l].cout_pad64, st);
@@ -1091,7 +1122,10 @@ jde_status jde_get_tensor(jde_handle* h, int id, void* dst, size_t dst_bytes, in
   if (!h->cur) return fail(h, JDE_ERR_NOT_FOUND, "no forward has run");
   int tid;
   if (id >= 0 && id < JDE_NUM_LAYERS && not_stored(h, id))
-    return fail(h, JDE_ERR_NOT_FOUND, "tensor %d: the embedding head runs only at kept detections (sparse_emb)", id);
+    return fail(h, JDE_ERR_NOT_FOUND,
+                id == 0 ? "tensor 0: the stem's output stays on chip, fused into layer 1 (keep_layer_outputs = 1 keeps it)"
+                        : "tensor %d: the embedding head runs only at kept detections (sparse_emb)",
+                id);
   if (id >= 0 && id < JDE_NUM_LAYERS && overwritten(h, id))
     return fail(h, JDE_ERR_NOT_FOUND, "tensor %d is overwritten in place by its residual block (keep_layer_outputs)", id);
   if (id >= 0 && id < JDE_NUM_LAYERS)
@@ -1195,6 +1229,7 @@ jde_status jde_autotune(jde_handle* h, int n, int in_w, int in_h, void* stream) 
   CUDA_OR(h, cudaEventCreate(&e1));
   for (int l = 0; l < JDE_NUM_LAYERS; ++l) {
     if (not_stored(h, l)) continue;                  // sparse embedding head: not a conv launch
+    if (l == 1 && plan->stem_s2) continue;           // fused with the stem: one tile shape
     const TcPlan& def = plan->tc[l];
     if (def.mode == 2 || def.mode == 3) continue;    // stem and window convs have one tile shape
     const LayerW& lw = h->w[l];
@@ -1263,6 +1298,7 @@ jde_status jde_estimate_device_bytes(const jde_config* cfg, int in_w, int in_h, 
   const auto& L = layers();
   size_t b = sizeof(int) + sizeof(LbAxis) * (size_t)(cfg->max_in_w + cfg->max_in_h);
   for (size_t l = 0; l < L.size(); ++l) b += layer_weight_bytes(L[l], cfg->precision, (int)l);
+  if (bf16) b += STEM_S2_PACK_BYTES;
   std::vector<TensorDesc> td;
   tensor_desc_table(&tmp, in_w, in_h, td);
   for (int t = 0; t < T_COUNT; ++t) {

@@ -57,8 +57,9 @@ def test_fp32_forward_320x192_matches_oracle():
 @pytest.mark.parametrize("keep", [1, 0])
 def test_bf16_forward_320x192_matches_oracle(keep):
     """keep_layer_outputs=1: every layer output against the oracle.  0 (the default): residual stages
-    run in place (each block's 3x3 reduce-adds into the block input's storage); the heads and every
-    layer output still held match, and the overwritten block inputs are refused."""
+    run in place (each block's 3x3 reduce-adds into the block input's storage) and the stem runs fused
+    with layer 1; the heads and every layer output still held match, and the overwritten block inputs
+    and the stem's output are refused."""
     j = jde()
     frames = synth.frames_uniform(1, 2, 192, 320)
     h = make_handle(j.JDE_BF16, max_batch=2, src_w=320, src_h=192, keep_layer_outputs=keep)
@@ -70,14 +71,17 @@ def test_bf16_forward_320x192_matches_oracle(keep):
         print("bf16 320x192 head errors", errs)
         assert bf16_heads_ok(errs), errs
         if keep:
-            bad = per_layer_report(h, acts, 2e-2)
+            # every layer against float64 end to end: the BF16 rounding noise of the layers before it (R23),
+            # up to 2.5e-2 as for the heads; the bit-level per-layer parity is the teacher-forced test
+            # against the BF16 scheme (test_gpu_precision.py)
+            bad = per_layer_report(h, acts, 2.5e-2)
             assert bad == [], bad
             return
         io = net.layer_io()
         block_inputs = {res for _, res in io if res is not None}
         specs = net.layer_specs()
         for l in range(len(specs)):
-            if l in block_inputs:                # overwritten by the block it feeds
+            if l in block_inputs or l == 0:      # overwritten by the block it feeds; the stem stays on chip
                 with pytest.raises(j.JdeError):
                     get_tensor(h, l)
                 continue

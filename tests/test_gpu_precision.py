@@ -95,6 +95,38 @@ def test_each_bf16_layer_matches_the_bf16_scheme_on_the_gpu_inputs():
         j.jde_destroy(h)
 
 
+@pytest.mark.parametrize("in_w,in_h,n", [(320, 192, 2), (1088, 608, 2), (864, 480, 1)])
+def test_fused_stem_and_stride2_conv_match_the_bf16_scheme(in_w, in_h, n):
+    """The stem fused into layer 1 (its output never leaves shared memory), read through
+    keep_layer_outputs = 2.  From the GPU's own letterbox the scheme computes the stem and layer 1; the
+    GPU's layer-1 output must agree up to float32-accumulation flips: almost every element exact, and
+    every element within one bfloat16 step of its own value plus what a flip of one stem value (one
+    step at the stem's largest magnitude) moves it by through layer 1 (times the largest |weight|),
+    twice."""
+    j = jde()
+    h = make_handle(j.JDE_BF16, max_batch=n, in_w=in_w, in_h=in_h, keep_layer_outputs=2)
+    try:
+        frames = synth.frames_uniform(21, n, 1080, 1920)
+        forward(h, frames, in_w, in_h)
+        lb = get_tensor(h, 100)
+        with pytest.raises(j.JdeError):
+            get_tensor(h, 0)                    # fused: the stem's output is not stored
+        t1 = get_tensor(h, 1)
+    finally:
+        j.jde_destroy(h)
+    layers = oracle_layers()
+    s0 = bf16.conv_layer(0, lb, layers)
+    s1 = bf16.conv_layer(1, s0, layers)
+    w1 = bf16.bf16(net.fold_bn(layers[1])[0])
+    flip = float(np.max(np.abs(w1))) * float(bf16_ulp(np.max(np.abs(s0))))
+    exact = float(np.mean(t1 == s1))
+    bound = bf16_ulp(np.maximum(np.abs(t1), np.abs(s1))) + 2 * flip
+    over = float(np.max(np.abs(t1 - s1) / bound))
+    print(in_w, in_h, "layer 1 exact share", exact, "worst diff / bound", over)
+    assert over <= 1.0, over
+    assert exact >= 0.99, exact
+
+
 def test_bf16_end_to_end_error_is_the_scheme_s():
     """The default BF16 handle's heads against float64, next to the BF16 scheme's own heads against
     float64 on the same frames.  Two evaluations of the scheme decorrelate through the network (R23,

@@ -77,7 +77,7 @@ def _act_bytes(n, hw, c, el, pad=1):
     return n * (h + 2 * pad) * (w + 2 * pad) * c * el
 
 
-def test_estimate_accounts_for_in_place_stages_and_the_sparse_embedding_head():
+def test_estimate_accounts_for_in_place_stages_the_fused_stem_and_the_sparse_embedding_head():
     """Host bookkeeping of the activation buffers (no GPU): with keep_layer_outputs = 0 every residual
     block's output shares its stage buffer (the 3x3 reduce-adds into the block input; the stride-16 and
     stride-8 stages live in their concat slices), and with sparse_emb = 1 the three f32 embedding maps
@@ -113,6 +113,8 @@ def test_estimate_accounts_for_in_place_stages_and_the_sparse_embedding_head():
         if s in (2, 3):
             blocks = blocks[:-1] + [first]
         saved += sum(_act_bytes(n, sizes[l], table[l][1], 2) for l in blocks)
+    # the stem's output (32 channels at full size) is not stored when it is fused into layer 1
+    saved += _act_bytes(n, sizes[0], table[0][1], 2)
     assert est(1, 0) - est(0, 0) == saved
     # sparse head: minus the padded f32 embedding maps, plus bf16 copies of their inputs (two sets each)
     emb = [59, 68, 77]
