@@ -57,6 +57,9 @@ def parse():
     p.add_argument("--serve-budget-gb", type=float, default=64.0, help="serving run: device memory budget")
     p.add_argument("--no-fp8", action="store_true", help="skip the E4M3 batch-32 line")
     p.add_argument("--no-autotune", action="store_true", help="default tile rule instead of jde_autotune")
+    p.add_argument("--profile-step", action="store_true",
+                   help="after the warm-up, run one step inside cudaProfilerStart/Stop (for ncu --profile-from-start "
+                        "off) and exit without timing")
     p.add_argument("--latency-batches", type=int, default=220,
                    help="batches of the pipelined step whose latency percentiles are reported (0: skip)")
     return p.parse_args()
@@ -456,6 +459,16 @@ def main():
     for t in range(W):
         step(t)
     torch.cuda.synchronize()
+    if args.profile_step:
+        # one step (forward, post-processing, tracker) inside the profiler range, then stop
+        torch.cuda.profiler.start()
+        step(W)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        assert jde.jde_kernel_errors(h) == 0
+        jde.jde_destroy(h)
+        print(json.dumps({"profile_step": True, "batch": B, "tiles": tiles}), flush=True)
+        return
     sampler = ClockSampler(local)
     sampler.start()
     for t in range(W, W + args.soak):      # keeps the GPU loaded while the clock sampler starts

@@ -228,8 +228,9 @@ jde_status jde_act_amax(jde_handle* h, float* amax, void* stream);
 
 /* Tile autotuner (tensor-core handles): for batches of n frames at in_w x in_h, times every
  * built tile width (64/128/256 output channels, 32 where that is the default; 256 runs on CTA
- * pairs) of every convolution that has more than one, on `stream` with CUDA events over three launches on the handle's
- * activation buffers, and keeps the fastest for later forwards of that shape.  Results do not
+ * pairs) of every convolution that has more than one, on `stream` with CUDA events on the handle's
+ * activation buffers (the median of five launches, each right after a launch of the layer before it,
+ * so the input is as cached as in a forward), and keeps the fastest for later forwards of that shape.  Results do not
  * change: every tile computes each output with the same K order.  Synchronises `stream`;
  * overwrites intermediate activations (the next forward recomputes them).  E4M3 handles need
  * their scales first. */

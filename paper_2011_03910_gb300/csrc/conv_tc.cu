@@ -747,7 +747,7 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
           for (int j = 0; j < FW; ++j) {
             const float acc = Q ? __uint_as_float(r[j]) * m[j] : __uint_as_float(r[j]);
             const float t = acc + v[j];
-            v[j] = c.act ? leaky01(t) : t;
+            v[j] = c.act ? leaky01f(t) : t;
           }
 #pragma unroll
           for (int u = 0; u < FW / 4; ++u) {
@@ -782,6 +782,7 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
         // Rows on the halo are written as zeros, which keeps the halo zero.  E4M3 rows are SWC
         // bytes (64-byte swizzle), one box per pass.
         const bool o8 = c.out.dtype == 2;
+        const uint32_t vmask = valid ? 0xFFFFFFFFu : 0u;   // rows on the halo are stored as zeros
         const int nsub = o8 ? 1 : Cfg::NSUB;
         const int sub_ch = o8 ? Cfg::SWC : Cfg::SUB;
         const int sub_bytes = o8 ? 128 * Cfg::SWC : Cfg::SUB_BYTES;
@@ -860,7 +861,7 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
             }
             if (c.act) {
 #pragma unroll
-              for (int e = 0; e < 32; ++e) v[e] = leaky01(v[e]);
+              for (int e = 0; e < 32; ++e) v[e] = leaky01f(v[e]);
             }
             uint4 outv[4];
             if (o8) {
@@ -903,10 +904,7 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
                 }
                 uint32_t pk[4];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                  __nv_bfloat162 h2 = valid ? __floats2bfloat162_rn(t[2 * e], t[2 * e + 1]) : __floats2bfloat162_rn(0.f, 0.f);
-                  pk[e] = *reinterpret_cast<uint32_t*>(&h2);
-                }
+                for (int e = 0; e < 4; ++e) pk[e] = pack_bf16x2(t[2 * e], t[2 * e + 1]) & vmask;
                 outv[u] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
               }
             }
@@ -961,7 +959,7 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
             for (int j = 0; j < 32; ++j) {
               const float acc = Q ? __uint_as_float(r[j]) * sMult[c0 + j] : __uint_as_float(r[j]);
               const float t = acc + sBias[c0 + j];
-              v[j] = c.act ? leaky01(t) : t;
+              v[j] = c.act ? leaky01f(t) : t;
             }
             if (c.res.ptr) {
               const size_t ro = tview_off(c.res, n, y, x) + ch0;

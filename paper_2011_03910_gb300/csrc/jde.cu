@@ -20,6 +20,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <map>
 #include <memory>
@@ -1224,9 +1225,22 @@ jde_status jde_autotune(jde_handle* h, int n, int in_w, int in_h, void* stream) 
   s = get_plan(h, rb, n, &plan);
   if (s != JDE_OK) return s;
   std::vector<int> best(JDE_NUM_LAYERS, 0);
-  cudaEvent_t e0, e1;
-  CUDA_OR(h, cudaEventCreate(&e0));
-  CUDA_OR(h, cudaEventCreate(&e1));
+  constexpr int REPS = 5;
+  cudaEvent_t e0[REPS], e1[REPS];
+  for (int r = 0; r < REPS; ++r) {
+    CUDA_OR(h, cudaEventCreate(&e0[r]));
+    CUDA_OR(h, cudaEventCreate(&e1[r]));
+  }
+  // the launch before layer l in a forward: its output is (mostly) layer l's input, so re-running it
+  // before each timed launch recreates the cache state a forward gives layer l
+  auto previous = [&](int l) -> cudaError_t {
+    for (int k = l - 1; k >= 0; --k) {
+      if (not_stored(h, k)) continue;
+      if (k == 1 && plan->stem_s2) return stem_s2_launch(plan->stem_s2.get(), st);
+      return conv_tc_launch(plan->tc[k], st);
+    }
+    return cudaSuccess;
+  };
   for (int l = 0; l < JDE_NUM_LAYERS; ++l) {
     if (not_stored(h, l)) continue;                  // sparse embedding head: not a conv launch
     if (l == 1 && plan->stem_s2) continue;           // fused with the stem: one tile shape
@@ -1246,20 +1260,27 @@ jde_status jde_autotune(jde_handle* h, int n, int in_w, int in_h, void* stream) 
         cudaGetLastError();
         continue;
       }
-      CUDA_OR(h, cudaEventRecord(e0, st));
-      for (int r = 0; r < 3; ++r) CUDA_OR(h, conv_tc_launch(cand, st));
-      CUDA_OR(h, cudaEventRecord(e1, st));
-      CUDA_OR(h, cudaEventSynchronize(e1));
-      float ms = 0.f;
-      CUDA_OR(h, cudaEventElapsedTime(&ms, e0, e1));
+      for (int r = 0; r < REPS; ++r) {
+        CUDA_OR(h, previous(l));
+        CUDA_OR(h, cudaEventRecord(e0[r], st));
+        CUDA_OR(h, conv_tc_launch(cand, st));
+        CUDA_OR(h, cudaEventRecord(e1[r], st));
+      }
+      CUDA_OR(h, cudaEventSynchronize(e1[REPS - 1]));
+      float t[REPS];
+      for (int r = 0; r < REPS; ++r) CUDA_OR(h, cudaEventElapsedTime(&t[r], e0[r], e1[r]));
+      std::sort(t, t + REPS);
+      const float ms = t[REPS / 2];   // median launch
       if (ms < best_ms) {
         best_ms = ms;
         best[l] = bn;
       }
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  for (int r = 0; r < REPS; ++r) {
+    cudaEventDestroy(e0[r]);
+    cudaEventDestroy(e1[r]);
+  }
   h->tuned_bn[key] = best;
   h->plans.erase(key);   // rebuilt with the chosen tiles on the next forward
   return JDE_OK;
