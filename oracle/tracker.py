@@ -297,3 +297,126 @@ class Tracker:
         self.last = dict(cost=raw, d2=d2, gated=cost, pairs=pairs, det_track=det_track,
                          matches=sorted((pool[i].id, j) for i, j in pairs if i in matched_t and j in matched_d))
         return [(t.id, t.state, z_to_xyxy(t.mean)) for t in self.tracks]
+
+
+# ----------------------------------------------------------------------------- association cascade
+# The cited JDE tracker associates in three stages instead of Appendix A's single one (readings; this
+# paper's Appendix A does not describe them):
+#  1. confirmed tracks (tracked or lost) against all detections on a motion-fused cost
+#     lambda (1 - cos) + (1 - lambda) d^2, lambda = 0.98, with the same gate (d^2 > gate -> "infinite")
+#     and the same rejection (cost > 0.7 or infinite);
+#  2. the confirmed tracks left unmatched that were tracked (not lost) before this frame, against the
+#     detections left, on 1 - IoU(predicted box, detection box); reject 1 - IoU > 0.5;
+#  3. unconfirmed tracks (born in an earlier frame, never matched since) against the detections still
+#     left, on 1 - IoU; reject 1 - IoU > 0.3; an unconfirmed track left unmatched is removed;
+#  then every matched track gets the Kalman update and the gallery update and becomes tracked,
+#  confirmed tracks left unmatched become lost (removed after the lost limit as before), and the
+#  detections left start tracks: tracked on the stream's first frame, unconfirmed after it.
+# Every stage is a Hungarian assignment (rows in creation order, columns in kept order, transposed
+# when there are more rows) on its sub-matrix.
+MOTION_LAMBDA = 0.98
+IOU_COST_2 = 0.5
+IOU_COST_3 = 0.3
+UNCONFIRMED = 3
+
+
+def iou_xyxy(a, b):
+    """IoU of two boxes (x1, y1, x2, y2), continuous coordinates, 0 for an empty union."""
+    iw = max(0.0, min(a[2], b[2]) - max(a[0], b[0]))
+    ih = max(0.0, min(a[3], b[3]) - max(a[1], b[1]))
+    inter = iw * ih
+    union = (a[2] - a[0]) * (a[3] - a[1]) + (b[2] - b[0]) * (b[3] - b[1]) - inter
+    return inter / union if union > 0 else 0.0
+
+
+class CascadeTracker(Tracker):
+    """Per-stream tracker state and one step of the three-stage association described above."""
+
+    def __init__(self, lam=MOTION_LAMBDA, iou_cost2=IOU_COST_2, iou_cost3=IOU_COST_3, **kw):
+        super().__init__(**kw)
+        self.lam, self.iou_cost2, self.iou_cost3 = lam, iou_cost2, iou_cost3
+        self.frame = 0
+
+    def _stage(self, cost, rows_idx, cols_idx, thresh):
+        """Hungarian on the sub-matrix; pairs (row id, col id) with cost <= thresh and below "infinite"."""
+        if not rows_idx or not cols_idx:
+            return [], np.zeros((len(rows_idx), len(cols_idx)))
+        sub = cost[np.ix_(rows_idx, cols_idx)] if isinstance(cost, np.ndarray) else cost
+        out = []
+        for i, j in assign(sub):
+            if sub[i, j] > thresh or sub[i, j] >= INF_COST:
+                continue
+            out.append((rows_idx[i], cols_idx[j]))
+        return out, sub
+
+    def step(self, rows):
+        rows = np.asarray(rows, np.float64).reshape(-1, 518)
+        K = len(rows)
+        pool = self.tracks
+        prev_state = [t.state for t in pool]
+        for t in pool:
+            t.mean, t.cov = predict(t.mean, t.cov)
+        zs = [xyxy_to_z(r[:4]) for r in rows]
+        Z = np.array(zs).reshape(-1, 4)
+        T = len(pool)
+        cos_cost = np.zeros((T, K))
+        d2 = np.zeros((T, K))
+        for i, t in enumerate(pool):
+            cos_cost[i] = 1.0 - rows[:, 6:] @ t.emb
+            zh, S = project(t.mean, t.cov)
+            L = cholesky_lower(S)
+            W = forward_sub(L, (Z - zh).T)
+            d2[i] = (W * W).sum(0)
+        fused = self.lam * cos_cost + (1.0 - self.lam) * d2
+        fused[d2 > self.gate] = INF_COST
+        confirmed = [i for i in range(T) if prev_state[i] != UNCONFIRMED]
+        unconf = [i for i in range(T) if prev_state[i] == UNCONFIRMED]
+        # stage 1: motion-fused appearance cost over the confirmed tracks
+        m1, sub1 = self._stage(fused, confirmed, list(range(K)), self.assign_thresh)
+        det_left = [j for j in range(K) if j not in {d for _, d in m1}]
+        matched1 = {i for i, _ in m1}
+        # stage 2: IoU of the predicted box for the confirmed tracks tracked before this frame
+        trk2 = [i for i in confirmed if i not in matched1 and prev_state[i] == TRACKED]
+        boxes = [z_to_xyxy(t.mean) for t in pool]
+        iou_cost = np.array([[1.0 - iou_xyxy(boxes[i], rows[j, :4]) for j in range(K)] for i in range(T)]).reshape(T, K)
+        m2, sub2 = self._stage(iou_cost, trk2, det_left, self.iou_cost2)
+        det_left3 = [j for j in det_left if j not in {d for _, d in m2}]
+        # stage 3: unconfirmed tracks on IoU
+        m3, sub3 = self._stage(iou_cost, unconf, det_left3, self.iou_cost3)
+        matches = m1 + m2 + m3
+        matched_t = {i for i, _ in matches}
+        matched_d = {j for _, j in matches}
+        for i, j in matches:
+            t = pool[i]
+            t.mean, t.cov = update(t.mean, t.cov, zs[j])
+            e = self.momentum * t.emb + (1 - self.momentum) * rows[j, 6:]
+            t.emb = e / math.sqrt(float(e @ e))
+            t.state = TRACKED
+            t.since = 0
+        det_track = [None] * K
+        for i, j in matches:
+            det_track[j] = pool[i].id
+        survivors = []
+        for i, t in enumerate(pool):
+            if i not in matched_t:
+                if prev_state[i] == UNCONFIRMED:
+                    continue                      # an unconfirmed track is dropped at its first miss
+                t.state = LOST
+                t.since += 1
+                if t.since > self.lost_max:
+                    continue
+            survivors.append(t)
+        first = self.frame == 0
+        for j in range(K):
+            if j not in matched_d:
+                nt = Track(self.next_id, zs[j], rows[j, 6:])
+                nt.state = TRACKED if first else UNCONFIRMED
+                survivors.append(nt)
+                det_track[j] = self.next_id
+                self.next_id += 1
+        self.tracks = survivors
+        self.frame += 1
+        self.last = dict(cost=cos_cost, d2=d2, gated=fused, fused=fused, iou=iou_cost, stages=(m1, m2, m3),
+                         subs=(sub1, sub2, sub3), det_track=det_track,
+                         matches=sorted((pool[i].id, j) for i, j in matches))
+        return [(t.id, t.state, z_to_xyxy(t.mean)) for t in self.tracks]

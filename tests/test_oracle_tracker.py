@@ -226,3 +226,146 @@ def test_gallery_update_is_the_normalised_momentum_average():
     # the cost of the next step uses the gallery: 1 - <gallery, d>
     T.step(np.stack([det_row([100, 100, 140, 220], d)]))
     assert T.last["cost"][0, 0] == pytest.approx(1.0 - float(v2 @ d[:2]) / np.linalg.norm(v2), abs=1e-15)
+
+
+# ----------------------------------------------------------------------------- association cascade
+def unit(v):
+    v = np.asarray(v, np.float64)
+    return v / np.linalg.norm(v)
+
+
+def test_cascade_iou_of_boxes_hand_cases():
+    assert tk.iou_xyxy([0, 0, 2, 2], [0, 0, 2, 2]) == 1.0
+    assert tk.iou_xyxy([0, 0, 2, 2], [3, 3, 4, 4]) == 0.0
+    assert tk.iou_xyxy([0, 0, 2, 2], [1, 0, 3, 2]) == pytest.approx(1.0 / 3.0, abs=1e-15)
+    assert tk.iou_xyxy([0, 0, 4, 4], [1, 1, 3, 3]) == pytest.approx(0.25, abs=1e-15)
+    assert tk.iou_xyxy([0, 0, 0, 0], [0, 0, 0, 0]) == 0.0
+
+
+def test_cascade_stage1_cost_is_the_motion_fused_cost():
+    """lambda (1 - <e, d>) + (1 - lambda) y^T S^-1 y, the Mahalanobis term by the explicit inverse."""
+    g = np.random.default_rng(21)
+    e, d = unit(g.standard_normal(512)), unit(g.standard_normal(512))
+    d = unit(0.9 * e + 0.3 * d)
+    T = tk.CascadeTracker()
+    T.step(np.stack([det_row([100, 100, 140, 220], e)]))
+    T.step(np.stack([det_row([103, 98, 143, 219], d)]))
+    # recompute from the track's state before the second step: predict, project, explicit inverse
+    T2 = tk.CascadeTracker()
+    T2.step(np.stack([det_row([100, 100, 140, 220], e)]))
+    t = T2.tracks[0]
+    mean, cov = tk.predict(t.mean, t.cov)
+    zh, S = tk.project(mean, cov)
+    y = tk.xyxy_to_z(np.array([103.0, 98.0, 143.0, 219.0])) - zh
+    d2 = float(y @ np.linalg.inv(S) @ y)
+    want = tk.MOTION_LAMBDA * (1.0 - float(e @ d)) + (1.0 - tk.MOTION_LAMBDA) * d2
+    assert T.last["fused"][0, 0] == pytest.approx(want, rel=1e-10)
+    assert T.last["stages"][0] == [(0, 0)] and T.tracks[0].id == 1
+
+
+def test_cascade_iou_stage_keeps_the_id_through_an_appearance_change():
+    """Same box, unrelated appearance: the single-stage association rejects it (cosine cost ~1 > 0.7)
+    and starts a new id; the cascade's IoU stage matches it to the tracked track (IoU 1 > 0.5)."""
+    g = np.random.default_rng(22)
+    e1, e2 = g.standard_normal(512), g.standard_normal(512)
+    A, C = tk.Tracker(), tk.CascadeTracker()
+    for T in (A, C):
+        T.step(np.stack([det_row([100, 100, 140, 220], e1)]))
+    a = A.step(np.stack([det_row([100, 100, 140, 220], e2)]))
+    c = C.step(np.stack([det_row([100, 100, 140, 220], e2)]))
+    assert [(i, s) for i, s, _ in a] == [(1, tk.LOST), (2, tk.TRACKED)]
+    assert [(i, s) for i, s, _ in c] == [(1, tk.TRACKED)]
+    m1, m2, m3 = C.last["stages"]
+    assert m1 == [] and m2 == [(0, 0)] and m3 == []
+
+
+def test_cascade_iou_stage_skips_lost_tracks_and_births_are_unconfirmed():
+    g = np.random.default_rng(23)
+    e1, e2 = g.standard_normal(512), g.standard_normal(512)
+    C = tk.CascadeTracker()
+    C.step(np.stack([det_row([100, 100, 140, 220], e1)]))
+    C.step(np.zeros((0, 518)))                                   # id 1 lost
+    out = C.step(np.stack([det_row([100, 100, 140, 220], e2)]))  # unrelated appearance, lost track
+    assert [(i, s) for i, s, _ in out] == [(1, tk.LOST), (2, tk.UNCONFIRMED)]
+
+
+def test_cascade_unconfirmed_tracks_are_confirmed_by_iou_or_removed():
+    g = np.random.default_rng(24)
+    ea, eb = g.standard_normal(512), g.standard_normal(512)
+    first = np.stack([det_row([100, 100, 140, 220], ea)])
+    second = np.stack([det_row([100, 100, 140, 220], ea), det_row([500, 300, 560, 450], eb)])
+    # confirmed: the next frame has B at IoU >= 0.7 (moved by a pixel), even with an unrelated embedding
+    C = tk.CascadeTracker()
+    C.step(first)
+    out = C.step(second)
+    assert [(i, s) for i, s, _ in out] == [(1, tk.TRACKED), (2, tk.UNCONFIRMED)]
+    out = C.step(np.stack([det_row([101, 101, 141, 221], ea), det_row([501, 301, 561, 451], g.standard_normal(512))]))
+    assert [(i, s) for i, s, _ in out] == [(1, tk.TRACKED), (2, tk.TRACKED)]
+    assert C.last["stages"][2] == [(1, 1)]
+    # removed: the next frame has no detection near B (not lost: an unconfirmed track is dropped)
+    C = tk.CascadeTracker()
+    C.step(first)
+    C.step(second)
+    out = C.step(np.stack([det_row([101, 101, 141, 221], ea)]))
+    assert [(i, s) for i, s, _ in out] == [(1, tk.TRACKED)]
+    # an IoU below 0.7 does not confirm (B moved by 20 px): B is dropped, the detection is a new unconfirmed id
+    C = tk.CascadeTracker()
+    C.step(first)
+    C.step(second)
+    out = C.step(np.stack([det_row([101, 101, 141, 221], ea), det_row([520, 320, 580, 470], eb)]))
+    assert tk.iou_xyxy([500, 300, 560, 450], [520, 320, 580, 470]) < 0.7
+    assert [(i, s) for i, s, _ in out] == [(1, tk.TRACKED), (3, tk.UNCONFIRMED)]
+
+
+def test_cascade_first_frame_births_are_confirmed():
+    g = np.random.default_rng(25)
+    C = tk.CascadeTracker()
+    out = C.step(np.stack([det_row([100 + 200 * k, 100, 140 + 200 * k, 220], g.standard_normal(512)) for k in range(3)]))
+    assert [(i, s) for i, s, _ in out] == [(1, tk.TRACKED), (2, tk.TRACKED), (3, tk.TRACKED)]
+
+
+def test_cascade_every_stage_is_an_optimal_assignment():
+    """Random small scenes: each stage's chosen pairs (before rejection) minimise the stage's summed cost
+    over all assignments of its sub-matrix (brute force)."""
+    g = np.random.default_rng(26)
+    for trial in range(20):
+        C = tk.CascadeTracker(assign_thresh=2.0, iou_cost2=1.0, iou_cost3=1.0)   # accept every pair
+        n0 = int(g.integers(2, 6))
+        embs = [g.standard_normal(512) for _ in range(n0)]
+        boxes = [np.array([50 + 120 * k, 100, 90 + 120 * k, 220], float) for k in range(n0)]
+        C.step(np.stack([det_row(b, e) for b, e in zip(boxes, embs)]))
+        k1 = int(g.integers(1, 6))
+        rows = [det_row(boxes[int(g.integers(0, n0))] + g.normal(0, 3, 4), unit(embs[int(g.integers(0, n0))] +
+                                                                                  g.normal(0, 0.5, 512)))
+                for _ in range(k1)]
+        C.step(np.stack(rows))
+        for sub in C.last["subs"]:
+            if sub.size == 0:
+                continue
+            r, c = sub.shape
+            if r <= c:
+                best = min(sum(sub[i, p[i]] for i in range(r)) for p in itertools.permutations(range(c), r))
+            else:
+                best = min(sum(sub[p[j], j] for j in range(c)) for p in itertools.permutations(range(r), c))
+            chosen = tk.assign(sub)
+            assert sum(sub[i, j] for i, j in chosen) == pytest.approx(best, rel=1e-12, abs=1e-12)
+
+
+def test_cascade_planted_objects_keep_their_ids():
+    """The three-stage association keeps every detected planted object on one id for the whole clip."""
+    r, nw, nh, px, py = net.letterbox_geometry(1920, 1080, 1088, 608)
+    clip = synth.PlantedClip(3, 8, 40, 1088, 608, pp.anchors(), pp.STRIDES, r, px, py)
+    C = tk.CascadeTracker()
+    owner = {}
+    for t in range(40):
+        dets, embs, truth = clip.frame(t)
+        rows = pp.postprocess_frame(dets, embs, r, px, py)["rows"]
+        C.step(rows)
+        for (o, cx, cy, w, h) in truth:
+            d = np.hypot((rows[:, 0] + rows[:, 2]) / 2 - cx, (rows[:, 1] + rows[:, 3]) / 2 - cy)
+            j = int(np.argmin(d))
+            if d[j] > 1e-3:
+                continue
+            tid = C.last["det_track"][j]
+            assert owner.setdefault(o, tid) == tid, "identity switch"
+    assert len(owner) == 8
