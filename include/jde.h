@@ -56,8 +56,9 @@ typedef enum {
  * the heads are written in f32. */
 typedef enum { JDE_FP32 = 0, JDE_BF16 = 1, JDE_FP8_E4M3 = 2 } jde_precision;
 
-/* Track states reported by jde_track_step (Appendix A: active / lost). */
-enum { JDE_TRACK_TRACKED = 1, JDE_TRACK_LOST = 2 };
+/* Track states reported by jde_track_step (Appendix A: active / lost; the association cascade adds
+ * unconfirmed tracks: born after a stream's first frame and not matched since). */
+enum { JDE_TRACK_TRACKED = 1, JDE_TRACK_LOST = 2, JDE_TRACK_UNCONFIRMED = 3 };
 
 /* Values a detection row carries (Appendix A: [n, num_detections, 518]). */
 #define JDE_ROW 518
@@ -96,6 +97,19 @@ typedef struct {
                            jde_postprocess with heads NULL), from copies of their input maps; their
                            dense maps are not computed (jde_get_tensor and jde_act_amax refuse them).
                            0: dense embedding maps */
+  int assoc_cascade;    /* 0 (default): the single-stage association of Appendix A (items 5-9).  1: the
+                           three-stage association of the cited JDE tracker: (1) confirmed tracks (tracked
+                           or lost) against all detections on motion_lambda (1 - cos) + (1 - motion_lambda)
+                           d^2 (d^2 the squared Mahalanobis distance, gated as in item 6), rejected above
+                           assign_thresh; (2) the confirmed tracks left that were tracked before the frame,
+                           against the detections left, on 1 - IoU(Kalman-predicted box, detection box),
+                           rejected above iou_cost2; (3) unconfirmed tracks against the detections still
+                           left on 1 - IoU, rejected above iou_cost3, an unmatched unconfirmed track being
+                           removed; detections left start tracks, tracked on a stream's first frame and
+                           unconfirmed after it */
+  double motion_lambda; /* cascade stage 1 weight of the appearance cost, default 0.98 */
+  double iou_cost2;     /* cascade stage 2 rejection threshold on 1 - IoU, default 0.5 */
+  double iou_cost3;     /* cascade stage 3 rejection threshold on 1 - IoU, default 0.3 */
 } jde_config;
 
 /* One layer of the network as this library builds it (for the weights blob). */

@@ -827,6 +827,10 @@ void jde_default_config(jde_config* c) {
   c->max_track_dets = 1024;
   c->device = 0;
   c->sparse_emb = 1;
+  c->assoc_cascade = 0;
+  c->motion_lambda = 0.98;
+  c->iou_cost2 = 0.5;
+  c->iou_cost3 = 0.3;
 }
 
 int jde_layer_table(jde_layer_desc* out, int cap) {
@@ -875,7 +879,9 @@ jde_status jde_create(const jde_config* cfg, const void* weights, size_t nbytes,
   if (c.max_batch < 1 || c.max_in_w < 32 || c.max_in_h < 32 || c.max_in_w % 32 || c.max_in_h % 32 ||
       c.max_src_w < 1 || c.max_src_h < 1 || c.max_cand < 64 || c.max_cand > 4096 || c.max_cand % 64 ||
       c.max_streams < 1 || c.max_tracks < 1 || c.max_track_dets < 1 || c.max_track_dets > 4096 ||
-      c.max_tracks > 4096 || c.keep_layer_outputs < 0 || c.keep_layer_outputs > 2)
+      c.max_tracks > 4096 || c.keep_layer_outputs < 0 || c.keep_layer_outputs > 2 || c.assoc_cascade < 0 ||
+      c.assoc_cascade > 1 || !(c.motion_lambda >= 0.0 && c.motion_lambda <= 1.0) || !(c.iou_cost2 >= 0.0) ||
+      !(c.iou_cost3 >= 0.0))
     return fail(nullptr, JDE_ERR_INVALID_ARG, "config out of range");
   if (cudaSetDevice(c.device) != cudaSuccess) return fail(nullptr, JDE_ERR_CUDA, "cudaSetDevice(%d)", c.device);
   jde_handle* h = new jde_handle();

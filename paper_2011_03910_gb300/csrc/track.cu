@@ -8,6 +8,10 @@
 //   cost   : C[k][j] = 1 - <e_k, d_j> (compensated f32 dot of unit embeddings), replaced by
 //            the "infinite" 1e5 when the squared Mahalanobis distance
 //            |L^-1 (z_j - H x_k)|^2 exceeds the chi-square gate;
+//   cascade (jde_config.assoc_cascade): cost holds lambda (1 - cos) + (1 - lambda) d^2 (gated), and
+//            assign_cascade runs three Hungarian stages on sub-matrices (confirmed tracks on that cost;
+//            the tracked ones left on 1 - IoU of the predicted box; unconfirmed tracks on 1 - IoU),
+//            removes unmatched unconfirmed tracks and confirms births only on a stream's first step;
 //   assign : shortest-augmenting-path Hungarian in f64 (one warp per stream;
 //            rows = the smaller side, tracks in creation order, detections in
 //            kept order; columns scanned ascending, first minimum wins), pairs
@@ -49,6 +53,8 @@ struct StepArgs {
   float assign_thresh;
   int lost_max;
   float momentum;
+  int cascade;            // three-stage association
+  double lam, iou2, iou3; // cascade: appearance weight of stage 1, rejection thresholds of stages 2 and 3
   int* err;
   // outputs
   long long* o_id;
@@ -84,6 +90,7 @@ __global__ void reset_kernel(TrackState t, int s) {
     t.n_tracks[s] = 0;
     t.next_id[s] = 1;
     t.free_top[s] = T;
+    t.frames[s] = 0;
   }
 }
 
@@ -234,6 +241,11 @@ __global__ void cost_kernel(StepArgs a, Slots sl) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) d2 += w[i] * w[i];
     double cost = 1.0 - ((double)acc[q] + (double)comp[q]);
+    if (a.cascade) {   // motion-fused cost, tracks x detections row-major
+      cost = d2 > a.gate ? INF_COST : a.lam * cost + (1.0 - a.lam) * d2;
+      A[(size_t)k * D + j] = cost;
+      continue;
+    }
     if (d2 > a.gate) cost = INF_COST;
     if (trans)
       A[(size_t)j * M + k] = cost;
@@ -253,6 +265,82 @@ __device__ __forceinline__ void argmin_warp(double& v, int& j) {
       j = oj;
     }
   }
+}
+
+// Shortest-augmenting-path Hungarian with row and column potentials on the R x M cost matrix A
+// (row-major, R <= M), run by one warp.  On return p[j] is the 1-based row assigned to column j (0 =
+// none).  Columns are scanned in ascending order and the first minimum wins.  Returns false when a step
+// finds no finite free column (the matrix holds NaN).
+__device__ bool hungarian_warp(const double* A, int R, int M, double* u, double* v, double* minv, int* p, int* way,
+                               uint8_t* used) {
+  const int lane = threadIdx.x & 31;
+  for (int j = lane; j <= M; j += 32) {
+    v[j] = 0.0;
+    p[j] = 0;
+    way[j] = 0;
+  }
+  for (int i = lane; i <= R; i += 32) u[i] = 0.0;
+  __syncwarp();
+  bool fail = false;
+  for (int i = 1; i <= R && !fail; ++i) {
+    if (lane == 0) p[0] = i;
+    for (int j = lane; j <= M; j += 32) {
+      minv[j] = INFINITY;
+      used[j] = 0;
+    }
+    __syncwarp();
+    int j0 = 0;
+    for (int iter = 0; iter <= M; ++iter) {
+      if (lane == 0) used[j0] = 1;
+      __syncwarp();
+      const int i0 = p[j0];
+      const double ui0 = u[i0];
+      const double* arow = A + (size_t)(i0 - 1) * M;
+      double best = INFINITY;
+      int bestj = 0x7fffffff;
+      for (int j = lane + 1; j <= M; j += 32) {
+        if (!used[j]) {
+          const double cur = (arow[j - 1] - ui0) - v[j];
+          if (cur < minv[j]) {
+            minv[j] = cur;
+            way[j] = j0;
+          }
+          if (minv[j] < best) {
+            best = minv[j];
+            bestj = j;
+          }
+        }
+      }
+      argmin_warp(best, bestj);
+      if (bestj == 0x7fffffff) {   // no finite free column
+        fail = true;
+        break;
+      }
+      const double delta = best;
+      for (int j = lane; j <= M; j += 32) {
+        if (used[j]) {
+          u[p[j]] += delta;
+          v[j] -= delta;
+        } else {
+          minv[j] -= delta;
+        }
+      }
+      __syncwarp();
+      j0 = bestj;
+      if (p[j0] == 0) break;
+    }
+    __syncwarp();
+    if (lane == 0 && !fail) {
+      int jj = j0;
+      for (int guard = 0; guard <= M && jj; ++guard) {
+        const int j1 = way[jj];
+        p[jj] = p[j1];
+        jj = j1;
+      }
+    }
+    __syncwarp();
+  }
+  return !fail;
 }
 
 __global__ void __launch_bounds__(256) assign_kernel(StepArgs a, Slots sl) {
@@ -278,7 +366,7 @@ __global__ void __launch_bounds__(256) assign_kernel(StepArgs a, Slots sl) {
   int* det_trk = trk_det + T;        // [Dmax]
   int* new_order = det_trk + Dmax;   // [T]
   uint8_t* used = reinterpret_cast<uint8_t*>(new_order + T);
-  __shared__ int s_fail, s_nnew, s_births;
+  __shared__ int s_fail, s_nnew;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const double* const Ag = a.t.cost + (size_t)b * T * Dmax;
   const bool cached = (long long)R * M <= ASSIGN_COST_CACHE;
@@ -291,71 +379,8 @@ __global__ void __launch_bounds__(256) assign_kernel(StepArgs a, Slots sl) {
   __syncthreads();
 
   if (warp == 0 && R > 0) {
-    for (int j = lane; j <= M; j += 32) {
-      v[j] = 0.0;
-      p[j] = 0;
-      way[j] = 0;
-    }
-    for (int i = lane; i <= R; i += 32) u[i] = 0.0;
+    if (!hungarian_warp(A, R, M, u, v, minv, p, way, used) && lane == 0) s_fail = 1;
     __syncwarp();
-    for (int i = 1; i <= R && !s_fail; ++i) {
-      if (lane == 0) p[0] = i;
-      for (int j = lane; j <= M; j += 32) {
-        minv[j] = INFINITY;
-        used[j] = 0;
-      }
-      __syncwarp();
-      int j0 = 0;
-      for (int iter = 0; iter <= M; ++iter) {
-        if (lane == 0) used[j0] = 1;
-        __syncwarp();
-        const int i0 = p[j0];
-        const double ui0 = u[i0];
-        const double* arow = A + (size_t)(i0 - 1) * M;
-        double best = INFINITY;
-        int bestj = 0x7fffffff;
-        for (int j = lane + 1; j <= M; j += 32) {
-          if (!used[j]) {
-            const double cur = (arow[j - 1] - ui0) - v[j];
-            if (cur < minv[j]) {
-              minv[j] = cur;
-              way[j] = j0;
-            }
-            if (minv[j] < best) {
-              best = minv[j];
-              bestj = j;
-            }
-          }
-        }
-        argmin_warp(best, bestj);
-        if (bestj == 0x7fffffff) {   // no finite free column: cost matrix holds NaN
-          if (lane == 0) s_fail = 1;
-          break;
-        }
-        const double delta = best;
-        for (int j = lane; j <= M; j += 32) {
-          if (used[j]) {
-            u[p[j]] += delta;
-            v[j] -= delta;
-          } else {
-            minv[j] -= delta;
-          }
-        }
-        __syncwarp();
-        j0 = bestj;
-        if (p[j0] == 0) break;
-      }
-      __syncwarp();
-      if (lane == 0 && !s_fail) {
-        int jj = j0;
-        for (int guard = 0; guard <= M && jj; ++guard) {
-          const int j1 = way[jj];
-          p[jj] = p[j1];
-          jj = j1;
-        }
-      }
-      __syncwarp();
-    }
     // pairs, rejected when the (gated) cost is above the threshold
     for (int j = lane + 1; j <= M; j += 32) {
       if (!p[j] || s_fail) continue;
@@ -466,7 +491,6 @@ __global__ void __launch_bounds__(256) assign_kernel(StepArgs a, Slots sl) {
       }
       new_order[nn++] = slot;
     }
-    int births = 0;
     long long nid = a.t.next_id[s];
     for (int j = 0; j < D; ++j) {
       if (det_trk[j] >= 0) continue;
@@ -482,12 +506,10 @@ __global__ void __launch_bounds__(256) assign_kernel(StepArgs a, Slots sl) {
       a.t.last_det[ts] = j;
       det_trk[j] = -2 - slot;   // marks the birth slot for the parallel init below
       new_order[nn++] = slot;
-      ++births;
     }
     a.t.next_id[s] = nid;
     a.t.free_top[s] = top;
     s_nnew = nn;
-    s_births = births;
   }
   __syncthreads();
   const int nn = s_nnew;
@@ -524,10 +546,297 @@ __global__ void __launch_bounds__(256) assign_kernel(StepArgs a, Slots sl) {
     const float* dv = rows + (size_t)j * 518 + 6;
     for (int q = 0; q < 16; ++q) e[q * 32 + lane] = dv[q * 32 + lane];
   }
-  if (tid == 0) a.t.n_tracks[s] = nn;
+  if (tid == 0) {
+    a.t.n_tracks[s] = nn;
+    a.t.frames[s] += 1;
+  }
   __syncthreads();
   // output in track order
   if (tid == 0) a.o_count[b] = nn;
+  for (int k = tid; k < nn && k < a.o_cap; k += blockDim.x) {
+    const int slot = new_order[k];
+    const size_t ts = (size_t)s * T + slot;
+    const double* m = a.t.mean + ts * 8;
+    const size_t o = (size_t)b * a.o_cap + k;
+    const double w = m[2] * m[3];
+    a.o_id[o] = a.t.id[ts];
+    a.o_box[o * 4 + 0] = (float)(m[0] - w / 2);
+    a.o_box[o * 4 + 1] = (float)(m[1] - m[3] / 2);
+    a.o_box[o * 4 + 2] = (float)(m[0] + w / 2);
+    a.o_box[o * 4 + 3] = (float)(m[1] + m[3] / 2);
+    a.o_state[o] = a.t.state[ts];
+    if (a.o_det) a.o_det[o] = a.t.last_det[ts];
+  }
+}
+
+
+// IoU of the track's Kalman box (state mean: cx, cy, a, h) and a detection row's box (x1, y1, x2, y2).
+__device__ double iou_mean_row(const double* m, const float* row) {
+  const double w = m[2] * m[3];
+  const double ax1 = m[0] - w / 2, ay1 = m[1] - m[3] / 2, ax2 = m[0] + w / 2, ay2 = m[1] + m[3] / 2;
+  const double bx1 = row[0], by1 = row[1], bx2 = row[2], by2 = row[3];
+  const double iw = fmax(0.0, fmin(ax2, bx2) - fmax(ax1, bx1));
+  const double ih = fmax(0.0, fmin(ay2, by2) - fmax(ay1, by1));
+  const double inter = iw * ih;
+  const double uni = (ax2 - ax1) * (ay2 - ay1) + (bx2 - bx1) * (by2 - by1) - inter;
+  return uni > 0.0 ? inter / uni : 0.0;
+}
+
+// Kalman update of track slot ts with measurement z (K = P H^T S^-1 through the factor L of S,
+// x += K (z - H x), P -= K S K^T).
+__device__ void kalman_update(double* m, double* P, const double* L, const double (&z)[4]) {
+  const double hp = m[3];
+  const double rp = (SP * hp) * (SP * hp);
+  double S[16];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) S[i * 4 + j] = P[i * 8 + j];
+  S[0] += rp;
+  S[5] += rp;
+  S[10] += 1e-1 * 1e-1;
+  S[15] += rp;
+  double K[32];
+  for (int i = 0; i < 8; ++i) {
+    double t[4];
+    for (int r = 0; r < 4; ++r) {
+      double vv = P[i * 8 + r];
+      for (int c = 0; c < r; ++c) vv -= L[r * 4 + c] * t[c];
+      t[r] = vv / L[r * 4 + r];
+    }
+    for (int r = 3; r >= 0; --r) {
+      double vv = t[r];
+      for (int c = r + 1; c < 4; ++c) vv -= L[c * 4 + r] * K[i * 4 + c];
+      K[i * 4 + r] = vv / L[r * 4 + r];
+    }
+  }
+  double y[4];
+  for (int r = 0; r < 4; ++r) y[r] = z[r] - m[r];
+  for (int i = 0; i < 8; ++i) {
+    double acc = 0.0;
+    for (int r = 0; r < 4; ++r) acc += K[i * 4 + r] * y[r];
+    m[i] += acc;
+  }
+  double KS[32];
+  for (int i = 0; i < 8; ++i)
+    for (int c = 0; c < 4; ++c) {
+      double acc = 0.0;
+      for (int r = 0; r < 4; ++r) acc += K[i * 4 + r] * S[r * 4 + c];
+      KS[i * 4 + c] = acc;
+    }
+  for (int i = 0; i < 8; ++i)
+    for (int j = 0; j < 8; ++j) {
+      double acc = 0.0;
+      for (int c = 0; c < 4; ++c) acc += KS[i * 4 + c] * K[j * 4 + c];
+      P[i * 8 + j] -= acc;
+    }
+}
+
+// Three-stage association (one block per stream): stage 1 confirmed tracks x all detections on the fused
+// cost, stage 2 the confirmed tracks left that were tracked before the step x the detections left on
+// 1 - IoU, stage 3 unconfirmed tracks x the detections still left on 1 - IoU.  Each stage's sub-matrix
+// (rows in creation order, columns in kept order, transposed when it has more rows) is solved by the
+// warp Hungarian; pairs above the stage's threshold (or "infinite") are rejected.  Then Kalman and
+// gallery updates of every matched track, lost bookkeeping of unmatched confirmed tracks, removal of
+// unmatched unconfirmed ones, births (confirmed on the stream's first step, else unconfirmed), output.
+constexpr int STATE_REMOVED = 0;
+__global__ void __launch_bounds__(256) assign_cascade_kernel(StepArgs a, Slots sl) {
+  extern __shared__ uint8_t smem[];
+  const int b = blockIdx.x;
+  const int s = sl.stream[b];
+  const int T = a.t.max_tracks;
+  const int Dmax = a.t.max_dets;
+  const int nt = a.t.n_tracks[s];
+  const int D = det_count(a, b);
+  const int MM = T > Dmax ? T : Dmax;
+  double* const cache = reinterpret_cast<double*>(smem);
+  double* u = cache + ASSIGN_COST_CACHE;
+  double* v = u + (MM + 1);
+  double* minv = v + (MM + 1);
+  int* p = reinterpret_cast<int*>(minv + (MM + 1));
+  int* way = p + (MM + 1);
+  int* trk_det = way + (MM + 1);     // [T] by order index
+  int* det_trk = trk_det + T;        // [Dmax]
+  int* new_order = det_trk + Dmax;   // [T]
+  int* ridx = new_order + T;         // [MM] rows of the current stage (order indices)
+  int* cidx = ridx + MM;             // [MM] columns of the current stage (detection rows)
+  int* pstate = cidx + MM;           // [T] state of each track before the step
+  uint8_t* used = reinterpret_cast<uint8_t*>(pstate + T);
+  __shared__ int s_fail, s_nr, s_nc, s_nnew;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double* const full = a.t.cost + (size_t)b * T * Dmax;    // stage-1 cost [nt][D]
+  double* const big = a.t.cost2 + (size_t)b * T * Dmax;          // sub-matrices above the shared cache
+  const float* rows = a.rows + (size_t)b * a.cap * 518;
+  for (int k = tid; k < T; k += blockDim.x) trk_det[k] = -1;
+  for (int j = tid; j < Dmax; j += blockDim.x) det_trk[j] = -1;
+  for (int k = tid; k < nt; k += blockDim.x) pstate[k] = a.t.state[(size_t)s * T + a.t.order[(size_t)s * T + k]];
+  if (tid == 0) s_fail = 0;
+  __syncthreads();
+
+  for (int stage = 0; stage < 3; ++stage) {
+    if (tid == 0) {   // the stage's rows and columns, in order (O(T + D) integer work)
+      int nr = 0, nc = 0;
+      for (int k = 0; k < nt; ++k) {
+        const int ps = pstate[k];
+        const bool take = stage == 0   ? ps != JDE_TRACK_UNCONFIRMED
+                          : stage == 1 ? (ps == JDE_TRACK_TRACKED && trk_det[k] < 0)
+                                       : ps == JDE_TRACK_UNCONFIRMED;
+        if (take) ridx[nr++] = k;
+      }
+      for (int j = 0; j < D; ++j)
+        if (det_trk[j] < 0) cidx[nc++] = j;
+      s_nr = nr;
+      s_nc = nc;
+    }
+    __syncthreads();
+    const int nr = s_nr, nc = s_nc;
+    if (nr == 0 || nc == 0 || s_fail) continue;   // block-uniform
+    const bool trans = nr > nc;
+    const int R = trans ? nc : nr, M = trans ? nr : nc;
+    double* const A = (long long)R * M <= ASSIGN_COST_CACHE ? cache : big;
+    for (int e = tid; e < R * M; e += blockDim.x) {
+      const int r = e / M, c = e - (e / M) * M;
+      const int k = ridx[trans ? c : r], j = cidx[trans ? r : c];
+      double cost;
+      if (stage == 0) {
+        cost = full[(size_t)k * D + j];
+      } else {
+        const int slot = a.t.order[(size_t)s * T + k];
+        cost = 1.0 - iou_mean_row(a.t.mean + ((size_t)s * T + slot) * 8, rows + (size_t)j * 518);
+      }
+      A[e] = cost;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      const bool ok = hungarian_warp(A, R, M, u, v, minv, p, way, used);
+      if (!ok && lane == 0) s_fail = 1;
+      const double thr = stage == 0 ? (double)a.assign_thresh : (stage == 1 ? a.iou2 : a.iou3);
+      for (int jj = lane + 1; ok && jj <= M; jj += 32) {
+        if (!p[jj]) continue;
+        const int r = p[jj] - 1, c = jj - 1;
+        const double cost = A[(size_t)r * M + c];
+        if (cost > thr || cost >= INF_COST) continue;
+        const int k = ridx[trans ? c : r], j = cidx[trans ? r : c];
+        trk_det[k] = j;
+        det_trk[j] = k;
+      }
+    }
+    __syncthreads();
+  }
+  if (s_fail) flag_error(a.err, KERR_TIMEOUT);
+
+  // Kalman update of matched tracks; lost bookkeeping; unmatched unconfirmed tracks marked removed
+  for (int k = tid; k < nt; k += blockDim.x) {
+    const int slot = a.t.order[(size_t)s * T + k];
+    const size_t ts = (size_t)s * T + slot;
+    const int d = trk_det[k];
+    if (d >= 0) {
+      double z[4];
+      measurement(rows + (size_t)d * 518, z);
+      kalman_update(a.t.mean + ts * 8, a.t.cov + ts * 64, a.t.gate_l + ((size_t)b * T + slot) * 16, z);
+      a.t.state[ts] = JDE_TRACK_TRACKED;
+      a.t.since[ts] = 0;
+      a.t.last_det[ts] = d;
+    } else if (pstate[k] == JDE_TRACK_UNCONFIRMED) {
+      a.t.state[ts] = STATE_REMOVED;
+      a.t.last_det[ts] = -1;
+    } else {
+      a.t.state[ts] = JDE_TRACK_LOST;
+      a.t.since[ts] += 1;
+      a.t.last_det[ts] = -1;
+    }
+  }
+  __syncthreads();
+  // gallery update of matched tracks (one warp per track): e <- normalise(m e + (1 - m) d)
+  for (int k = warp; k < nt; k += blockDim.x / 32) {
+    const int d = trk_det[k];
+    if (d < 0) continue;
+    const int slot = a.t.order[(size_t)s * T + k];
+    float* e = a.t.emb + ((size_t)s * T + slot) * 512;
+    const float* dv = rows + (size_t)d * 518 + 6;
+    float vals[16], ss = 0.f;
+    for (int q = 0; q < 16; ++q) {
+      const int c = q * 32 + lane;
+      vals[q] = a.momentum * e[c] + (1.f - a.momentum) * dv[c];
+      ss += vals[q] * vals[q];
+    }
+    for (int off = 16; off > 0; off >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, off);
+    const float inv = ss > 0.f ? 1.f / sqrtf(ss) : 0.f;
+    for (int q = 0; q < 16; ++q) e[q * 32 + lane] = vals[q] * inv;
+  }
+  __syncthreads();
+  // removals, order compaction and births (one thread; O(T + D) integer work)
+  if (tid == 0) {
+    int nn = 0;
+    int top = a.t.free_top[s];
+    for (int k = 0; k < nt; ++k) {
+      const int slot = a.t.order[(size_t)s * T + k];
+      const size_t ts = (size_t)s * T + slot;
+      if (a.t.state[ts] == STATE_REMOVED || (a.t.state[ts] == JDE_TRACK_LOST && a.t.since[ts] > a.lost_max)) {
+        a.t.free_stack[(size_t)s * T + top++] = slot;
+        continue;
+      }
+      new_order[nn++] = slot;
+    }
+    const int born_state = a.t.frames[s] == 0 ? JDE_TRACK_TRACKED : JDE_TRACK_UNCONFIRMED;
+    long long nid = a.t.next_id[s];
+    for (int j = 0; j < D; ++j) {
+      if (det_trk[j] >= 0) continue;
+      if (top == 0 || nn >= T) {
+        flag_error(a.err, KERR_CAPACITY);
+        break;
+      }
+      const int slot = a.t.free_stack[(size_t)s * T + --top];
+      const size_t ts = (size_t)s * T + slot;
+      a.t.id[ts] = nid++;
+      a.t.state[ts] = born_state;
+      a.t.since[ts] = 0;
+      a.t.last_det[ts] = j;
+      det_trk[j] = -2 - slot;   // marks the birth slot for the parallel init below
+      new_order[nn++] = slot;
+    }
+    a.t.next_id[s] = nid;
+    a.t.free_top[s] = top;
+    s_nnew = nn;
+  }
+  __syncthreads();
+  const int nn = s_nnew;
+  for (int k = tid; k < nn; k += blockDim.x) a.t.order[(size_t)s * T + k] = new_order[k];
+  for (int j = tid; j < D; j += blockDim.x) {
+    if (det_trk[j] > -2) continue;
+    const int slot = -2 - det_trk[j];
+    const size_t ts = (size_t)s * T + slot;
+    double z[4];
+    measurement(rows + (size_t)j * 518, z);
+    double* m = a.t.mean + ts * 8;
+    double* P = a.t.cov + ts * 64;
+    for (int i = 0; i < 4; ++i) {
+      m[i] = z[i];
+      m[i + 4] = 0.0;
+    }
+    for (int i = 0; i < 64; ++i) P[i] = 0.0;
+    const double h = z[3];
+    const double sp2 = (2 * SP * h) * (2 * SP * h), sv2 = (10 * SV * h) * (10 * SV * h);
+    P[0] = sp2;
+    P[9] = sp2;
+    P[18] = 1e-2 * 1e-2;
+    P[27] = sp2;
+    P[36] = sv2;
+    P[45] = sv2;
+    P[54] = 1e-5 * 1e-5;
+    P[63] = sv2;
+  }
+  for (int j = warp; j < D; j += blockDim.x / 32) {
+    if (det_trk[j] > -2) continue;
+    const int slot = -2 - det_trk[j];
+    float* e = a.t.emb + ((size_t)s * T + slot) * 512;
+    const float* dv = rows + (size_t)j * 518 + 6;
+    for (int q = 0; q < 16; ++q) e[q * 32 + lane] = dv[q * 32 + lane];
+  }
+  if (tid == 0) {
+    a.t.n_tracks[s] = nn;
+    a.t.frames[s] += 1;
+    a.o_count[b] = nn;
+  }
+  __syncthreads();
   for (int k = tid; k < nn && k < a.o_cap; k += blockDim.x) {
     const int slot = new_order[k];
     const size_t ts = (size_t)s * T + slot;
@@ -549,6 +858,11 @@ size_t assign_smem(const TrackState& t) {
   return sizeof(double) * ASSIGN_COST_CACHE + sizeof(double) * 3 * (MM + 1) + sizeof(int) * 2 * (MM + 1) + sizeof(int) * (2 * t.max_tracks + t.max_dets) +
          (MM + 1) + 16;
 }
+// the cascade adds the stage's row and column lists and the tracks' states before the step
+size_t cascade_smem(const TrackState& t) {
+  const int MM = t.max_tracks > t.max_dets ? t.max_tracks : t.max_dets;
+  return assign_smem(t) + sizeof(int) * (2 * (size_t)MM + t.max_tracks);
+}
 
 bool dalloc(void** p, size_t bytes) {
   if (cudaMalloc(p, bytes ? bytes : 16) != cudaSuccess) {
@@ -567,7 +881,7 @@ size_t track_bytes(const jde_config& cfg) {
   return sizeof(int) * S + sizeof(long long) * S + 2 * sizeof(int) * S * T + sizeof(int) * S +
          sizeof(long long) * S * T + 2 * sizeof(int) * S * T + sizeof(double) * S * T * (8 + 64) +
          sizeof(float) * S * T * 512 + sizeof(int) * S * T + sizeof(double) * B * T * (16 + 4) +
-         sizeof(double) * B * T * D + sizeof(int) * B;
+         sizeof(double) * B * T * D * (cfg.assoc_cascade ? 2 : 1) + sizeof(int) * B + sizeof(int) * S;
 }
 
 int track_alloc(TrackState& t, const jde_config& cfg) {
@@ -583,8 +897,14 @@ int track_alloc(TrackState& t, const jde_config& cfg) {
             dalloc((void**)&t.mean, sizeof(double) * S * T * 8) && dalloc((void**)&t.cov, sizeof(double) * S * T * 64) &&
             dalloc((void**)&t.emb, sizeof(float) * S * T * 512) && dalloc((void**)&t.last_det, sizeof(int) * S * T) &&
             dalloc((void**)&t.gate_l, sizeof(double) * B * T * 16) && dalloc((void**)&t.gate_z, sizeof(double) * B * T * 4) &&
-            dalloc((void**)&t.cost, sizeof(double) * B * T * D) && dalloc((void**)&t.slot_stream, sizeof(int) * B);
+            dalloc((void**)&t.cost, sizeof(double) * B * T * D) && dalloc((void**)&t.slot_stream, sizeof(int) * B) &&
+            dalloc((void**)&t.frames, sizeof(int) * S);
+  t.cascade = cfg.assoc_cascade ? 1 : 0;
+  if (ok && t.cascade) ok = dalloc((void**)&t.cost2, sizeof(double) * B * T * D);
   if (!ok) return 1;
+  if (t.cascade && cudaFuncSetAttribute(assign_cascade_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)cascade_smem(t)) != cudaSuccess)
+    return 1;
   if (cudaFuncSetAttribute(assign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)assign_smem(t)) !=
       cudaSuccess)
     return 1;
@@ -597,7 +917,7 @@ int track_alloc(TrackState& t, const jde_config& cfg) {
 
 void track_free(TrackState& t) {
   void* ptrs[] = {t.n_tracks, t.next_id, t.order, t.free_stack, t.free_top, t.id, t.state, t.since, t.mean, t.cov,
-                  t.emb, t.last_det, t.gate_l, t.gate_z, t.cost, t.slot_stream, t.rows_stage, t.count_stage,
+                  t.emb, t.last_det, t.gate_l, t.gate_z, t.cost, t.cost2, t.frames, t.slot_stream, t.rows_stage, t.count_stage,
                   t.o_id, t.o_box, t.o_state, t.o_det, t.o_count};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -663,6 +983,10 @@ int track_step(TrackState& t, const jde_config& cfg, int n, const int32_t* strea
   a.assign_thresh = cfg.assign_thresh;
   a.lost_max = cfg.lost_max_frames;
   a.momentum = cfg.emb_momentum;
+  a.cascade = t.cascade;
+  a.lam = cfg.motion_lambda;
+  a.iou2 = cfg.iou_cost2;
+  a.iou3 = cfg.iou_cost3;
   a.err = err;
   a.o_cap = out->cap;
   if (out->on_device) {
@@ -699,7 +1023,10 @@ int track_step(TrackState& t, const jde_config& cfg, int n, const int32_t* strea
   jde_count_launch();
   cost_kernel<<<gc, 256, 0, st>>>(a, sl);
   jde_count_launch();
-  assign_kernel<<<n, 256, assign_smem(t), st>>>(a, sl);
+  if (t.cascade)
+    assign_cascade_kernel<<<n, 256, cascade_smem(t), st>>>(a, sl);
+  else
+    assign_kernel<<<n, 256, assign_smem(t), st>>>(a, sl);
   if (cudaGetLastError() != cudaSuccess) {
     snprintf(msg, msg_len, "tracker launch failed");
     return JDE_ERR_CUDA;

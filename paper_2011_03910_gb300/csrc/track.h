@@ -23,10 +23,13 @@ struct TrackState {
   double* cov = nullptr;            // [S][T][64]
   float* emb = nullptr;             // [S][T][512]
   int* last_det = nullptr;          // [S][T]  detection row assigned in the last step, -1 if none
+  int* frames = nullptr;            // [S]     steps since the stream's reset (births on step 0 are confirmed)
   // per call slot scratch (call slot b < max_batch)
   double* gate_l = nullptr;         // [B][T][16]  Cholesky factor of S (row-major 4x4)
   double* gate_z = nullptr;         // [B][T][4]   projected mean H x
-  double* cost = nullptr;           // [B][T*D]    gated cost, rows = min(T, D)
+  double* cost = nullptr;           // [B][T*D]    gated cost, rows = min(T, D); cascade: fused cost [T][D]
+  double* cost2 = nullptr;          // [B][T*D]    cascade: a stage's sub-matrix when it exceeds the shared cache
+  int cascade = 0;                  // three-stage association (jde_config.assoc_cascade)
   int* slot_stream = nullptr;       // [B]
   float* rows_stage = nullptr;      // [B][cap][518] host-provided detections staged on the device
   size_t rows_stage_cap = 0;        // floats rows_stage holds

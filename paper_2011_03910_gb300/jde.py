@@ -20,7 +20,7 @@ lib = C.CDLL(_LIB_PATH)
 
 JDE_OK = 0
 JDE_FP32, JDE_BF16, JDE_FP8_E4M3 = 0, 1, 2
-JDE_TRACK_TRACKED, JDE_TRACK_LOST = 1, 2
+JDE_TRACK_TRACKED, JDE_TRACK_LOST, JDE_TRACK_UNCONFIRMED = 1, 2, 3
 JDE_ROW, JDE_EMB, JDE_NUM_LAYERS = 518, 512, 78
 STATUS = {0: "JDE_OK", 1: "JDE_ERR_INVALID_ARG", 2: "JDE_ERR_OOM", 3: "JDE_ERR_CUDA", 4: "JDE_ERR_CAPACITY",
           5: "JDE_ERR_ADMISSION", 6: "JDE_ERR_TIMEOUT", 7: "JDE_ERR_NOT_FOUND", 8: "JDE_ERR_WEIGHTS",
@@ -33,7 +33,8 @@ class jde_config(C.Structure):
                 ("nms_iou", C.c_float), ("assign_thresh", C.c_float), ("gate_chi2", C.c_double),
                 ("lost_max_frames", C.c_int), ("emb_momentum", C.c_float), ("max_streams", C.c_int),
                 ("max_tracks", C.c_int), ("max_track_dets", C.c_int), ("device", C.c_int),
-                ("keep_layer_outputs", C.c_int), ("sparse_emb", C.c_int)]
+                ("keep_layer_outputs", C.c_int), ("sparse_emb", C.c_int), ("assoc_cascade", C.c_int),
+                ("motion_lambda", C.c_double), ("iou_cost2", C.c_double), ("iou_cost3", C.c_double)]
 
 
 class jde_layer_desc(C.Structure):

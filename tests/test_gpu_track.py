@@ -49,18 +49,23 @@ def tie_in_step(T):
         return False
     near_cost = np.abs(last["gated"] - tk.ASSIGN_THRESH) <= 1e-6 * tk.ASSIGN_THRESH
     near_gate = np.abs(last["d2"] - tk.GATE_CHI2) <= 1e-6 * tk.GATE_CHI2
-    return bool(near_cost.any() or near_gate.any())
+    near_iou = False
+    if "iou" in last:   # the cascade's IoU stages
+        near_iou = any(bool((np.abs(last["iou"] - t) <= 1e-6).any()) for t in (tk.IOU_COST_2, tk.IOU_COST_3))
+    return bool(near_cost.any() or near_gate.any() or near_iou)
 
 
+@pytest.mark.parametrize("cascade", [0, 1])
 @pytest.mark.parametrize("n_obj", [5, 50, 200])
-def test_planted_clip_post_and_track_match_oracle(n_obj):
+def test_planted_clip_post_and_track_match_oracle(n_obj, cascade):
     """60-frame clip at 1088x608 from 1920x1080, constant-velocity objects, sigma 2 px jitter,
-    unit identity embeddings + noise of norm 0.1, 10% occlusions."""
+    unit identity embeddings + noise of norm 0.1, 10% occlusions.  cascade = 0: the single-stage
+    association of Appendix A; 1: the JDE three-stage association (oracle CascadeTracker)."""
     j = jde()
     r, nw, nh, px, py = net.letterbox_geometry(1920, 1080, 1088, 608)
     clip = synth.PlantedClip(3, n_obj, 60, 1088, 608, pp.anchors(), pp.STRIDES, r, px, py)
-    h = make_handle(j.JDE_FP32, max_batch=1, in_w=1088, in_h=608)
-    T = tk.Tracker()
+    h = make_handle(j.JDE_FP32, max_batch=1, in_w=1088, in_h=608, assoc_cascade=cascade)
+    T = tk.CascadeTracker() if cascade else tk.Tracker()
     tb = TrackBufs(1, 1024)
     stream = torch.cuda.current_stream()
     try:
@@ -96,10 +101,10 @@ def det_row(box, emb, conf=0.9):
     return r
 
 
-def run_both(h, frames_rows, stream_id=0):
+def run_both(h, frames_rows, stream_id=0, T=None):
     """Feed identical f32 rows (host buffers) to the GPU tracker and the oracle; compare every step."""
     j = jde()
-    T = tk.Tracker()
+    T = T if T is not None else tk.Tracker()
     tb = TrackBufs(1, 256, on_device=False)
     for rows in frames_rows:
         cap = 64
@@ -157,5 +162,27 @@ def test_streams_are_independent_in_one_call():
                 m = mix.frame(s)
                 assert a[0].tolist() == m[0].tolist() and a[1].tolist() == m[1].tolist()
                 np.testing.assert_array_equal(a[2], m[2])
+    finally:
+        j.jde_destroy(h)
+
+
+def test_cascade_scenarios_match_oracle():
+    """The cascade's scripted cases on the GPU: an appearance change re-matched by IoU, a lost track not
+    re-matched by IoU, unconfirmed births confirmed by IoU >= 0.7 or removed at their first miss."""
+    j = jde()
+    g = np.random.default_rng(31)
+    e1, e2, e3 = g.standard_normal(512), g.standard_normal(512), g.standard_normal(512)
+    frames = [[det_row([100, 100, 140, 220], e1)]]
+    frames += [[det_row([100, 100, 140, 220], e2)]]                                     # IoU stage keeps id 1
+    frames += [[]]                                                                      # id 1 lost
+    frames += [[det_row([100, 100, 140, 220], e3)]]                                     # lost: unconfirmed birth
+    frames += [[det_row([101, 101, 141, 221], e3), det_row([500, 300, 560, 450], e1)]]  # confirmed; new unconfirmed
+    frames += [[det_row([102, 102, 142, 222], e3)]]                                     # unconfirmed removed
+    frames += [[det_row([103, 103, 143, 223], e3), det_row([520, 320, 580, 470], e2)]]
+    frames += [[det_row([104, 104, 144, 224], e3), det_row([521, 321, 581, 471], g.standard_normal(512))]]
+    h = make_handle(j.JDE_FP32, max_batch=4, assoc_cascade=1)
+    try:
+        T = run_both(h, frames, T=tk.CascadeTracker())
+        assert T.next_id >= 4
     finally:
         j.jde_destroy(h)
