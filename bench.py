@@ -291,6 +291,38 @@ def run_fp8(torch, jde, dev, blob, stream, table, B=32, K=20, autotune=True, spa
             "detections_last_batch": n_dets, "launch_count_note": "graph replays; library launches are inside graphs"}
 
 
+def run_sparse_compare(torch, jde, dev, blob, stream, B=16, K=10):
+    """jde_detect_batch on the network's own detections (letterbox, forward, decode, NMS, embeddings) with the
+    dense embedding maps and with the sparse embedding head (tensor-core gathered GEMM at the kept
+    detections): ms per batch of B frames and the detections kept."""
+    import synth
+    frames = torch.from_numpy(synth.frames_uniform(3000, B, SRC_H, SRC_W)).to(dev)
+    out = {}
+    for sparse in (0, 1):
+        cfg = jde.jde_default_config()
+        cfg.max_batch, cfg.max_streams, cfg.device, cfg.sparse_emb = B, 1, dev.index or 0, sparse
+        h = jde.jde_create(cfg, blob)
+        cap = 256
+        rows = torch.zeros((B, cap, 518), dtype=torch.float32, device=dev)
+        count = torch.zeros(B, dtype=torch.int32, device=dev)
+        dets = jde.make_dets(rows, count, None, cap=cap)
+        for _ in range(3):
+            jde.jde_detect_batch(h, frames, B, SRC_W, SRC_H, IN_W, IN_H, dets, True, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            jde.jde_detect_batch(h, frames, B, SRC_W, SRC_H, IN_W, IN_H, dets, True, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        assert jde.jde_kernel_errors(h) == 0
+        out["sparse" if sparse else "dense"] = {"ms_per_batch": e0.elapsed_time(e1) / K,
+                                                "rows_kept": int(torch.clamp(count, max=cap).sum())}
+        jde.jde_destroy(h)
+    out["what"] = (f"jde_detect_batch, BF16 batch {B} at {IN_W}x{IN_H}, the network's own detections (rows capped at "
+                   "256 per frame): dense embedding maps vs the sparse embedding head")
+    return out
+
+
 def run_serving(torch, jde, dev, blob, seconds, budget_gb, n_streams=16, warm_s=2.0):
     """Serving: 16 streams, Poisson arrivals at 30 fps each, input 1088x608 / 864x480 / 576x320 by stream,
     20 + 80u planted objects per stream; continuous batching (paper_2011_03910_gb300.serve)."""
@@ -677,6 +709,10 @@ def main():
         fp32 = {"fps": 1000.0 / ms32, "ms_per_frame": ms32, "steps": n32, "batch": 1, "graph": False}
         jde.jde_destroy(h32)
 
+    sparse_cmp = None
+    if rank == 0 and not args.no_fp8:
+        sparse_cmp = run_sparse_compare(torch, jde, dev, blob, F)
+
     fp8 = None
     if not args.no_fp8 and rank == 0:
         fp8 = run_fp8(torch, jde, dev, blob, F, table, autotune=not args.no_autotune)
@@ -711,6 +747,7 @@ def main():
             "fp32_plain_batch1": fp32,
             "batch_sweep": sweep,
             "fp8_batch32": fp8,
+            "sparse_embedding_head": sparse_cmp,
             "tiles": tiles,
             "serving": serving,
             "roofline": roofline,

@@ -109,14 +109,15 @@ struct EmbSparse {
   const float* bias[3];  // [>= 512]
   const float* mult[3];  // E4M3: input scale x weight scale per channel, else null
   int cin[3];
-  int ldw[3];            // elements per weight row (>= 9 cin)
+  int ldw[3];            // elements per weight row (= 9 cin, a multiple of 64)
   int q[3];
 };
 // es != null: the embedding maps heads[3..5] are not read; the kept detections' embeddings are
-// computed from es (sparse head) into their rows, then normalised.
-void post_launch(const float* const* heads, const HeadGeom& g, float conf_thresh, float nms_iou, PostBufs& b,
-                 float* rows, int32_t* count, int32_t* anchor_index, int cap, int* err, cudaStream_t st,
-                 const EmbSparse* es = nullptr);
+// computed from es (sparse head, tensor cores) into their rows, then normalised.  Returns the launch
+// status (cudaErrorInvalidValue when the sparse head's weight tensor maps cannot be built).
+cudaError_t post_launch(const float* const* heads, const HeadGeom& g, float conf_thresh, float nms_iou, PostBufs& b,
+                        float* rows, int32_t* count, int32_t* anchor_index, int cap, int* err, cudaStream_t st,
+                        const EmbSparse* es = nullptr);
 
 // Loads the fixed scratch array of jde_postprocess_noalloc onto the current device and records its
 // address; 0 on success, else 1 with a reason in msg.

@@ -1092,9 +1092,8 @@ jde_status jde_postprocess(jde_handle* h, const float* const* heads, int n, int 
       es.q[s] = lw.q;
     }
   }
-  post_launch(hp, g, h->cfg.conf_thresh, h->cfg.nms_iou, h->pb, rows, count, aidx, out->cap, h->d_err, st,
-              sparse ? &es : nullptr);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = post_launch(hp, g, h->cfg.conf_thresh, h->cfg.nms_iou, h->pb, rows, count, aidx, out->cap,
+                              h->d_err, st, sparse ? &es : nullptr);
   if (e != cudaSuccess) return fail(h, JDE_ERR_CUDA, "post-processing launch: %s", cudaGetErrorString(e));
   if (!out->on_device) {
     CUDA_OR(h, cudaMemcpyAsync(out->count, count, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));

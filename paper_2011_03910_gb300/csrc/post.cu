@@ -263,7 +263,7 @@ __global__ void emit_kernel(const float* e0, const float* e1, const float* e2, H
   locate(g, gi, s, a, y, x);
   float* row = rows + ((size_t)n * cap + r) * 518;
   const int ep = g.epad;
-  // sparse head (e0 null): the raw embedding was written into the row by emb_gemm_kernel
+  // sparse head (e0 null): the raw embedding was written into the row by emb_tc_kernel
   const float* e = e0 == nullptr ? row + 6
                                  : (s == 0 ? e0 : (s == 1 ? e1 : e2)) +
                                        ((size_t)(n * (g.gh[s] + 2 * ep) + y + ep) * (g.gw[s] + 2 * ep) + x + ep) * 512;
@@ -313,121 +313,216 @@ __global__ void emb_list_kernel(HeadGeom g, const uint64_t* sorted, const int* k
 
 __device__ __forceinline__ float e4m3_value(uint8_t code) { return e4m3x2_to_float2((uint32_t)code).x; }
 
-// Sparse embedding head, step 2: for the listed detections of scale blockIdx.z, out[o] = sum_k
-// W[o][k] x[k] over K = (tap, channel) of the 3x3 input patch around (y, x), times the E4M3
-// dequantisation multiplier, plus the bias; the raw (unnormalised) values go into the detection's
-// row.  Tiles of 64 detections x 128 outputs (8 x 4 per thread), fp32 accumulation, K in chunks
-// of 32 channels of one tap, operands read with 16-byte loads.
-constexpr int EG_D = 64, EG_O = 128, EG_K = 32;
-// 16 bytes -> 8 bf16 values, or 16 E4M3 codes (Q)
+// Sparse embedding head, step 2 (tensor cores): for the listed detections of scale blockIdx.z,
+// out[o] = sum_k W[o][k] x[k] over K = (tap, channel) of the 3x3 input patch around (y, x), times the
+// E4M3 dequantisation multiplier, plus the bias; the raw (unnormalised) values go into the
+// detection's row.  One CTA computes 128 detections x 256 outputs (blockIdx.y: which half of 512):
+//   * warps 0..3 gather, per k-block (one 128-byte slice of one tap: 64 bf16 or 128 E4M3 channels),
+//     each detection's input row into a 128-byte-swizzled A tile; warp 0 / lane 0 loads the weight
+//     tile (256 output rows x 128 bytes) with TMA; a 4-deep ring;
+//   * warp 4 / lane 0 issues tcgen05.mma (M = 128, N = 256, K = 16 bf16 or 32 E4M3) into a TMEM
+//     accumulator and frees ring slots with tcgen05.commit;
+//   * warps 4..7 read the accumulator rows (TMEM lane = detection) and write the row values.
+// Waits are bounded; on a timeout the CTA flags the error word and stops.
+constexpr int EMB_M = 128, EMB_N = 256, EMB_STAGES = 4;
+constexpr int EMB_A_BYTES = EMB_M * 128, EMB_B_BYTES = EMB_N * 128;
+constexpr int EMB_SMEM = EMB_STAGES * (EMB_A_BYTES + EMB_B_BYTES) + 1024 + 256;
+
+struct EmbMaps {
+  alignas(64) CUtensorMap w[3];   // weights [512][K] of each scale, boxes {128 bytes of K, 256 rows}
+};
+struct EmbArgs {
+  EmbSparse es;
+  const int4* list;
+  const int* count;
+  int list_stride;
+  float* rows;
+  int cap;
+  int* err;
+};
+
 template <int Q>
-__device__ __forceinline__ void unpack16b(const uint4 v, float (&out)[16]) {
-  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-  if (Q) {
+__global__ void __launch_bounds__(256, 1) emb_tc_kernel(const __grid_constant__ EmbMaps maps, const EmbArgs a) {
+  const int sc = blockIdx.z, n0 = blockIdx.y * EMB_N, d0 = blockIdx.x * EMB_M;
+  const int total = a.count[sc];
+  if (d0 >= total) return;   // the whole CTA
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ int s_abort;
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + EMB_STAGES * EMB_A_BYTES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + EMB_STAGES * (EMB_A_BYTES + EMB_B_BYTES));
+  uint64_t* empty = full + EMB_STAGES;
+  uint64_t* acc_full = empty + EMB_STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const TView in = a.es.in[sc];
+  const int cin = a.es.cin[sc];
+  constexpr int KEL = Q ? 128 : 64;          // elements of one 128-byte k-block
+  constexpr int ES = Q ? 1 : 2;              // bytes per element
+  const int nkb = 9 * cin / KEL;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < EMB_STAGES; ++i) {
+      mbar_init(&full[i], 5);                // four gather warps + the weight load
+      mbar_init(&empty[i], 1);
+    }
+    mbar_init(acc_full, 1);
+    fence_barrier_init();
+    s_abort = 0;
+  }
+  if (warp == 4) tmem_alloc(tmem_slot, EMB_N);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp < 4) {
+    // ---------------- gather: detection row t of the tile, one 128-byte k-block slice per stage
+    const int t = threadIdx.x;
+    const int det = d0 + t;
+    int4 e = make_int4(-1, 0, 0, 0);
+    if (det < total) e = a.list[(size_t)sc * a.list_stride + det];
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int st = kb % EMB_STAGES;
+      bool ok = true;
+      if (lane == 0 && kb >= EMB_STAGES) ok = mbar_wait(&empty[st], ((kb / EMB_STAGES) - 1) & 1);
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (!ok || *((volatile int*)&s_abort)) {
+        if (lane == 0) {
+          flag_error(a.err, KERR_TIMEOUT);
+          atomicExch(&s_abort, 1);
+        }
+        break;
+      }
+      if (threadIdx.x == 0) {
+        mbar_expect_tx(&full[st], EMB_B_BYTES);
+        tma_load_2d(sB + st * EMB_B_BYTES, &maps.w[sc], &full[st], kb * KEL, n0);
+      }
+      const int k0 = kb * KEL, tap = k0 / cin, c0 = k0 - tap * cin;
+      uint4 v[8];
+      if (e.x >= 0) {
+        const uint8_t* src = static_cast<const uint8_t*>(in.ptr) +
+                             (tview_off(in, e.x, e.z + tap / 3 - 1, e.w + tap % 3 - 1) + c0) * ES;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const float2 lo = e4m3x2_to_float2(w[i] & 0xFFFFu), hi = e4m3x2_to_float2(w[i] >> 16);
-      out[4 * i] = lo.x;
-      out[4 * i + 1] = lo.y;
-      out[4 * i + 2] = hi.x;
-      out[4 * i + 3] = hi.y;
+        for (int u = 0; u < 8; ++u) v[u] = __ldg(reinterpret_cast<const uint4*>(src) + u);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = make_uint4(0u, 0u, 0u, 0u);
+      }
+      uint8_t* dst = sA + st * EMB_A_BYTES + t * 128;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) *reinterpret_cast<uint4*>(dst + ((u ^ (t & 7)) << 4)) = v[u];
+      fence_proxy_async();                   // generic-proxy writes -> visible to the MMAs
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&full[st]);
     }
   } else {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[i]));
-      out[2 * i] = f.x;
-      out[2 * i + 1] = f.y;
-    }
-  }
-}
-template <int Q>
-__global__ void __launch_bounds__(256) emb_gemm_kernel(EmbSparse es, const int4* list, const int* count, int list_stride,
-                                                       float* rows, int cap) {
-  const int s = blockIdx.z;
-  const int o0 = blockIdx.y * EG_O;
-  const int total = count[s];
-  const TView in = es.in[s];
-  const int cin = es.cin[s], K = 9 * cin, ldw = es.ldw[s];
-  constexpr int es_b = Q ? 1 : 2;             // bytes per element
-  constexpr int vec = 16 / es_b;              // elements per 16-byte load
-  __shared__ __align__(16) float As[EG_K][EG_D + 4];
-  __shared__ __align__(16) float Bs[EG_K][EG_O + 4];
-  __shared__ int4 ent[EG_D];
-  const int t = threadIdx.x;
-  const int td = (t / 32) * 8;                // 8 detections
-  const int to = (t % 32) * 4;                // 4 outputs
-  for (int d0 = blockIdx.x * EG_D; d0 < total; d0 += gridDim.x * EG_D) {
-    __syncthreads();
-    if (t < EG_D) ent[t] = d0 + t < total ? list[(size_t)s * list_stride + d0 + t] : make_int4(-1, -1, 0, 0);
-    __syncthreads();
-    float acc[8][4] = {};
-    for (int k0 = 0; k0 < K; k0 += EG_K) {
-      const int tap = k0 / cin, c0 = k0 % cin;
-      const int ky = tap / 3, kx = tap % 3;
-      // A: 64 detections x 32 channels of one tap
-      for (int i = t; i < EG_D * (EG_K / vec); i += 256) {
-        const int d = i / (EG_K / vec), part = i % (EG_K / vec);
-        const int4 e = ent[d];
-        float v[16];
-        if (e.x >= 0) {
-          const size_t off = tview_off(in, e.x, e.z + ky - 1, e.w + kx - 1) + c0 + part * vec;
-          unpack16b<Q>(__ldg(reinterpret_cast<const uint4*>(static_cast<const uint8_t*>(in.ptr) + off * es_b)), v);
-        } else {
-#pragma unroll
-          for (int j = 0; j < 16; ++j) v[j] = 0.f;
+    if (warp == 4 && lane == 0) {
+      // ---------------- MMA issuer
+      constexpr uint32_t idesc = Q ? idesc_e4m3(EMB_M, EMB_N) : idesc_bf16(EMB_M, EMB_N);
+      const uint64_t a0 = smem_desc(smem_u32(sA), 1024, 2u);   // 128-byte rows, 128-byte swizzle
+      const uint64_t b0 = smem_desc(smem_u32(sB), 1024, 2u);
+      bool ok = true;
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int st = kb % EMB_STAGES;
+        if (!mbar_wait(&full[st], (kb / EMB_STAGES) & 1)) {
+          ok = false;
+          break;
         }
+        tc_fence_after();
+        const uint64_t ad = desc_add(a0, (uint32_t)(st * EMB_A_BYTES) >> 4);
+        const uint64_t bd = desc_add(b0, (uint32_t)(st * EMB_B_BYTES) >> 4);
 #pragma unroll
-        for (int j = 0; j < vec; ++j) As[part * vec + j][d] = v[j];
+        for (int kk = 0; kk < 4; ++kk) {     // 32 bytes of K per MMA
+          if (Q)
+            umma_e4m3(tmem, desc_add(ad, 2 * kk), desc_add(bd, 2 * kk), idesc, (kb | kk) != 0 ? 1u : 0u);
+          else
+            umma_bf16(tmem, desc_add(ad, 2 * kk), desc_add(bd, 2 * kk), idesc, (kb | kk) != 0 ? 1u : 0u);
+        }
+        umma_commit(&empty[st]);
       }
-      // B: 128 outputs x 32 K
-      for (int i = t; i < EG_O * (EG_K / vec); i += 256) {
-        const int o = i / (EG_K / vec), part = i % (EG_K / vec);
-        const size_t off = (size_t)(o0 + o) * ldw + k0 + part * vec;
-        float v[16];
-        unpack16b<Q>(__ldg(reinterpret_cast<const uint4*>(static_cast<const uint8_t*>(es.w[s]) + off * es_b)), v);
-#pragma unroll
-        for (int j = 0; j < vec; ++j) Bs[part * vec + j][o] = v[j];
+      umma_commit(acc_full);
+      if (!ok) {
+        flag_error(a.err, KERR_TIMEOUT);
+        atomicExch(&s_abort, 1);
       }
-      __syncthreads();
-#pragma unroll 4
-      for (int kk = 0; kk < EG_K; ++kk) {
-        const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][td]);
-        const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][td + 4]);
-        const float4 b = *reinterpret_cast<const float4*>(&Bs[kk][to]);
-        const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-        const float bb[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], bb[j], acc[i][j]);
-      }
-      __syncthreads();
     }
+    // ---------------- epilogue: TMEM lane = detection row of the tile
+    __syncwarp();
+    const int quarter = warp & 3;
+    const int t = quarter * 32 + lane;
+    const int det = d0 + t;
+    bool ok = lane == 0 ? mbar_wait(acc_full, 0) : true;
+    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+    if (!ok && lane == 0) flag_error(a.err, KERR_TIMEOUT);
+    tc_fence_after();
+    float* row = nullptr;
+    if (det < total && ok && !*((volatile int*)&s_abort)) {
+      const int4 e = a.list[(size_t)sc * a.list_stride + det];
+      row = a.rows + ((size_t)e.x * a.cap + e.y) * 518 + 6 + n0;
+    }
+#pragma unroll 1
+    for (int c0 = 0; c0 < EMB_N; c0 += 32) {
+      uint32_t r[32];
+      tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, r);
+      tmem_ld_wait();
+      if (row) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int4 e = ent[td + i];
-      if (e.x < 0) continue;
-      float* row = rows + ((size_t)e.x * cap + e.y) * 518 + 6;
-      float v[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int o = o0 + to + j;
-        v[j] = acc[i][j] * (Q ? es.mult[s][o] : 1.f) + es.bias[s][o];
+        for (int j = 0; j < 32; j += 2) {
+          const int o = n0 + c0 + j;
+          float v0 = __uint_as_float(r[j]), v1 = __uint_as_float(r[j + 1]);
+          if (Q) {
+            v0 *= a.es.mult[sc][o];
+            v1 *= a.es.mult[sc][o + 1];
+          }
+          // rows are 518 floats: 8-byte aligned only
+          reinterpret_cast<float2*>(row + c0 + j)[0] = make_float2(v0 + a.es.bias[sc][o], v1 + a.es.bias[sc][o + 1]);
+        }
       }
-      // rows are 518 floats: 8-byte aligned only
-      reinterpret_cast<float2*>(row + o0 + to)[0] = make_float2(v[0], v[1]);
-      reinterpret_cast<float2*>(row + o0 + to)[1] = make_float2(v[2], v[3]);
     }
   }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 4) tmem_dealloc(tmem, EMB_N);
+}
+
+typedef CUresult (*EmbEncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// Weight tensor maps of the three scales; false if the driver entry point or an encoding fails.
+bool emb_maps(const EmbSparse& es, EmbMaps& m) {
+  static EmbEncodeFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EmbEncodeFn>(p);
+  });
+  if (!fn) return false;
+  for (int sc = 0; sc < 3; ++sc) {
+    const int es_b = es.q[sc] ? 1 : 2;
+    const cuuint64_t K = (cuuint64_t)es.ldw[sc];
+    cuuint64_t dims[2] = {K, 512};
+    cuuint64_t strides[1] = {K * es_b};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / es_b), EMB_N};
+    cuuint32_t el[2] = {1, 1};
+    if (fn(&m.w[sc], es.q[sc] ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+           const_cast<void*>(es.w[sc]), dims, strides, box, el, CU_TENSOR_MAP_INTERLEAVE_NONE,
+           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  return true;
 }
 
 }  // namespace
 
-void post_launch(const float* const* heads, const HeadGeom& g, float conf_thresh, float nms_iou, PostBufs& b,
-                 float* rows, int32_t* count, int32_t* anchor_index, int cap, int* err, cudaStream_t st,
-                 const EmbSparse* es) {
-  (void)err;
+cudaError_t post_launch(const float* const* heads, const HeadGeom& g, float conf_thresh, float nms_iou, PostBufs& b,
+                        float* rows, int32_t* count, int32_t* anchor_index, int cap, int* err, cudaStream_t st,
+                        const EmbSparse* es) {
   {
     // the kernel's dynamic shared-memory limit is a per-device attribute: set it once per device
     static std::mutex mu;
@@ -465,17 +560,45 @@ void post_launch(const float* const* heads, const HeadGeom& g, float conf_thresh
     jde_count_launch();
     emb_list_kernel<<<n, 256, 0, st>>>(g, b.sorted, b.keep_idx, b.n_keep, b.kmax, cap, b.emb_list, b.emb_count);
     const int per = n * (cap < b.kmax ? cap : b.kmax);   // most detections of one scale
-    int gx = (per + EG_D - 1) / EG_D;
-    if (gx > 64) gx = 64;
-    jde_count_launch();
-    // the three heads of a handle are all BF16 or all E4M3
-    if (es->q[0])
-      emb_gemm_kernel<1><<<dim3(gx, 512 / EG_O, 3), 256, 0, st>>>(*es, b.emb_list, b.emb_count, n * b.kmax, rows, cap);
-    else
-      emb_gemm_kernel<0><<<dim3(gx, 512 / EG_O, 3), 256, 0, st>>>(*es, b.emb_list, b.emb_count, n * b.kmax, rows, cap);
+    const int gx = (per + EMB_M - 1) / EMB_M;
+    EmbMaps maps;
+    EmbArgs ea;
+    ea.es = *es;
+    ea.list = b.emb_list;
+    ea.count = b.emb_count;
+    ea.list_stride = n * b.kmax;
+    ea.rows = rows;
+    ea.cap = cap;
+    ea.err = err;
+    if (emb_maps(*es, maps)) {
+      {
+        // dynamic shared-memory limit of the two instantiations, once per device
+        static std::mutex mu;
+        static bool attr[JDE_MAX_DEVICES] = {false};
+        int dev = -1;
+        if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < JDE_MAX_DEVICES) {
+          std::lock_guard<std::mutex> lock(mu);
+          if (!attr[dev] &&
+              cudaFuncSetAttribute(emb_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, EMB_SMEM) ==
+                  cudaSuccess &&
+              cudaFuncSetAttribute(emb_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, EMB_SMEM) ==
+                  cudaSuccess)
+            attr[dev] = true;
+        }
+      }
+      jde_count_launch();
+      // the three heads of a handle are all BF16 or all E4M3
+      if (es->q[0])
+        emb_tc_kernel<1><<<dim3(gx, 512 / EMB_N, 3), 256, EMB_SMEM, st>>>(maps, ea);
+      else
+        emb_tc_kernel<0><<<dim3(gx, 512 / EMB_N, 3), 256, EMB_SMEM, st>>>(maps, ea);
+    } else {
+      return cudaErrorInvalidValue;   // the weight tensor maps could not be built
+    }
   }
   dim3 ge((b.kmax + 3) / 4, n);
   jde_count_launch();
   emit_kernel<<<ge, 128, 0, st>>>(es ? nullptr : heads[3], heads[4], heads[5], g, b.sorted, b.boxes, b.conf, b.cls,
                                   b.keep_idx, b.n_keep, b.kmax, rows, count, anchor_index, cap);
+  return cudaGetLastError();
 }

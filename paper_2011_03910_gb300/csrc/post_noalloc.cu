@@ -178,9 +178,8 @@ extern "C" jde_status jde_postprocess_noalloc(const float* const* heads, int n, 
   b.keep_idx = reinterpret_cast<int*>(s + o_keep);
   b.n_keep = reinterpret_cast<int*>(s + o_nkeep);
   b.kmax = max_cand;
-  post_launch(heads, g, conf_thresh, nms_iou, b, out->rows, out->count, out->anchor_index, out->cap, nullptr,
-              static_cast<cudaStream_t>(stream));
-  const cudaError_t e = cudaGetLastError();
+  const cudaError_t e = post_launch(heads, g, conf_thresh, nms_iou, b, out->rows, out->count, out->anchor_index,
+                                    out->cap, nullptr, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) {
     snprintf(buf, sizeof(buf), "jde_postprocess_noalloc: launch failed: %s", cudaGetErrorString(e));
     say(err_msg, err_len, buf);
