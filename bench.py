@@ -325,35 +325,50 @@ def run_sparse_compare(torch, jde, dev, blob, stream, B=16, K=10):
 
 def run_serving(torch, jde, dev, blob, seconds, budget_gb, n_streams=16, warm_s=2.0):
     """Serving: 16 streams, Poisson arrivals at 30 fps each, input 1088x608 / 864x480 / 576x320 by stream,
-    20 + 80u planted objects per stream; continuous batching (paper_2011_03910_gb300.serve)."""
+    20 + 80u planted objects per stream; the library's native server (jde_server_*: admission by budget,
+    continuous batching per input size, CUDA-graph replays) driven by paper_2011_03910_gb300.serve."""
     import synth
     from paper_2011_03910_gb300 import serve
     sizes = [(1088, 608), (864, 480), (576, 320)]
     g = np.random.Generator(np.random.PCG64(4))
     specs = [serve.StreamSpec(i, *sizes[i % 3], fps=30.0, n_objects=int(20 + 80 * g.uniform()), seed=4000 + i)
              for i in range(n_streams)]
-    srv = serve.Server(jde, torch, dev, blob, budget_bytes=int(budget_gb * 1e9))
+    srv = serve.Server(jde, torch, dev, blob, budget_bytes=int(budget_gb * 1e9), caller_heads=True)
     total_s = seconds + warm_s
+    T = 150
     for sp in specs:
         fr = torch.from_numpy(synth.frames_uniform(5000 + sp.stream_id, 4, SRC_H, SRC_W)).to(dev)
-        srv.open_stream(sp, [fr[k] for k in range(4)])
-    reqs = serve.poisson_arrivals([sp for sp in specs if sp.stream_id in srv.group_of], total_s, seed=4)
+        r, px, py = serve.letterbox_geometry(SRC_W, SRC_H, sp.in_w, sp.in_h)
+        clip = synth.PlantedClip(100 + sp.seed, sp.n_objects, T, sp.in_w, sp.in_h, serve.anchor_table(),
+                                 serve.STRIDES, r, px, py, max_speed=min(3.0, 600.0 / (T - 1)))
+        srv.open_stream(sp, [fr[k] for k in range(4)], heads=synth.PlantedHeadFrames(clip))
+    reqs = serve.poisson_arrivals([sp for sp in specs if sp.stream_id in srv.streams], total_s, seed=4)
+    # the planted entries of every frame are built before the clock starts
+    for sp in specs:
+        if sp.stream_id in srv.streams:
+            for t in range(T):
+                srv.streams[sp.stream_id].heads.entries(t)
     l0 = jde.jde_launch_count()
     stats = srv.run(reqs, warm_s=warm_s)
-    stats.update({"streams": n_streams, "admitted": len(srv.group_of), "refused": list(srv.refused),
-                  "offered_fps": 30.0 * len(srv.group_of), "seconds": seconds, "warmup_s": warm_s,
+    charged, held = srv.device_bytes()
+    stats.update({"streams": n_streams, "admitted": len(srv.streams), "refused": list(srv.refused),
+                  "offered_fps": 30.0 * len(srv.streams), "seconds": seconds, "warmup_s": warm_s,
                   "inputs": {f"{w}x{h}": sum(1 for sp in specs if (sp.in_w, sp.in_h) == (w, h)) for w, h in sizes},
-                  "device_bytes": srv.device_bytes(), "budget_bytes": srv.ledger.budget,
-                  "gpu_launches": int(jde.jde_launch_count() - l0),
-                  "what": "latency per frame: device time its tracker step finished minus its Poisson arrival; "
-                          "fps = frames served / time from the end of warm-up to the last frame's completion"})
+                  "device_bytes_charged": charged, "device_bytes_held": held, "budget_bytes": srv.budget,
+                  "host_launches": int(jde.jde_launch_count() - l0), "server": srv.stats(),
+                  "what": "latency per frame: device time its batch finished minus its Poisson arrival; "
+                          "fps = frames served / time from the end of warm-up to the last frame's completion; "
+                          "host_launches counts kernels launched eagerly (graph replays launch theirs from "
+                          "the graph)"})
     # capacity: the same streams with every frame released at once (batches fill to max_batch per size)
-    sat = [serve.Request(0.0, sp.stream_id, k) for k in range(60) for sp in specs if sp.stream_id in srv.group_of]
+    sat = [serve.Request(0.0, sp.stream_id, k) for k in range(60) for sp in specs if sp.stream_id in srv.streams]
     st2 = srv.run(sat, realtime=False)
     stats["saturated_fps"] = st2["fps"]
+    stats["server_after_saturation"] = srv.stats()
     for sp in specs:
-        if sp.stream_id in srv.group_of:
+        if sp.stream_id in srv.streams:
             srv.close_stream(sp.stream_id)
+    srv.close()
     return stats
 
 

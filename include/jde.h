@@ -312,6 +312,120 @@ jde_status jde_postprocess_noalloc(const float* const* heads, int n, int in_w, i
                                    float conf_thresh, float nms_iou, int max_cand, jde_dets* out, void* stream,
                                    char* err_msg, size_t err_len);
 
+/* ---------------------------------------------------------------------------------------------
+ * Serving many video streams in one process (the paper's capture -> prediction -> post-processing
+ * pipeline of Sec. 4.3-4.4, Fig. 4, generalised from one video to many).
+ *
+ * A server groups streams by model input size.  A group owns one handle (created from
+ * cfg.group with max_in_w/h = the group's size, max_src_w/h = src_w/h, max_streams =
+ * max_streams_per_group), one CUDA stream and its batch buffers.  jde_stream_open admits a stream
+ * into the group of its size when that group has a free tracker slot, or creates the group when
+ * jde_estimate_device_bytes of its handle plus its batch buffers fits in what hbm_budget_bytes has
+ * left (else JDE_ERR_ADMISSION, nothing allocated).  jde_submit queues one frame of a stream;
+ * jde_poll, which never blocks, collects finished batches and starts, in every group with no batch on
+ * the device, a batch of the queued frames (at most max_batch, at most one per stream, oldest first).
+ * A batch is forward + post-processing + tracker step of its frames on the group's stream.  With
+ * use_graphs the launch sequence of a batch of n frames is captured into a CUDA graph the second
+ * time a batch of n frames starts in that group (the first runs eagerly and sets everything up)
+ * and replayed from then on.  The server is not thread-safe: one host thread drives it.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct jde_server jde_server;
+
+typedef struct {
+  jde_config group;          /* template of each group's handle (precision, max_batch = frames per batch,
+                                thresholds, tracker options, device); sizes are set per group as above.
+                                With caller_heads the handles compute the embedding heads densely
+                                (sparse_emb forced to 0), so the forward does all of its work. */
+  int src_w, src_h;          /* size of every stream's frames (uint8 RGB, HWC, rows tightly packed) */
+  int max_streams_per_group; /* tracker slots of a group, 1..1024 */
+  size_t hbm_budget_bytes;   /* device bytes the groups may be charged in total */
+  int det_cap;               /* detection rows kept per frame (jde_dets.cap of the groups) */
+  int track_cap;             /* tracks reported per frame (jde_tracks.cap) */
+  int caller_heads;          /* 1: every frame is submitted with its six head tensors (layout of
+                                jde_postprocess), which the post-processing reads instead of the
+                                network's; 0: the network's own heads */
+  int collect_net_heads;     /* 1: the network's three detection maps of each frame are kept and can be
+                                returned through jde_frame_out.net_det */
+  int use_graphs;            /* 1: replay each batch size's launch sequence as a CUDA graph */
+} jde_server_config;
+
+/* Host buffers a frame's results are written to when jde_poll returns it (each optional, NULL to
+ * skip; they must stay valid until then).  Track arrays hold track_cap entries, rows det_cap rows
+ * of JDE_ROW values, net_det[k] the [H_k][W_k][24] f32 detection map of stride 32, 16, 8 (needs
+ * collect_net_heads). */
+typedef struct {
+  int64_t* track_id;
+  float* track_box;     /* [track_cap][4] */
+  int32_t* track_state; /* JDE_TRACK_* */
+  int32_t* track_det;   /* row of the frame's detection assigned to the track, or -1 */
+  float* rows;          /* [det_cap][518] as jde_postprocess writes them */
+  float* net_det[3];
+} jde_frame_out;
+
+typedef struct {
+  long long ticket;   /* as returned by jde_submit */
+  int stream_id;
+  int n_dets;         /* detections kept (rows beyond det_cap were not written) */
+  int n_tracks;       /* tracks alive after the step (beyond track_cap not reported) */
+  int errors;         /* kernel error word of the frame's batch (jde_kernel_errors), 0 if none */
+  float done_ms;      /* device time at which the frame's batch finished, ms after the server's clock
+                         start (jde_server_create or jde_server_reset_clock) */
+} jde_frame_result;
+
+/* Fill *cfg with defaults: jde_default_config for the groups, 1920x1080 sources, 16 streams per group,
+ * budget 64 GiB, det_cap 256, track_cap 256, network heads, no collection, graphs on. */
+void jde_default_server_config(jde_server_config* cfg);
+
+/* Create a server (no device memory until a stream is opened).  `weights` is the blob of
+ * jde_create, copied.  Errors: JDE_ERR_INVALID_ARG, JDE_ERR_CUDA. */
+jde_status jde_server_create(const jde_server_config* cfg, const void* weights, size_t nbytes, jde_server** out);
+
+/* Wait for the device work of every group, then release everything.  NULL is a no-op. */
+void jde_server_destroy(jde_server* s);
+
+/* Message of the last failed call on s. */
+const char* jde_server_last_error(jde_server* s);
+
+/* Restart the clock of done_ms: records the start event and waits for it. */
+jde_status jde_server_reset_clock(jde_server* s);
+
+/* Admit a stream with model input size in_w x in_h (multiples of 32); its tracker slot starts empty.
+ * *stream_id receives its id (ids are never reused).  JDE_ERR_ADMISSION when neither a free slot
+ * nor the budget allows it; JDE_ERR_OOM / JDE_ERR_WEIGHTS / JDE_ERR_CUDA from creating a group. */
+jde_status jde_stream_open(jde_server* s, int in_w, int in_h, int* stream_id);
+
+/* Finish the stream's submitted frames (their results stay queued for jde_poll), free its slot, and
+ * destroy its group, returning the group's charge to the budget, when no stream is left in it.
+ * JDE_ERR_NOT_FOUND for an unknown id. */
+jde_status jde_stream_close(jde_server* s, int stream_id);
+
+/* Queue one frame of a stream.  `frame` (device, src_h x src_w x 3 uint8) and, with caller_heads,
+ * heads[0..5] (device) must stay unchanged until the frame's result is returned by jde_poll; `out`
+ * (copied) names host buffers for its results, or NULL.  *ticket (optional) receives the frame's
+ * ticket, increasing from 1.  Frames of a stream are processed in submission order. */
+jde_status jde_submit(jde_server* s, int stream_id, const uint8_t* frame, const float* const* heads,
+                      const jde_frame_out* out, long long* ticket);
+
+/* Advance the server without blocking (see above) and move up to cap results of finished frames
+ * into results[0..*n), in completion order.  A failed launch or batch returns its status (the
+ * message in jde_server_last_error). */
+jde_status jde_poll(jde_server* s, jde_frame_result* results, int cap, int* n);
+
+/* Device bytes a group of in_w x in_h is charged at creation: jde_estimate_device_bytes of its handle's
+ * configuration plus its batch buffers (frames, caller heads, detection rows, track outputs, the
+ * network's detection maps when collected, stream slots).  Pure host arithmetic; needs no GPU. */
+jde_status jde_server_group_cost(const jde_server_config* cfg, int in_w, int in_h, size_t* out);
+
+/* Block until every submitted frame has finished (results stay queued for jde_poll). */
+jde_status jde_server_flush(jde_server* s);
+
+/* *charged: bytes charged to the budget by the open groups; *held: device bytes their handles hold
+ * (jde_device_bytes) plus their batch buffers.  Either pointer may be NULL. */
+jde_status jde_server_device_bytes(jde_server* s, size_t* charged, size_t* held);
+
+/* Counters of the server: batches launched eagerly, graphs captured, graph replays. */
+jde_status jde_server_stats(jde_server* s, long long* eager, long long* captured, long long* replays);
+
 #ifdef __cplusplus
 }
 #endif

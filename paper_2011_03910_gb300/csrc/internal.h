@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/jde.h"
 #include "common.cuh"
 
 // One convolution launch: out = act(conv(in, W) + bias) (+ res), optionally
@@ -136,3 +137,9 @@ StemS2Plan* stem_s2_plan_new(const TView& lb, const TView& out, const void* w0b,
                              int* err, char* msg, size_t msg_len);
 void stem_s2_plan_free(StemS2Plan* p);
 cudaError_t stem_s2_launch(const StemS2Plan* p, cudaStream_t st);
+
+// jde_track_step whose kernels read the call's stream slots from dev_slots (device, n entries, the same
+// values as stream_ids) instead of kernel arguments, so that a captured CUDA graph of the step serves
+// any batch of n streams after the caller rewrites dev_slots.
+jde_status track_step_device_slots(jde_handle* h, int n, const int32_t* stream_ids, const int* dev_slots,
+                                   const jde_dets* dets, jde_tracks* out, cudaStream_t st);

@@ -717,8 +717,11 @@ void geometry(int src_w, int src_h, int in_w, int in_h, double& r, int& nw, int&
   py = (in_h - nh) / 2;
 }
 
+// The post-processing scratch is allocated once, for max_batch frames, at the first call: it never moves
+// afterwards, so a CUDA graph that captured a post-processing launch stays valid for any later batch size.
 jde_status ensure_post(jde_handle* h, int n) {
   if (h->pb_n >= n && h->pb.cand_keys) return JDE_OK;
+  n = h->cfg.max_batch;
   PostBufs& b = h->pb;
   void* ptrs[] = {b.cand_keys, b.cand_count, b.sorted, b.n_sorted, b.boxes, b.conf, b.cls, b.mask, b.keep_idx,
                   b.n_keep, b.emb_list, b.emb_count};
@@ -1355,6 +1358,21 @@ jde_status jde_track_step(jde_handle* h, int n, const int32_t* stream_ids, const
   if (r != JDE_OK) return fail(h, (jde_status)r, "jde_track_step: %s", msg);
   return JDE_OK;
 }
+
+}  // extern "C"
+
+jde_status track_step_device_slots(jde_handle* h, int n, const int32_t* stream_ids, const int* dev_slots,
+                                   const jde_dets* dets, jde_tracks* out, cudaStream_t st) {
+  if (!h || !dev_slots) return fail(h, JDE_ERR_INVALID_ARG, "track_step_device_slots: NULL argument");
+  if (!dets->on_device || !out->on_device)
+    return fail(h, JDE_ERR_INVALID_ARG, "track_step_device_slots: detections and tracks must be on the device");
+  char msg[256] = {0};
+  const int r = track_step(h->trk, h->cfg, n, stream_ids, dets, out, h->d_err, st, msg, sizeof(msg), dev_slots);
+  if (r != JDE_OK) return fail(h, (jde_status)r, "jde_track_step: %s", msg);
+  return JDE_OK;
+}
+
+extern "C" {
 
 unsigned long long jde_launch_count(void) { return g_launches.load(); }
 

@@ -53,6 +53,7 @@ struct StepArgs {
   float assign_thresh;
   int lost_max;
   float momentum;
+  const int* dslots;      // device stream slots of the call (graph replays), else null: the by-value slots
   int cascade;            // three-stage association
   double lam, iou2, iou3; // cascade: appearance weight of stage 1, rejection thresholds of stages 2 and 3
   int* err;
@@ -97,7 +98,7 @@ __global__ void reset_kernel(TrackState t, int s) {
 // ---------------------------------------------------------------- predict + gating factors
 __global__ void prep_kernel(StepArgs a, Slots sl) {
   const int b = blockIdx.y;
-  const int s = sl.stream[b];
+  const int s = a.dslots ? a.dslots[b] : sl.stream[b];
   const int T = a.t.max_tracks;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= a.t.n_tracks[s]) return;
@@ -176,7 +177,7 @@ __global__ void prep_kernel(StepArgs a, Slots sl) {
 // 32 tracks x 32 detections per CTA, 256 threads: thread (tx, ty) owns det tx, tracks 4ty..4ty+3.
 __global__ void cost_kernel(StepArgs a, Slots sl) {
   const int b = blockIdx.z;
-  const int s = sl.stream[b];
+  const int s = a.dslots ? a.dslots[b] : sl.stream[b];
   const int T = a.t.max_tracks;
   const int nt = a.t.n_tracks[s];
   const int D = det_count(a, b);
@@ -346,7 +347,7 @@ __device__ bool hungarian_warp(const double* A, int R, int M, double* u, double*
 __global__ void __launch_bounds__(256) assign_kernel(StepArgs a, Slots sl) {
   extern __shared__ uint8_t smem[];
   const int b = blockIdx.x;
-  const int s = sl.stream[b];
+  const int s = a.dslots ? a.dslots[b] : sl.stream[b];
   const int T = a.t.max_tracks;
   const int Dmax = a.t.max_dets;
   const int nt = a.t.n_tracks[s];
@@ -641,7 +642,7 @@ constexpr int STATE_REMOVED = 0;
 __global__ void __launch_bounds__(256) assign_cascade_kernel(StepArgs a, Slots sl) {
   extern __shared__ uint8_t smem[];
   const int b = blockIdx.x;
-  const int s = sl.stream[b];
+  const int s = a.dslots ? a.dslots[b] : sl.stream[b];
   const int T = a.t.max_tracks;
   const int Dmax = a.t.max_dets;
   const int nt = a.t.n_tracks[s];
@@ -931,7 +932,7 @@ int track_reset(TrackState& t, int s, cudaStream_t st) {
 }
 
 int track_step(TrackState& t, const jde_config& cfg, int n, const int32_t* stream_ids, const jde_dets* dets,
-               jde_tracks* out, int* err, cudaStream_t st, char* msg, size_t msg_len) {
+               jde_tracks* out, int* err, cudaStream_t st, char* msg, size_t msg_len, const int* dev_slots) {
   if (n < 1 || n > t.max_batch || !stream_ids || !dets || !out || !dets->rows || !dets->count || dets->cap < 1 ||
       !out->id || !out->box || !out->state || !out->count || out->cap < 1) {
     snprintf(msg, msg_len, "bad arguments (n=%d, at most %d streams per call)", n, t.max_batch);
@@ -983,6 +984,7 @@ int track_step(TrackState& t, const jde_config& cfg, int n, const int32_t* strea
   a.assign_thresh = cfg.assign_thresh;
   a.lost_max = cfg.lost_max_frames;
   a.momentum = cfg.emb_momentum;
+  a.dslots = dev_slots;
   a.cascade = t.cascade;
   a.lam = cfg.motion_lambda;
   a.iou2 = cfg.iou_cost2;

@@ -47,6 +47,8 @@ int track_alloc(TrackState& t, const jde_config& cfg);
 size_t track_bytes(const jde_config& cfg);   // device bytes track_alloc takes
 void track_free(TrackState& t);
 int track_reset(TrackState& t, int stream_id, cudaStream_t st);
-// Returns a jde_status value; msg receives a reason on failure.
+// Returns a jde_status value; msg receives a reason on failure.  dev_slots (device, n ints, optional): the
+// kernels read the stream slots from it instead of the by-value copy of stream_ids (a captured CUDA graph
+// then serves any set of streams; stream_ids is still validated and must hold the same ids).
 int track_step(TrackState& t, const jde_config& cfg, int n, const int32_t* stream_ids, const jde_dets* dets,
-               jde_tracks* out, int* err, cudaStream_t st, char* msg, size_t msg_len);
+               jde_tracks* out, int* err, cudaStream_t st, char* msg, size_t msg_len, const int* dev_slots = nullptr);

@@ -53,6 +53,24 @@ class jde_tracks(C.Structure):
 
 
 _P = C.c_void_p
+
+
+class jde_server_config(C.Structure):
+    _fields_ = [("group", jde_config), ("src_w", C.c_int), ("src_h", C.c_int), ("max_streams_per_group", C.c_int),
+                ("hbm_budget_bytes", C.c_size_t), ("det_cap", C.c_int), ("track_cap", C.c_int),
+                ("caller_heads", C.c_int), ("collect_net_heads", C.c_int), ("use_graphs", C.c_int)]
+
+
+class jde_frame_out(C.Structure):
+    _fields_ = [("track_id", _P), ("track_box", _P), ("track_state", _P), ("track_det", _P), ("rows", _P),
+                ("net_det", _P * 3)]
+
+
+class jde_frame_result(C.Structure):
+    _fields_ = [("ticket", C.c_longlong), ("stream_id", C.c_int), ("n_dets", C.c_int), ("n_tracks", C.c_int),
+                ("errors", C.c_int), ("done_ms", C.c_float)]
+
+
 _sig = {
     "jde_default_config": (None, [C.POINTER(jde_config)]),
     "jde_layer_table": (C.c_int, [C.POINTER(jde_layer_desc), C.c_int]),
@@ -78,6 +96,19 @@ _sig = {
     "jde_selftest_wait": (C.c_int, [_P, C.c_longlong, C.POINTER(C.c_int), _P]),
     "jde_postprocess_noalloc": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float, C.c_float,
                                           C.c_int, C.POINTER(jde_dets), _P, C.c_char_p, C.c_size_t]),
+    "jde_default_server_config": (None, [C.POINTER(jde_server_config)]),
+    "jde_server_create": (C.c_int, [C.POINTER(jde_server_config), _P, C.c_size_t, C.POINTER(_P)]),
+    "jde_server_destroy": (None, [_P]),
+    "jde_server_last_error": (C.c_char_p, [_P]),
+    "jde_server_reset_clock": (C.c_int, [_P]),
+    "jde_stream_open": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.c_int)]),
+    "jde_stream_close": (C.c_int, [_P, C.c_int]),
+    "jde_submit": (C.c_int, [_P, C.c_int, _P, _P, C.POINTER(jde_frame_out), C.POINTER(C.c_longlong)]),
+    "jde_poll": (C.c_int, [_P, C.POINTER(jde_frame_result), C.c_int, C.POINTER(C.c_int)]),
+    "jde_server_flush": (C.c_int, [_P]),
+    "jde_server_group_cost": (C.c_int, [C.POINTER(jde_server_config), C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
+    "jde_server_device_bytes": (C.c_int, [_P, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
+    "jde_server_stats": (C.c_int, [_P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(lib, _name)
@@ -266,3 +297,91 @@ def jde_selftest_wait(h, limit_cycles, stream=None) -> tuple[int, int]:
     if st not in (JDE_OK, 6):
         _check(h, st)
     return st, w.value
+
+
+# ----------------------------------------------------------------------------- server
+def _check_server(s, status):
+    if status != JDE_OK:
+        msg = lib.jde_server_last_error(s).decode(errors="replace") if s else "invalid argument"
+        raise JdeError(status, msg)
+
+
+def jde_default_server_config() -> jde_server_config:
+    cfg = jde_server_config()
+    lib.jde_default_server_config(C.byref(cfg))
+    return cfg
+
+
+def jde_server_create(cfg: jde_server_config, blob: bytes):
+    out = _P()
+    buf = C.create_string_buffer(blob, len(blob))
+    st = lib.jde_server_create(C.byref(cfg), buf, len(blob), C.byref(out))
+    if st != JDE_OK:
+        raise JdeError(st, "jde_server_create")
+    return out
+
+
+def jde_server_destroy(s) -> None:
+    lib.jde_server_destroy(s)
+
+
+def jde_server_reset_clock(s) -> None:
+    _check_server(s, lib.jde_server_reset_clock(s))
+
+
+def jde_stream_open(s, in_w, in_h) -> int:
+    """Returns the stream id; raises JdeError (status JDE_ERR_ADMISSION = 5 when refused)."""
+    sid = C.c_int()
+    _check_server(s, lib.jde_stream_open(s, in_w, in_h, C.byref(sid)))
+    return sid.value
+
+
+def jde_stream_close(s, stream_id) -> None:
+    _check_server(s, lib.jde_stream_close(s, stream_id))
+
+
+def make_frame_out(track_id=None, track_box=None, track_state=None, track_det=None, rows=None, net_det=None):
+    """jde_frame_out over host numpy arrays (kept alive by the caller until the frame's result is polled)."""
+    nd = list(net_det) if net_det is not None else [None, None, None]
+    return jde_frame_out(ptr(track_id), ptr(track_box), ptr(track_state), ptr(track_det), ptr(rows),
+                         (_P * 3)(*[ptr(x) for x in nd]))
+
+
+def jde_submit(s, stream_id, frame, heads=None, out: jde_frame_out | None = None) -> int:
+    hp = None if heads is None else (_P * 6)(*[ptr(x) for x in heads])
+    t = C.c_longlong()
+    _check_server(s, lib.jde_submit(s, stream_id, ptr(frame), hp, None if out is None else C.byref(out), C.byref(t)))
+    return t.value
+
+
+def jde_poll(s, cap=256):
+    """Results of finished frames (jde_frame_result structures), at most cap."""
+    arr = (jde_frame_result * cap)()
+    n = C.c_int()
+    _check_server(s, lib.jde_poll(s, arr, cap, C.byref(n)))
+    return [arr[i] for i in range(n.value)]
+
+
+def jde_server_flush(s) -> None:
+    _check_server(s, lib.jde_server_flush(s))
+
+
+def jde_server_group_cost(cfg: jde_server_config, in_w, in_h) -> int:
+    out = C.c_size_t()
+    st = lib.jde_server_group_cost(C.byref(cfg), in_w, in_h, C.byref(out))
+    if st != JDE_OK:
+        raise JdeError(st, f"jde_server_group_cost({in_w}, {in_h})")
+    return int(out.value)
+
+
+def jde_server_device_bytes(s) -> tuple[int, int]:
+    a, b = C.c_size_t(), C.c_size_t()
+    _check_server(s, lib.jde_server_device_bytes(s, C.byref(a), C.byref(b)))
+    return int(a.value), int(b.value)
+
+
+def jde_server_stats(s) -> tuple[int, int, int]:
+    """(batches launched eagerly, graphs captured, graph replays)."""
+    e, c, r = C.c_longlong(), C.c_longlong(), C.c_longlong()
+    _check_server(s, lib.jde_server_stats(s, C.byref(e), C.byref(c), C.byref(r)))
+    return e.value, c.value, r.value

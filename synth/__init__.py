@@ -301,3 +301,45 @@ class PlantedClip:
         for s, y, x, vec in emb_e:
             embs[s][y, x] = vec
         return dets, embs, truth
+
+
+class PlantedHeadFrames:
+    """The frames of a ``PlantedClip`` written as dense head tensors on a torch device.
+
+    ``write(torch, bufs, t)`` fills ``bufs`` (the three ``[H_s, W_s, 24]`` detection maps and the three
+    ``[H_s, W_s, 512]`` embedding maps of one frame, float32, on the device) with frame ``t mod T`` of
+    the clip on torch's current stream: the background values of ``PlantedClip.frame``, then one
+    scatter per tensor of the frame's entries (kept in compact form, built once per frame).
+    """
+
+    def __init__(self, clip: PlantedClip):
+        self.clip = clip
+        self._entries = {}
+
+    def entries(self, t: int):
+        t %= self.clip.T
+        if t not in self._entries:
+            det_e, emb_e, _ = self.clip.frame_entries(t)
+            per = []
+            for s, (gh, gw) in enumerate(self.clip.grids):
+                de = [e for e in det_e if e[0] == s]
+                ee = [e for e in emb_e if e[0] == s]
+                lin = np.array([(y * gw + x) * 24 + 6 * a + k for _, y, x, a, _ in de for k in range(6)], np.int64)
+                vals = np.array([v for e in de for v in e[4]], np.float32)
+                cells = np.array([y * gw + x for _, y, x, _ in ee], np.int64)
+                vecs = np.array([e[3] for e in ee], np.float32).reshape(-1, 512)
+                per.append((lin, vals, cells, vecs))
+            self._entries[t] = per
+        return self._entries[t]
+
+    def write(self, torch, bufs, t: int):
+        dev = bufs[0].device
+        for s, (lin, vals, cells, vecs) in enumerate(self.entries(t)):
+            d, e = bufs[s], bufs[3 + s]
+            d.zero_()
+            d[..., 4::6] = -6.0
+            e.zero_()
+            if len(lin):
+                d.view(-1)[torch.from_numpy(lin).to(dev)] = torch.from_numpy(vals).to(dev)
+            if len(cells):
+                e.view(-1, 512)[torch.from_numpy(cells).to(dev)] = torch.from_numpy(vecs).to(dev)

@@ -26,19 +26,6 @@ def test_poisson_arrivals_are_seeded_sorted_and_at_the_stream_rate():
     assert abs(gaps.mean() - 1 / 30) < 0.005
 
 
-def test_admission_ledger_charges_once_and_refuses_over_budget():
-    led = serve.AdmissionLedger(10_000)
-    assert led.try_charge("a", 6000)
-    assert led.try_charge("a", 6000)          # already charged: no second charge
-    assert led.used == 6000
-    assert not led.try_charge("b", 4001)
-    assert led.try_charge("c", 4000)
-    assert led.used == 10_000
-    led.credit("a")
-    assert led.used == 4000
-    assert led.try_charge("b", 4001)
-
-
 def test_estimated_device_bytes_scale_with_input_size_and_batch():
     from paper_2011_03910_gb300 import jde
     cfg = jde.jde_default_config()
@@ -55,21 +42,48 @@ def test_estimated_device_bytes_scale_with_input_size_and_batch():
         jde.jde_estimate_device_bytes(cfg, 1100, 608)      # not a multiple of 32
 
 
-def test_budget_admits_groups_in_arrival_order_until_full():
-    """Admission rule of Server.open_stream with the library's own estimates: a group is charged when
-    its first stream arrives; a size whose group does not fit is refused."""
+def _server_cfg(caller_heads=0, collect=0, batch=16):
     from paper_2011_03910_gb300 import jde
-    cfg = jde.jde_default_config()
-    cfg.precision = jde.JDE_BF16
-    cfg.max_batch = 16
-    cost = {}
-    for w, h in [(1088, 608), (864, 480), (576, 320)]:
-        cfg.max_in_w, cfg.max_in_h = w, h
-        cost[(w, h)] = jde.jde_estimate_device_bytes(cfg, w, h) + serve._Group.buffer_bytes(16, w, h, 256, 256)
-    budget = cost[(1088, 608)] + cost[(576, 320)] + 1
-    led = serve.AdmissionLedger(budget)
-    admitted = [led.try_charge((s.in_w, s.in_h), cost[(s.in_w, s.in_h)]) for s in specs(6)]
-    assert admitted == [True, False, True, True, False, True]
+    c = jde.jde_default_server_config()
+    c.group.precision = jde.JDE_BF16
+    c.group.max_batch = batch
+    c.caller_heads, c.collect_net_heads = caller_heads, collect
+    return c
+
+
+def test_server_group_cost_is_the_handle_estimate_plus_the_batch_buffers():
+    """jde_server_group_cost (host arithmetic, no GPU): the handle's estimate for the group's size plus
+    frames, caller heads, detection rows, track outputs, collected detection maps and stream slots."""
+    from paper_2011_03910_gb300 import jde
+    B, W, H = 16, 1088, 608
+    cells = sum((H // s) * (W // s) for s in (32, 16, 8))
+    for caller, collect in [(0, 0), (1, 0), (1, 1), (0, 1)]:
+        c = _server_cfg(caller, collect, B)
+        g = jde.jde_config.from_buffer_copy(c.group)
+        g.max_in_w, g.max_in_h, g.max_src_w, g.max_src_h = W, H, 1920, 1080
+        g.max_streams = c.max_streams_per_group
+        if caller:
+            g.sparse_emb = 0          # the forward computes the embedding maps densely
+        est = jde.jde_estimate_device_bytes(g, W, H)
+        buf = (B * 1920 * 1080 * 3 + caller * B * cells * 536 * 4 + B * c.det_cap * 518 * 4 + B * 4 +
+               B * c.track_cap * 32 + B * 4 + collect * B * cells * 24 * 4 + B * 4)
+        assert jde.jde_server_group_cost(c, W, H) == est + buf
+    with pytest.raises(jde.JdeError):
+        jde.jde_server_group_cost(_server_cfg(), 1100, 608)     # not a multiple of 32
+    bad = _server_cfg()
+    bad.group.max_batch = 65
+    with pytest.raises(jde.JdeError):
+        jde.jde_server_group_cost(bad, 1088, 608)
+
+
+def test_server_group_cost_orders_the_serving_sizes():
+    from paper_2011_03910_gb300 import jde
+    c = _server_cfg()
+    cost = [jde.jde_server_group_cost(c, w, h) for w, h in [(1088, 608), (864, 480), (576, 320)]]
+    assert cost[0] > cost[1] > cost[2] > 16 * 1920 * 1080 * 3
+    # with caller heads the dense embedding maps come back into the handle and the heads into the group
+    c1 = _server_cfg(caller_heads=1)
+    assert jde.jde_server_group_cost(c1, 1088, 608) > cost[0]
 
 
 def _act_bytes(n, hw, c, el, pad=1):
