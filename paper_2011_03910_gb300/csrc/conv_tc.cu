@@ -44,6 +44,7 @@ struct TcArgs {
   int total_units;                 // work units: tiles, or (CTA pairs) pairs of M tiles x N tiles
   int kel;                         // elements of one k-block along K (E4M3: twice the bf16 count, same bytes)
   int wnb, whb;                    // mode 4: TMA boxes per window, pixel rows per box
+  int msub;                        // mode 4: 128-row M sub-tiles per CTA and unit (1 or 2)
   ConvSpec c;
 };
 
@@ -69,8 +70,13 @@ __host__ __device__ constexpr int tc_threads(int gw) { return 32 * (gw + 1 + EPI
 // Q = 1: E4M3 operands (one byte per element; a k-block row holds 2 * BKC elements, the same
 // bytes as BKC bf16 ones) and E4M3 staged outputs.
 // WM = 1: mode 4 (flat window); the ring holds weight tiles only, the windows are sized at launch.
+// WM = 2: mode 4 with two M sub-tiles per CTA: a unit is 256 rows x BN columns per CTA (512 x BN per
+// pair), each weight tile feeding the MMAs of both sub-tiles, whose accumulators sit side by side
+// (columns [0, BN) and [BN, 2 BN) of the unit's TMEM buffer); epilogue group g drains sub-tile g.
 template <int BN, int BKC, int STAGES, int CG = 1, int Q = 0, int WM = 0>
 struct TcCfg {
+  static constexpr int MS = WM == 2 ? 2 : 1;            // M sub-tiles per unit
+  static constexpr int ACC = BN * MS;                   // TMEM columns of one unit's accumulators
   static constexpr int A_BYTES = 128 * BKC * 2;
   static constexpr int B_BYTES = (BN / CG) * BKC * 2;
   static constexpr int STAGE_BYTES = WM ? B_BYTES : A_BYTES + B_BYTES;
@@ -87,11 +93,12 @@ struct TcCfg {
       STAGES * STAGE_BYTES + 2 * SDEPTH * C_BYTES + 1024 /*align*/ + BAR_BYTES + BIAS_BYTES;
   static constexpr uint32_t LAYOUT = BKC == 64 ? 2u : 4u;     // SW128 : SW64 (MMA operand tiles)
   static constexpr uint32_t SBO = 8 * BKC * 2;                 // bytes per 8-row group
-  static constexpr int NBUF = BN <= 128 ? 4 : 2;               // TMEM accumulator buffers
+  static constexpr int NBUF = ACC <= 128 ? 4 : 2;              // TMEM accumulator buffers
   // 256-wide tiles (two TMEM buffers): both epilogue groups drain every tile, each half of its
-  // columns, so a buffer is free again in half the time; narrower tiles alternate between groups
-  static constexpr bool SPLIT = BN == 256;
-  static constexpr uint32_t TMEM_COLS = NBUF * BN;
+  // columns (WM = 2: each one sub-tile), so a buffer is free again in half the time; narrower
+  // tiles alternate between groups
+  static constexpr bool SPLIT = ACC == 256;
+  static constexpr uint32_t TMEM_COLS = NBUF * ACC;
   static_assert(SMEM <= 227 * 1024 - 64, "shared memory budget (64 bytes left for static shared variables)");
   static_assert((2 * STAGES + 2 * NBUF + 2 + 2 * MAX_WIN + 1) * 8 + 4 <= BAR_BYTES, "barrier region");
   static_assert(TMEM_COLS >= 32 && TMEM_COLS <= 512, "TMEM budget");
@@ -177,7 +184,7 @@ __device__ __forceinline__ TileCoord tile_coord(const TcArgs& a, int tile, int b
   t.oy0 = 0;
   t.ox0 = 0;
   if (!patch_mode(a.mode)) {
-    t.m0 = m_tile * 128;
+    t.m0 = m_tile * 128 * a.msub;
   } else {
     const int per_img = a.tiles_x * a.tiles_y;
     t.img = m_tile / per_img;
@@ -538,7 +545,7 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
           break;
         }
         tc_fence_after();
-        const uint32_t d = tmem + buf * BN;
+        const uint32_t d = tmem + buf * Cfg::ACC;
         if constexpr (CG == 1 && !Q) if (a.mode == 3) {
           const uint32_t wb = local % (uint32_t)a.nwin;
           if (!mbar_wait(&win_full[wb], (local / (uint32_t)a.nwin) & 1u)) {
@@ -578,8 +585,10 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
               const uint64_t bd_s = desc_add(b_desc0, (s * (uint32_t)Cfg::B_BYTES) >> 4);
 #pragma unroll
               for (int kk = 0; kk < BKC / 16; ++kk)
-                mma_step<CG, Q>(d, desc_add(ad_t, 2 * kk), desc_add(bd_s, 2 * kk), idesc,
-                                (cb | tap | kk) != 0 ? 1u : 0u);
+#pragma unroll
+                for (int ms = 0; ms < Cfg::MS; ++ms)   // sub-tile ms: 128 window rows (8 KB) further on
+                  mma_step<CG, Q>(d + (uint32_t)(ms * BN), desc_add(ad_t, 2 * kk + ms * 512), desc_add(bd_s, 2 * kk),
+                                  idesc, (cb | tap | kk) != 0 ? 1u : 0u);
               if constexpr (CG == 2)
                 umma_commit_pair(&empty[s], 3);
               else
@@ -660,6 +669,9 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
     const int row = quarter * 32 + lane;
     const bool elected = (ew & 3) == 0 && lane == 0;
     const int bar_id = 1 + g;
+    // WM = 2: group g drains sub-tile g (rows 128 g .. 128 g + 127 of the unit, TMEM columns g BN ..)
+    const int mrow = WM == 2 ? g * 128 : 0;
+    const uint32_t cbase = WM == 2 ? (uint32_t)(g * BN) : 0u;
     // the group's SDEPTH staging tiles take the passes in turn, so a pass only waits for the
     // store issued SDEPTH passes earlier to have read its tile
     uint8_t* const stg_base = sC + g * Cfg::SDEPTH * Cfg::C_BYTES;
@@ -701,7 +713,7 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
       int n = 0, y = 0, x = 0;
       bool valid;
       if (!patch_mode(a.mode)) {
-        const int m = tc.m0 + row;
+        const int m = tc.m0 + mrow + row;
         const int plane = a.Hp * a.Wp;
         n = m / plane;
         const int r = m % plane;
@@ -720,14 +732,14 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
         // TMA store box; rows on the halo are written as zeros
         constexpr int FW = Cfg::C_BYTES / (128 * 4);
         constexpr int NSP = BN / FW;
-        const int sp_begin = Cfg::SPLIT ? g * (NSP / 2) : 0;
-        const int sp_end = Cfg::SPLIT ? sp_begin + NSP / 2 : NSP;
+        const int sp_begin = Cfg::SPLIT && WM != 2 ? g * (NSP / 2) : 0;
+        const int sp_end = Cfg::SPLIT && WM != 2 ? sp_begin + NSP / 2 : NSP;
         for (int sp = sp_begin; sp < sp_end; ++sp) {
           stg = stg_base + (npass++ % Cfg::SDEPTH) * Cfg::C_BYTES;
-          const bool live = tile_live(a, tc);
+          const bool live = WM == 2 ? tc.m0 + mrow < a.M_total : tile_live(a, tc);
           const int c0 = sp * FW;
           uint32_t r[32];
-          const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + buf * BN + (uint32_t)c0;
+          const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + buf * Cfg::ACC + cbase + (uint32_t)c0;
           if (FW == 32)
             tmem_ld32(taddr, r);
           else
@@ -771,7 +783,7 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
           named_bar(bar_id, 128);
           if (elected && ok && live && !aborted(&s_abort)) {
             if (!patch_mode(a.mode))
-              tma_store_2d(&plan.o, stg, tc.n0 + c0, tc.m0);
+              tma_store_2d(&plan.o, stg, tc.n0 + c0, tc.m0 + mrow);
             else
               tma_store_4d(&plan.o, stg, tc.n0 + c0, tc.ox0 + 1, tc.oy0 + 1, tc.img);
             bulk_commit();
@@ -786,11 +798,11 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
         const int nsub = o8 ? 1 : Cfg::NSUB;
         const int sub_ch = o8 ? Cfg::SWC : Cfg::SUB;
         const int sub_bytes = o8 ? 128 * Cfg::SWC : Cfg::SUB_BYTES;
-        const int p_begin = Cfg::SPLIT ? g * (Cfg::PASSES / 2) : 0;
-        const int p_end = Cfg::SPLIT ? p_begin + Cfg::PASSES / 2 : Cfg::PASSES;
+        const int p_begin = Cfg::SPLIT && WM != 2 ? g * (Cfg::PASSES / 2) : 0;
+        const int p_end = Cfg::SPLIT && WM != 2 ? p_begin + Cfg::PASSES / 2 : Cfg::PASSES;
         for (int p = p_begin; p < p_end; ++p) {
           stg = stg_base + (npass++ % Cfg::SDEPTH) * Cfg::C_BYTES;
-          const bool live = tile_live(a, tc);
+          const bool live = WM == 2 ? tc.m0 + mrow < a.M_total : tile_live(a, tc);
           const bool use_res = a.tma_res && ok && live;
           if (elected) {
             bulk_wait_read<Cfg::SDEPTH - 1>();   // the store that last used this staging tile has read it
@@ -801,7 +813,7 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
                 if (patch_mode(a.mode))
                   tma_load_4d(stg + j * sub_bytes, &plan.r, &res_full[g], ch, tc.ox0 + 1, tc.oy0 + 1, tc.img);
                 else
-                  tma_load_2d(stg + j * sub_bytes, &plan.r, &res_full[g], ch, tc.m0);
+                  tma_load_2d(stg + j * sub_bytes, &plan.r, &res_full[g], ch, tc.m0 + mrow);
               }
             }
           }
@@ -816,7 +828,7 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
 #pragma unroll 1
           for (int c0 = 0; c0 < Cfg::SWC; c0 += 32) {
             uint32_t r[32];
-            tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + buf * BN + (uint32_t)(p * Cfg::SWC + c0), r);
+            tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + buf * Cfg::ACC + cbase + (uint32_t)(p * Cfg::SWC + c0), r);
             // the chunk's shared-memory operands (bias, scale, residual) are all read before any of
             // its stores, so the loads overlap each other and the TMEM read
             const int nu = o8 ? 2 : 4;               // 16-byte staging units of the chunk's 32 columns
@@ -930,9 +942,9 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
               // in place over the residual: the tile is added to it (the residual add of the block)
               if (!patch_mode(a.mode)) {
                 if (a.red_res)
-                  tma_reduce_add_2d(&plan.o, stg + j * sub_bytes, ch, tc.m0);
+                  tma_reduce_add_2d(&plan.o, stg + j * sub_bytes, ch, tc.m0 + mrow);
                 else
-                  tma_store_2d(&plan.o, stg + j * sub_bytes, ch, tc.m0);
+                  tma_store_2d(&plan.o, stg + j * sub_bytes, ch, tc.m0 + mrow);
               } else {
                 if (a.red_res)
                   tma_reduce_add_4d(&plan.o, stg + j * sub_bytes, ch, tc.ox0 + 1, tc.oy0 + 1, tc.img);
@@ -949,7 +961,7 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
 #pragma unroll 1
         for (int c0 = Cfg::SPLIT ? g * (BN / 2) : 0; c0 < (Cfg::SPLIT ? (g + 1) * (BN / 2) : BN); c0 += 32) {
           uint32_t r[32];
-          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + buf * BN + (uint32_t)c0, r);
+          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + buf * Cfg::ACC + (uint32_t)c0, r);
           tmem_ld_wait();
           const int ch0 = tc.n0 + c0;
           if (valid && ch0 < c.cout) {
@@ -1007,15 +1019,17 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
 // E4M3 weight tiles are consumed twice as fast (K = 32 per MMA), so their ring is deeper
 constexpr int W4_STAGES = 8;
 constexpr int W4_STAGES_Q = 12;
-template <int BN, int CG, int Q>
+constexpr int W4M2_STAGES = 12;   // two sub-tiles: half-size weight tiles (64 rows per CTA), each used twice
+template <int BN, int CG, int Q, int WM>
 constexpr int w4_fixed() {
-  constexpr int S = Q ? W4_STAGES_Q : W4_STAGES;
-  using C = TcCfg<BN, 32, S, CG, Q, 1>;
+  constexpr int S = WM == 2 ? W4M2_STAGES : (Q ? W4_STAGES_Q : W4_STAGES);
+  using C = TcCfg<BN, 32, S, CG, Q, WM>;
   return S * C::B_BYTES + 2 * C::SDEPTH * C::C_BYTES + 1024 + C::BAR_BYTES + C::BIAS_BYTES;
 }
-int w4_fixed_bytes(int bn, int q) {
-  if (bn == 128) return q ? w4_fixed<128, 2, 1>() : w4_fixed<128, 2, 0>();
-  return q ? w4_fixed<256, 2, 1>() : w4_fixed<256, 2, 0>();
+int w4_fixed_bytes(int bn, int q, int msub) {
+  if (msub == 2) return q ? w4_fixed<128, 2, 1, 2>() : w4_fixed<128, 2, 0, 2>();
+  if (bn == 128) return q ? w4_fixed<128, 2, 1, 1>() : w4_fixed<128, 2, 0, 1>();
+  return q ? w4_fixed<256, 2, 1, 1>() : w4_fixed<256, 2, 0, 1>();
 }
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -1146,10 +1160,15 @@ int conv_tc_pick_bn(int cout) {
 }
 
 bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const void* w_any, int cout_pad, int bn, char* msg,
-                  size_t msg_len) {
+                  size_t msg_len, int msub) {
   const __nv_bfloat16* w = static_cast<const __nv_bfloat16*>(w_any);
   plan = TcPlan();
   plan.spec = c;
+  plan.msub = 1;
+  if (msub != 1 && (msub != 2 || bn != 128 || c.k != 3 || c.stride != 1)) {
+    snprintf(msg, msg_len, "two M sub-tiles: flat-window 3x3 convs with 128-wide tiles only");
+    return false;
+  }
   if (c.cin == 3 && c.k == 3 && c.stride == 1 && c.in.dtype == 1 && c.in.pad == 1 && c.in.pixstride == 4 &&
       (bn == 32 || bn == 64)) {
     // stem: im2col rows gathered in the kernel (K = 27 padded to 32), flat over the padded image
@@ -1294,14 +1313,16 @@ bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const void* w_any, int cout_p
     const int kel4 = q ? 64 : 32;           // 64-byte k-blocks
     // (measured: E4M3 convs of two 64-byte k-blocks, 128 input channels, run faster flat)
     if (c.k == 3 && (bn == 128 || bn == 256) && c.cin % kel4 == 0 && !(q && c.cin / kel4 == 2)) {
-      const int npx = 128 + 2 * Wp + 2;      // rows m0 - Wp - 1 .. m0 + 128 + Wp
+      const int npx = 128 * msub + 2 * Wp + 2;   // rows m0 - Wp - 1 .. m0 + 128 msub + Wp
       const int wnb = (npx + 255) / 256;     // a TMA box spans at most 256 rows
       const int whb = ((npx + wnb - 1) / wnb + 15) / 16 * 16;   // rows per box: 1024-byte multiples
       const int win_bytes = wnb * whb * 64;
-      int nwin = (227 * 1024 - 64 - w4_fixed_bytes(bn, q)) / win_bytes;
+      int nwin = (227 * 1024 - 64 - w4_fixed_bytes(bn, q, msub)) / win_bytes;
       if (nwin > MAX_WIN) nwin = MAX_WIN;
       if (nwin >= 2) {
         plan.mode = 4;
+        plan.msub = msub;
+        plan.m_tiles = (plan.M_total + 128 * msub - 1) / (128 * msub);
         plan.wnb = wnb;
         plan.whb = whb;
         plan.win_bytes = win_bytes;
@@ -1445,6 +1466,7 @@ cudaError_t conv_tc_launch(const TcPlan& p, cudaStream_t st) {
   a.plane_tx = p.WW * p.WH * 64;
   a.wnb = p.wnb;
   a.whb = p.whb;
+  a.msub = p.msub > 1 ? p.msub : 1;
   a.c = p.spec;
   if (p.mode == 2) {
     if (p.bn == 32) return launch_cfg<32, 32, 16, 4>(p, a, st);
@@ -1452,8 +1474,13 @@ cudaError_t conv_tc_launch(const TcPlan& p, cudaStream_t st) {
     return cudaErrorInvalidValue;
   }
   if (p.mode == 4) {
-    const int smem = p.nwin * p.win_bytes + w4_fixed_bytes(p.bn, p.q);
+    const int smem = p.nwin * p.win_bytes + w4_fixed_bytes(p.bn, p.q, p.msub);
     if (smem > 227 * 1024 - 64) return cudaErrorInvalidValue;
+    if (p.msub == 2) {
+      if (p.bn != 128 || p.cg != 2 || !p.tma_out) return cudaErrorInvalidValue;
+      return p.q ? launch_cfg<128, 32, W4M2_STAGES, 1, 2, 1, 2>(p, a, st, smem)
+                 : launch_cfg<128, 32, W4M2_STAGES, 1, 2, 0, 2>(p, a, st, smem);
+    }
     if (p.bn == 128 && p.cg == 2)
       return p.q ? launch_cfg<128, 32, W4_STAGES_Q, 1, 2, 1, 1>(p, a, st, smem)
                  : launch_cfg<128, 32, W4_STAGES, 1, 2, 0, 1>(p, a, st, smem);

@@ -49,14 +49,17 @@ struct TcPlan {
   int cg;                        // 2: 256-wide tiles on CTA pairs (cta_group::2), else 1
   int q;                         // 1: E4M3 operands (kind::f8f6f4)
   int kel;                       // elements of one k-block along K (bf16: bkc, E4M3: 2 * bkc)
+  int msub;                      // mode 4: M tiles of 128 rows per CTA and work unit (1 or 2)
   ConvSpec spec;
 };
 // Fill plan (tensor maps and grid) for a conv whose input is a padded bf16
 // view and whose weights are w ([cout_pad][K] bf16).  Returns false with a
 // message if the shape is not supported by the tensor-core path.
 // w: [cout_pad][K] bf16, or E4M3 codes when c.q.
+// msub = 2 (flat-window 3x3 convs with bn = 128 only): each CTA computes 256 rows x bn columns per
+// work unit, two M=128 sub-tiles sharing every weight tile and one window.
 bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const void* w, int cout_pad, int bn, char* msg,
-                  size_t msg_len);
+                  size_t msg_len, int msub = 1);
 cudaError_t conv_tc_launch(const TcPlan& plan, cudaStream_t st);
 // Point a planned conv at another output buffer of the same shape (the double-buffered heads);
 // re-encodes the output tensor map of a TMA-stored f32 head.  False if the map cannot be built.

@@ -472,7 +472,8 @@ jde_status get_plan(jde_handle* h, ResBuffers* rb, int n, Plan** out) {
       int bn = h->w[l].bn;
       auto tb = h->tuned_bn.find(key);
       if (tb != h->tuned_bn.end() && tb->second[l] > 0) bn = tb->second[l];
-      if (!conv_tc_plan(p.tc[l], c, w, h->w[l].cout_pad_tc, bn, msg, sizeof(msg)))
+      // tile code: output channels per tile, + 1 for two 128-row M sub-tiles per CTA (flat-window 3x3)
+      if (!conv_tc_plan(p.tc[l], c, w, h->w[l].cout_pad_tc, bn & ~1, msg, sizeof(msg), (bn & 1) ? 2 : 1))
         return fail(h, JDE_ERR_UNSUPPORTED, "layer %zu: %s", l, msg);
     }
   }
@@ -1257,13 +1258,15 @@ jde_status jde_autotune(jde_handle* h, int n, int in_w, int in_h, void* stream) 
     const LayerW& lw = h->w[l];
     const void* w = lw.q ? static_cast<const void*>(lw.w_q) : static_cast<const void*>(lw.w_nk);
     float best_ms = 1e30f;
-    for (int bn : {32, 64, 128, 256}) {
+    for (int code : {32, 64, 128, 256, 129}) {
+      const int bn = code & ~1, msub = (code & 1) ? 2 : 1;
       // 32-wide tiles only where they are the default (the 24-channel heads, 32-channel outputs)
       if (lw.cout_pad_tc % bn || (bn == 32 && lw.bn != 32)) continue;
       TcPlan cand;
       char msg[256];
-      if (!conv_tc_plan(cand, plan->specs[l], w, lw.cout_pad_tc, bn, msg, sizeof(msg))) continue;
-      if (cand.mode != def.mode) continue;   // same addressing mode: the same order of the K sum, same bits
+      if (!conv_tc_plan(cand, plan->specs[l], w, lw.cout_pad_tc, bn, msg, sizeof(msg), msub)) continue;
+      if (cand.mode != def.mode || cand.msub != msub) continue;   // same addressing mode: the same order of the K sum
+      if (msub == 2 && !cand.tma_out) continue;
       if (conv_tc_launch(cand, st) != cudaSuccess) {   // shape without a built configuration
         cudaGetLastError();
         continue;
@@ -1281,7 +1284,7 @@ jde_status jde_autotune(jde_handle* h, int n, int in_w, int in_h, void* stream) 
       const float ms = t[REPS / 2];   // median launch
       if (ms < best_ms) {
         best_ms = ms;
-        best[l] = bn;
+        best[l] = code;
       }
     }
   }
@@ -1291,6 +1294,53 @@ jde_status jde_autotune(jde_handle* h, int n, int in_w, int in_h, void* stream) 
   }
   h->tuned_bn[key] = best;
   h->plans.erase(key);   // rebuilt with the chosen tiles on the next forward
+  return JDE_OK;
+}
+
+jde_status jde_set_tile_choice(jde_handle* h, int n, int in_w, int in_h, const int* bn) {
+  if (!h || !bn) return fail(h, JDE_ERR_INVALID_ARG, "jde_set_tile_choice: NULL argument");
+  if (h->cfg.precision == JDE_FP32) return fail(h, JDE_ERR_UNSUPPORTED, "jde_set_tile_choice: tensor-core handles only");
+  if (n < 1 || n > h->cfg.max_batch || in_w % 32 || in_h % 32 || in_w < 32 || in_h < 32 || in_w > h->cfg.max_in_w ||
+      in_h > h->cfg.max_in_h)
+    return fail(h, JDE_ERR_INVALID_ARG, "jde_set_tile_choice: bad arguments");
+  std::vector<int> codes(bn, bn + JDE_NUM_LAYERS);
+  for (int l = 0; l < JDE_NUM_LAYERS; ++l)
+    if (!(codes[l] == 0 || codes[l] == 32 || codes[l] == 64 || codes[l] == 128 || codes[l] == 256 || codes[l] == 129))
+      return fail(h, JDE_ERR_INVALID_ARG, "jde_set_tile_choice: layer %d: tile code %d", l, codes[l]);
+  ResBuffers* rb;
+  jde_status s = get_res(h, in_w, in_h, &rb);
+  if (s != JDE_OK) return s;
+  const auto key = std::make_tuple(in_w, in_h, n);
+  auto prev = h->tuned_bn.find(key);
+  const bool had = prev != h->tuned_bn.end();
+  const std::vector<int> old = had ? prev->second : std::vector<int>();
+  h->tuned_bn[key] = codes;
+  h->plans.erase(key);
+  Plan* plan;
+  s = get_plan(h, rb, n, &plan);
+  if (s == JDE_OK) {
+    // a code the layer cannot run as asked (e.g. two sub-tiles whose windows do not fit) is refused
+    for (int l = 0; l < JDE_NUM_LAYERS && s == JDE_OK; ++l) {
+      if (codes[l] == 0 || plan->tc.empty() || not_stored(h, l) || (l == 1 && plan->stem_s2)) continue;
+      const TcPlan& t = plan->tc[l];
+      // the default tile's addressing mode: another mode would sum K in another order
+      TcPlan def;
+      char msg[256];
+      const LayerW& lw = h->w[l];
+      const void* w = lw.q ? static_cast<const void*>(lw.w_q) : static_cast<const void*>(lw.w_nk);
+      const bool def_ok = conv_tc_plan(def, plan->specs[l], w, lw.cout_pad_tc, lw.bn, msg, sizeof(msg));
+      if (t.bn != (codes[l] & ~1) || t.msub != ((codes[l] & 1) ? 2 : 1) || !def_ok || def.mode != t.mode)
+        s = fail(h, JDE_ERR_UNSUPPORTED, "jde_set_tile_choice: layer %d cannot run tile code %d", l, codes[l]);
+    }
+  }
+  if (s != JDE_OK) {
+    if (had)
+      h->tuned_bn[key] = old;
+    else
+      h->tuned_bn.erase(key);
+    h->plans.erase(key);
+    return s;
+  }
   return JDE_OK;
 }
 

@@ -87,6 +87,7 @@ _sig = {
     "jde_kernel_errors": (C.c_int, [_P, C.POINTER(C.c_int), _P]),
     "jde_autotune": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P]),
     "jde_tile_choice": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]),
+    "jde_set_tile_choice": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]),
     "jde_set_act_amax": (C.c_int, [_P, C.POINTER(C.c_float), C.c_int]),
     "jde_act_amax": (C.c_int, [_P, C.POINTER(C.c_float), _P]),
     "jde_device_bytes": (C.c_int, [_P, C.POINTER(C.c_size_t)]),
@@ -243,6 +244,11 @@ def jde_tile_choice(h, n, in_w, in_h):
     arr = (C.c_int * k)()
     _check(h, lib.jde_tile_choice(h, n, in_w, in_h, arr))
     return list(arr)
+
+
+def jde_set_tile_choice(h, n, in_w, in_h, codes) -> None:
+    arr = (C.c_int * JDE_NUM_LAYERS)(*[int(c) for c in codes])
+    _check(h, lib.jde_set_tile_choice(h, n, in_w, in_h, arr))
 
 
 def jde_set_act_amax(h, amax) -> None:

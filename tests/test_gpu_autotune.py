@@ -14,9 +14,10 @@ pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "fp8_amax_320x192.json")
 
 
-def _layer_outputs(j, h, frames):
+def _layer_outputs(j, h, frames, in_w=320, in_h=192):
     f = torch.from_numpy(frames).cuda()
-    j.jde_forward(h, f, frames.shape[0], 320, 192, 320, 192, True, torch.cuda.current_stream())
+    j.jde_forward(h, f, frames.shape[0], frames.shape[2], frames.shape[1], in_w, in_h, True,
+                  torch.cuda.current_stream())
     torch.cuda.synchronize()
     assert j.jde_kernel_errors(h) == 0
     outs = []
@@ -41,10 +42,73 @@ def test_autotuned_forward_is_bit_identical(fp8):
         default = j.jde_tile_choice(h, 2, 320, 192)
         j.jde_autotune(h, 2, 320, 192, torch.cuda.current_stream())
         tuned = j.jde_tile_choice(h, 2, 320, 192)
-        assert all(b in (32, 64, 128, 256) for b in tuned)
+        assert all(b in (32, 64, 128, 256, 129) for b in tuned)
         print("tile widths changed on", sum(a != b for a, b in zip(default, tuned)), "layers:", tuned)
         after = _layer_outputs(j, h, frames)
         for l, (a, b) in enumerate(zip(before, after)):
             np.testing.assert_array_equal(a, b, err_msg=f"layer {l}")
+    finally:
+        j.jde_destroy(h)
+
+
+def _two_subtile_codes(j, h, n, in_w, in_h, fp8=False):
+    """Tile code 129 (128 channels x 256 rows per CTA) on every stride-1 3x3 conv whose output channel
+    count is a multiple of 128 and whose output the handle stores (E4M3: not the 128-channel-input
+    convs, which run without windows)."""
+    codes = j.jde_tile_choice(h, n, in_w, in_h)
+    stored = set()
+    for l in range(78):
+        try:
+            j.jde_get_tensor(h, l)
+            stored.add(l)
+        except j.JdeError:
+            pass
+    table = j.jde_layer_table()
+    for l, (cin, cout, k, stride, _, _) in enumerate(table):
+        if k == 3 and stride == 1 and cin % 32 == 0 and cout % 128 == 0 and l in stored and not (fp8 and cin == 128):
+            codes[l] = 129
+    return codes
+
+
+@pytest.mark.parametrize("fp8,size", [(False, (320, 192)), (True, (320, 192)), (False, (1088, 608))])
+def test_two_m_subtiles_per_cta_are_bit_identical(fp8, size):
+    """Code 129 runs each flat-window 3x3 conv as 256 rows x 128 channels per CTA (two M sub-tiles sharing
+    every weight tile); each output is the same K sum in the same order, so every layer is bit-identical
+    to the default tiles."""
+    j = jde()
+    in_w, in_h = size
+    n = 2 if in_w == 320 else 1
+    h = make_handle(j.JDE_FP8_E4M3 if fp8 else j.JDE_BF16, max_batch=n, in_w=in_w, in_h=in_h, src_w=in_w,
+                    src_h=in_h, keep_layer_outputs=1)
+    try:
+        if fp8:
+            j.jde_set_act_amax(h, json.load(open(GOLDEN))["amax"])
+        frames = synth.frames_uniform(3, n, in_h, in_w)
+        before = _layer_outputs(j, h, frames, in_w, in_h)
+        codes = _two_subtile_codes(j, h, n, in_w, in_h, fp8)
+        assert sum(c == 129 for c in codes) >= 20
+        j.jde_set_tile_choice(h, n, in_w, in_h, codes)
+        assert j.jde_tile_choice(h, n, in_w, in_h) == codes
+        after = _layer_outputs(j, h, frames, in_w, in_h)
+        for l, (a, b) in enumerate(zip(before, after)):
+            np.testing.assert_array_equal(a, b, err_msg=f"layer {l} (code {codes[l]})")
+    finally:
+        j.jde_destroy(h)
+
+
+def test_set_tile_choice_refuses_codes_a_layer_cannot_run():
+    j = jde()
+    h = make_handle(j.JDE_BF16, max_batch=2, src_w=320, src_h=192)
+    try:
+        codes = j.jde_tile_choice(h, 2, 320, 192)
+        bad = list(codes)
+        bad[2] = 129                       # a 1x1 conv has no flat-window form
+        with pytest.raises(j.JdeError):
+            j.jde_set_tile_choice(h, 2, 320, 192, bad)
+        bad = list(codes)
+        bad[5] = 96                        # not a tile width
+        with pytest.raises(j.JdeError):
+            j.jde_set_tile_choice(h, 2, 320, 192, bad)
+        assert j.jde_tile_choice(h, 2, 320, 192) == codes     # the previous choice stands
     finally:
         j.jde_destroy(h)
