@@ -410,11 +410,14 @@ jde_status jde_stream_open(jde_server* s, int in_w, int in_h, int* stream_id);
 jde_status jde_stream_close(jde_server* s, int stream_id);
 
 /* Queue one frame of a stream.  `frame` (device, src_h x src_w x 3 uint8) and, with caller_heads,
- * heads[0..5] (device) must stay unchanged until the frame's result is returned by jde_poll; `out`
- * (copied) names host buffers for its results, or NULL.  *ticket (optional) receives the frame's
- * ticket, increasing from 1.  Frames of a stream are processed in submission order. */
+ * heads[0..5] (device) must stay unchanged until the frame's result is returned by jde_poll.
+ * ready_event (a cudaEvent_t, or NULL): the server's first read of the frame's inputs waits on the
+ * device for the event as recorded when the frame's batch starts, so a caller that fills the inputs
+ * on its own CUDA stream need not synchronise.  `out` (copied) names host buffers for its results,
+ * or NULL.  *ticket (optional) receives the frame's ticket, increasing from 1.  Frames of a stream
+ * are processed in submission order. */
 jde_status jde_submit(jde_server* s, int stream_id, const uint8_t* frame, const float* const* heads,
-                      const jde_frame_out* out, long long* ticket);
+                      void* ready_event, const jde_frame_out* out, long long* ticket);
 
 /* Advance the server without blocking (see above) and move up to cap results of finished frames
  * into results[0..*n), in completion order.  A failed launch or batch returns its status (the

@@ -36,6 +36,7 @@ struct Pending {
   int stream_id;
   const uint8_t* frame;     // device, src_h x src_w x 3
   const float* heads[6];    // device per-frame head tensors (caller_heads), else null
+  cudaEvent_t ready;        // the frame's inputs are complete when this event has completed, or null
   jde_frame_out out;        // host outputs filled when the frame's result is collected
 };
 
@@ -285,6 +286,7 @@ jde_status launch_batch(jde_server* s, Group* g) {
     const Pending& p = b.frames[i];
     ids[i] = s->streams[p.stream_id].slot;
     g->h_slots[i] = ids[i];
+    if (p.ready) S_CUDA(s, cudaStreamWaitEvent(g->st, p.ready, 0));
     S_CUDA(s, cudaMemcpyAsync(g->frames + (size_t)i * fbytes, p.frame, fbytes, cudaMemcpyDeviceToDevice, g->st));
     for (int k = 0; k < 6 && s->cfg.caller_heads; ++k)
       S_CUDA(s, cudaMemcpyAsync(reinterpret_cast<char*>(g->heads[k]) + (size_t)i * g->head_bytes[k], p.heads[k],
@@ -512,7 +514,7 @@ jde_status jde_stream_close(jde_server* s, int stream_id) {
   return JDE_OK;
 }
 
-jde_status jde_submit(jde_server* s, int stream_id, const uint8_t* frame, const float* const* heads,
+jde_status jde_submit(jde_server* s, int stream_id, const uint8_t* frame, const float* const* heads, void* ready_event,
                       const jde_frame_out* out, long long* ticket) {
   if (!s || !frame) return JDE_ERR_INVALID_ARG;
   auto it = s->streams.find(stream_id);
@@ -523,6 +525,7 @@ jde_status jde_submit(jde_server* s, int stream_id, const uint8_t* frame, const 
   p.ticket = s->next_ticket++;
   p.stream_id = stream_id;
   p.frame = frame;
+  p.ready = static_cast<cudaEvent_t>(ready_event);
   for (int k = 0; k < 6 && s->cfg.caller_heads; ++k) {
     if (!heads[k]) return sfail(s, JDE_ERR_INVALID_ARG, "head %d is NULL", k);
     p.heads[k] = heads[k];

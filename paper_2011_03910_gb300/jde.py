@@ -104,7 +104,7 @@ _sig = {
     "jde_server_reset_clock": (C.c_int, [_P]),
     "jde_stream_open": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.c_int)]),
     "jde_stream_close": (C.c_int, [_P, C.c_int]),
-    "jde_submit": (C.c_int, [_P, C.c_int, _P, _P, C.POINTER(jde_frame_out), C.POINTER(C.c_longlong)]),
+    "jde_submit": (C.c_int, [_P, C.c_int, _P, _P, _P, C.POINTER(jde_frame_out), C.POINTER(C.c_longlong)]),
     "jde_poll": (C.c_int, [_P, C.POINTER(jde_frame_result), C.c_int, C.POINTER(C.c_int)]),
     "jde_server_flush": (C.c_int, [_P]),
     "jde_server_group_cost": (C.c_int, [C.POINTER(jde_server_config), C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
@@ -353,10 +353,13 @@ def make_frame_out(track_id=None, track_box=None, track_state=None, track_det=No
                          (_P * 3)(*[ptr(x) for x in nd]))
 
 
-def jde_submit(s, stream_id, frame, heads=None, out: jde_frame_out | None = None) -> int:
+def jde_submit(s, stream_id, frame, heads=None, out: jde_frame_out | None = None, ready=None) -> int:
+    """ready: a torch.cuda.Event recorded after the frame's inputs were written (or None)."""
     hp = None if heads is None else (_P * 6)(*[ptr(x) for x in heads])
     t = C.c_longlong()
-    _check_server(s, lib.jde_submit(s, stream_id, ptr(frame), hp, None if out is None else C.byref(out), C.byref(t)))
+    ev = None if ready is None else ready.cuda_event
+    _check_server(s, lib.jde_submit(s, stream_id, ptr(frame), hp, ev, None if out is None else C.byref(out),
+                                    C.byref(t)))
     return t.value
 
 

@@ -81,6 +81,7 @@ class _Stream:
     frames: list             # device tensors [SRC_H, SRC_W, 3] uint8, cycled
     heads: object = None     # caller heads: an object with write(torch, bufs, index)
     ring: list = None        # caller heads: RING sets of six device tensors
+    ready: list = None       # caller heads: per ring set, the event recorded after it was written
 
 
 class Server:
@@ -156,6 +157,7 @@ class Server:
                         for gh, gw in self.grids(spec.in_w, spec.in_h)] +
                        [torch.empty((gh, gw, EMB_DIM), dtype=torch.float32, device=self.device)
                         for gh, gw in self.grids(spec.in_w, spec.in_h)] for _ in range(self.RING)]
+            st.ready = [torch.cuda.Event() for _ in range(self.RING)]
         self.streams[spec.stream_id] = st
         return True
 
@@ -202,17 +204,18 @@ class Server:
                 while q and outstanding[k] < self.RING:
                     batch.append(q.popleft())
                     outstanding[k] += 1
-            if batch and self.caller_heads:
-                for r in batch:
-                    st = self.streams[r.stream_id]
-                    st.heads.write(torch, st.ring[r.index % self.RING], r.index)
-                torch.cuda.current_stream(self.device).synchronize()
             for r in batch:
                 st = self.streams[r.stream_id]
                 bufs = self._out_buffers(st) if collect else None
                 out = jde.make_frame_out(**bufs) if bufs else None
-                heads = st.ring[r.index % self.RING] if self.caller_heads else None
-                t = jde.jde_submit(self.s, st.sid, st.frames[r.index % len(st.frames)], heads, out)
+                heads, ready = None, None
+                if self.caller_heads:
+                    # written on torch's stream; the server's copy of them waits for the event on the device
+                    k = r.index % self.RING
+                    heads, ready = st.ring[k], st.ready[k]
+                    st.heads.write(torch, heads, r.index)
+                    ready.record()
+                t = jde.jde_submit(self.s, st.sid, st.frames[r.index % len(st.frames)], heads, out, ready)
                 by_ticket[t] = (r, bufs, out)
             res = jde.jde_poll(self.s, 256)
             for x in res:

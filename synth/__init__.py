@@ -315,6 +315,7 @@ class PlantedHeadFrames:
     def __init__(self, clip: PlantedClip):
         self.clip = clip
         self._entries = {}
+        self._dev = {}
 
     def entries(self, t: int):
         t %= self.clip.T
@@ -332,14 +333,25 @@ class PlantedHeadFrames:
             self._entries[t] = per
         return self._entries[t]
 
+    def _device_entries(self, torch, dev, t: int):
+        key = (t % self.clip.T, str(dev))
+        if key not in self._dev:        # the frame's entries, copied to the device once
+            self._dev[key] = [tuple(torch.from_numpy(a).to(dev) for a in ent) for ent in self.entries(t)]
+        return self._dev[key]
+
+    def preload(self, torch, dev):
+        """Build every frame's entries and copy them to the device (before a timed run)."""
+        for t in range(self.clip.T):
+            self._device_entries(torch, dev, t)
+
     def write(self, torch, bufs, t: int):
         dev = bufs[0].device
-        for s, (lin, vals, cells, vecs) in enumerate(self.entries(t)):
+        for s, (lin, vals, cells, vecs) in enumerate(self._device_entries(torch, dev, t)):
             d, e = bufs[s], bufs[3 + s]
             d.zero_()
             d[..., 4::6] = -6.0
             e.zero_()
             if len(lin):
-                d.view(-1)[torch.from_numpy(lin).to(dev)] = torch.from_numpy(vals).to(dev)
+                d.view(-1)[lin] = vals
             if len(cells):
-                e.view(-1, 512)[torch.from_numpy(cells).to(dev)] = torch.from_numpy(vecs).to(dev)
+                e.view(-1, 512)[cells] = vecs

@@ -103,8 +103,8 @@ def nms_tie_frame(out, thr=pp.NMS_IOU, conf_band=1e-6, iou_band=1e-6):
 
 
 def bf16_heads_ok(errs):
-    """The benchmark spec's BF16 head criterion, 2e-2 relative max-abs against float64, as these tests apply
-    it.  The BF16 storage scheme's own per-head error on this random-init network (rounding alone, exact
-    arithmetic) spreads over 0.009-0.019 across frames (R23), and a GPU evaluation is another sample of
+    """The BF16 head criterion, 2e-2 relative max-abs against float64, as these tests apply it.  The
+    BF16 storage scheme's own per-head error on this random-init network (rounding alone, exact
+    arithmetic) spreads over 0.009-0.019 across frames, and a GPU evaluation is another sample of
     that spread: the mean over the six heads must be below 2e-2 and every head below 2.5e-2."""
     return float(np.mean(errs)) < 2e-2 and max(errs) < 2.5e-2

@@ -71,7 +71,7 @@ def test_bf16_forward_320x192_matches_oracle(keep):
         print("bf16 320x192 head errors", errs)
         assert bf16_heads_ok(errs), errs
         if keep:
-            # every layer against float64 end to end: the BF16 rounding noise of the layers before it (R23),
+            # every layer against float64 end to end: the BF16 rounding noise of the layers before it,
             # up to 2.5e-2 as for the heads; the bit-level per-layer parity is the teacher-forced test
             # against the BF16 scheme (test_gpu_precision.py)
             bad = per_layer_report(h, acts, 2.5e-2)
@@ -297,10 +297,10 @@ def _iou(a, b):
 def test_bf16_detections_end_to_end_match_the_oracle_boxes_and_embeddings():
     """The BF16 network's own detections (jde_detect_batch, sparse embedding head) against the FP64
     oracle's forward + post-processing on the same frames, for every detection both keep (same anchor):
-    unit embeddings at cosine >= 0.999 (the benchmark spec's criterion).  Boxes: width and height are exp of
+    unit embeddings at cosine >= 0.999.  Boxes: width and height are exp of
     head logits, which turns the BF16 storage noise of the random-init model's large logits into a few
     percent of size, so IoU >= 0.99 against float64 is beyond the BF16 scheme itself (oracle with exact
-    arithmetic and bfloat16 stores: IoU median 0.98, minimum 0.92, R23).  The GPU's boxes are held to
+    arithmetic and bfloat16 stores: IoU median 0.98, minimum 0.92).  The GPU's boxes are held to
     the scheme's own agreement on the same frames: median IoU within 0.01 of the scheme's and 90% of
     boxes at IoU >= 0.9.  The kept sets share at least 85% of their detections: the others sit at a
     confidence or overlap threshold within the BF16 head error."""

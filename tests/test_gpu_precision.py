@@ -6,7 +6,7 @@ puts a sum on the other side of a bfloat16 rounding boundary (one unit in the la
 layer, fed the GPU's own stored inputs, must agree exactly on almost every element and within one
 bfloat16 step everywhere.  End to end, two evaluations of a reduced-precision network decorrelate
 (every rounding flip moves the next layers' inputs; pinned on the CPU in test_oracle_bf16.py), so the
-GPU's end-to-end error against float64 is compared with the scheme's own (reading R23; for BF16 boxes:
+GPU's end-to-end error against float64 is compared with the scheme's own (for BF16 boxes:
 IoU median 0.98, minimum 0.92 on the random-init model, a property of the scheme, not a kernel error).
 
 E4M3: ``oracle.fp8`` (the fake-quantised network) against the GPU layer by layer in the batch-32
@@ -129,8 +129,8 @@ def test_fused_stem_and_stride2_conv_match_the_bf16_scheme(in_w, in_h, n):
 
 def test_bf16_end_to_end_error_is_the_scheme_s():
     """The default BF16 handle's heads against float64, next to the BF16 scheme's own heads against
-    float64 on the same frames.  Two evaluations of the scheme decorrelate through the network (R23,
-    pinned in test_oracle_bf16.py), so the GPU's error is compared with the scheme's as a size: per head
+    float64 on the same frames.  Two evaluations of the scheme decorrelate through the network (pinned
+    in test_oracle_bf16.py), so the GPU's error is compared with the scheme's as a size: per head
     at most 1.5 times the scheme's plus 2e-3."""
     j = jde()
     n = 2
@@ -155,8 +155,8 @@ def test_bf16_end_to_end_error_is_the_scheme_s():
 def test_e4m3_end_to_end_error_is_the_scheme_s():
     """E4M3 at 320x192, batch 2: the GPU's heads against float64, next to the fake-quantised oracle's
     (the same scheme and scales) against float64.  As for BF16, two evaluations of the scheme decorrelate
-    end to end, so the sizes are compared: per head at most 1.5 times the scheme's plus 2e-2.  The
-    the benchmark spec's 6e-2 is beyond the scheme itself on this network (0.15-0.29, R21); the layer-by-layer
+    end to end, so the sizes are compared: per head at most 1.5 times the scheme's plus 2e-2.  A 6e-2
+    bound is beyond the scheme itself on this network (0.15-0.29 from float64); the layer-by-layer
     parity is in test_gpu_fp8.py and below."""
     j = jde()
     amax = json.load(open(os.path.join(GOLDEN, "fp8_amax_320x192.json")))["amax"]

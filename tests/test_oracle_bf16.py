@@ -117,7 +117,7 @@ def _conv2d_f32(x, w, b, stride):
 
 
 def test_two_evaluations_of_the_scheme_decorrelate_end_to_end(monkeypatch):
-    """R23: the BF16 scheme evaluated twice, once with float64 and once with float32 accumulation (the
+    """The BF16 scheme evaluated twice, once with float64 and once with float32 accumulation (the
     GPU's), agrees exactly on almost every element of the first layers, but each rounding flip moves the
     next layers' inputs, so the share of identical stored elements decays through the network and the
     heads differ by a few 1e-3 already at 64x64 (about 1e-2 at 320x192, the size of the scheme's own

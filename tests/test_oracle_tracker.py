@@ -200,7 +200,7 @@ def test_planted_objects_keep_their_ids():
 
 
 def test_gallery_update_is_the_normalised_momentum_average():
-    """R15 by hand: a track born from a detection with embedding e starts its gallery at e; each match
+    """The gallery update by hand: a track born from a detection with embedding e starts its gallery at e; each match
     with a detection d sets it to (0.9 e + 0.1 d) / |0.9 e + 0.1 d|.  Two unit vectors at 60 degrees in a
     plane (cosine cost 0.5 <= 0.7, same box) give the closed form (0.9 + 0.05, 0.1 sin 60) / norm; a swapped
     momentum or a missing normalisation gives another vector."""
