@@ -278,6 +278,7 @@ def run_fp8(torch, jde, dev, blob, stream, table, B=32, K=20, autotune=True, spa
     jde.jde_destroy(h8)
     flops = conv_flops(table, IN_W, IN_H) * B
     peak8 = fp8_gemm_peak(torch)
+    peaks, _ = measured_peaks()
     achieved = flops / (conv_ms * 1e-3) / 1e12
     return {"fps": B * 1000.0 / ms, "ms_per_batch": ms, "batch": B, "steps": K, "graph": True,
             "autotuned_tiles_changed": changed,
@@ -286,19 +287,23 @@ def run_fp8(torch, jde, dev, blob, stream, table, B=32, K=20, autotune=True, spa
             "calibration": "amax per layer output: 64 seeded 1920x1080 uniform frames through a BF16 handle that keeps every layer output",
             "conv_ms": conv_ms, "conv_tflops": achieved,
             "fp8_peak_tflops": peak8, "conv_frac_of_fp8_peak": achieved / peak8 if peak8 else None,
-            "peak_note": "E4M3 peak measured in this run: torch._scaled_mm (cuBLASLt) E4M3 x E4M3 -> bf16 GEMM, "
-                         "8192^3, per-tensor scales, best of 10 launches",
+            "fp8_peak_derived_tflops": 2.0 * peaks["bf16_tflops"],
+            "conv_frac_of_fp8_peak_derived": achieved / (2.0 * peaks["bf16_tflops"]),
+            "peak_note": "fp8_peak_tflops: measured in this run, torch._scaled_mm (cuBLASLt) E4M3 x E4M3 -> bf16 "
+                         "GEMM, 8192^3, per-tensor scales, best of 30 launches; fp8_peak_derived_tflops: the measured "
+                         "BF16 burst peak x 2 (nominal dense E4M3 / BF16 ratio 4.5 / 2.25)",
             "detections_last_batch": n_dets, "launch_count_note": "graph replays; library launches are inside graphs"}
 
 
-def fp8_gemm_peak(torch, n=8192, reps=10):
+def fp8_gemm_peak(torch, n=8192, reps=30):
     """Dense E4M3 tensor-core peak on this GPU, TFLOP/s: the best of `reps` cuBLASLt GEMMs
-    (torch._scaled_mm, E4M3 x E4M3 -> bf16, per-tensor scales of 1) of n x n x n, timed with CUDA events."""
+    (torch._scaled_mm, E4M3 x E4M3 -> bf16, per-tensor scales of 1) of n x n x n, timed with CUDA events
+    after ten untimed ones."""
     a = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn)
     b = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn).t()
     one = torch.tensor(1.0, device="cuda")
     f = lambda: torch._scaled_mm(a, b, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
-    for _ in range(5):
+    for _ in range(10):
         f()
     torch.cuda.synchronize()
     best = float("inf")
