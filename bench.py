@@ -492,7 +492,8 @@ def main():
               for i in range(NF)]
     ratio, px, py = letterbox_geometry(SRC_W, SRC_H, IN_W, IN_H)
     soak = args.soak
-    n_heads = W + soak + K
+    K1 = 10                     # single-forward-stream steps that time the conv phase (kernel roofline)
+    n_heads = W + K1 + soak + K   # planted heads of every step up to the end of the timed region
     clips = planted_clips(B, n_heads, args.objects, anchor_table(), ratio, px, py)
     heads = [build_heads_device(torch, clips, t, dev) for t in range(n_heads)]
     cap = 256
@@ -506,99 +507,126 @@ def main():
     tracks = jde.make_tracks(*tr, cap=tcap)
     streams = list(range(B))
 
-    # Two streams (the paper's parallel post-processing, Sec. 4.3, on the device): the forward of
-    # batch t+1 runs on F while batch t is post-processed and tracked on P.  P waits for forward t;
-    # forward t+2 (which reuses the head-tensor set of batch t) waits for post-processing t.
-    F = torch.cuda.Stream(device=dev)
+    # The pipelined step.  Two forward streams F[0], F[1] over two handles with the same weights and
+    # tiles (each with its own activation buffers): batch t runs its forward on handle t % 2, so the
+    # forward of batch t+1 fills the SMs that the last wave of each layer of batch t leaves idle.  One
+    # stream P post-processes and tracks the batches in order (the paper's parallel post-processing,
+    # Sec. 4.3, on the device) with the first handle's tracker, so every video stream's tracks live in
+    # one state.  P waits for forward t; a handle's next-but-one forward (which reuses the head-tensor
+    # set of batch t) waits for post-processing t.  nf = 1 is the single-forward-stream form.
+    h2 = jde.jde_create(cfg, blob)
+    jde.jde_set_tile_choice(h2, B, IN_W, IN_H, jde.jde_tile_choice(h, B, IN_W, IN_H))
+    hs = [h, h2]
+    F = [torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)]
     P = torch.cuda.Stream(device=dev)
-    n_ev = W + args.soak + K
-    fwd_start = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
-    fwd_done = [torch.cuda.Event() for _ in range(n_ev)]
-    post_done = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
+    rows_b = torch.zeros_like(rows)
+    count_b = torch.zeros_like(count)
+    D = [dets, jde.make_dets(rows_b, count_b, None, cap=cap)]
+    fwd_start, fwd_done, post_done = {}, {}, {}
 
-    def step(t, prof=None):
-        if t >= 2:
-            F.wait_event(post_done[t - 2])
+    def step(t, nf, prof=None):
+        f = t % nf
+        hh = hs[f]
+        if t - 2 * nf in post_done:
+            F[f].wait_event(post_done[t - 2 * nf])
         if prof is not None:
-            jde.jde_set_profile_events(h, *prof)
-        fwd_start[t].record(F)
-        jde.jde_forward(h, frames[t % NF], B, SRC_W, SRC_H, IN_W, IN_H, True, F)
-        fwd_done[t].record(F)
-        P.wait_event(fwd_done[t])
-        jde.jde_postprocess(h, heads[t], B, IN_W, IN_H, SRC_W, SRC_H, dets, P)
-        jde.jde_track_step(h, streams, dets, tracks, P)
-        post_done[t].record(P)
+            jde.jde_set_profile_events(hh, *prof)
+        e = fwd_start[t] = torch.cuda.Event(enable_timing=True)
+        e.record(F[f])
+        jde.jde_forward(hh, frames[t % NF], B, SRC_W, SRC_H, IN_W, IN_H, True, F[f])
+        e = fwd_done[t] = torch.cuda.Event()
+        e.record(F[f])
+        P.wait_event(e)
+        d = D[t % 2]
+        jde.jde_postprocess(hh, heads[t % len(heads)], B, IN_W, IN_H, SRC_W, SRC_H, d, P)
+        jde.jde_track_step(h, streams, d, tracks, P)
+        e = post_done[t] = torch.cuda.Event(enable_timing=True)
+        e.record(P)
 
-    for t in range(W):
-        step(t)
-    torch.cuda.synchronize()
+    def drain():
+        torch.cuda.synchronize()
+        fwd_start.clear()
+        fwd_done.clear()
+        post_done.clear()
+
+    t = 0
+    for _ in range(W):
+        step(t, 2)
+        t += 1
+    drain()
     if args.profile_step:
-        # one step (forward, post-processing, tracker) inside the profiler range, then stop
+        # one single-stream step (forward, post-processing, tracker) inside the profiler range, then stop
         torch.cuda.profiler.start()
-        step(W)
+        step(t, 1)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
         assert jde.jde_kernel_errors(h) == 0
         jde.jde_destroy(h)
+        jde.jde_destroy(h2)
         print(json.dumps({"profile_step": True, "batch": B, "tiles": tiles}), flush=True)
         return
-    sampler = ClockSampler(local)
-    sampler.start()
-    for t in range(W, W + args.soak):      # keeps the GPU loaded while the clock sampler starts
-        step(t)
-    torch.cuda.synchronize()
-    prof = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+
+    # kernel roofline: the conv phase of single-stream steps, timed with the CUDA events the library
+    # records around the convolutions of each forward (no other forward overlaps them)
+    prof = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K1)]
     for p3 in prof:          # torch creates the CUDA event on its first record; the library re-records it
         for e in p3:
-            e.record(F)
+            e.record(F[0])
+    torch.cuda.synchronize()
+    for i in range(K1):
+        step(t, 1, prof[i])
+        t += 1
+    drain()
+    for hh in hs:
+        jde.jde_set_profile_events(hh)
+    conv_ms1 = sum(p[1].elapsed_time(p[2]) for p in prof) / K1
+    fwd_ms1 = sum(p[0].elapsed_time(p[2]) for p in prof) / K1
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    for _ in range(args.soak):      # keeps the GPU loaded while the clock sampler starts
+        step(t, 2)
+        t += 1
+    drain()
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     l0 = jde.jde_launch_count()
-    t0 = W + args.soak
-    t_start.record(F)
+    t_start.record(F[0])
+    F[1].wait_event(t_start)
     P.wait_event(t_start)
     for i in range(K):
-        step(t0 + i, prof[i])
-    F.wait_event(post_done[t0 + K - 1])
-    t_end.record(F)
+        step(t, 2)
+        t += 1
+    F[0].wait_event(post_done[t - 1])
+    t_end.record(F[0])
     torch.cuda.synchronize()
     l1 = jde.jde_launch_count()
     if dist:
         dist.barrier()
     clocks = sampler.stop()
-    jde.jde_set_profile_events(h)
-    assert jde.jde_kernel_errors(h) == 0
+    assert jde.jde_kernel_errors(h) == 0 and jde.jde_kernel_errors(h2) == 0
     total_ms = t_start.elapsed_time(t_end)
-    conv_ms = sum(p[1].elapsed_time(p[2]) for p in prof)
-    fwd_ms = sum(p[0].elapsed_time(p[2]) for p in prof)
     value, total_ms = whole_job_rate(B * K, total_ms, dist, dev)
+    drain()
 
     # latency percentiles over LAT_BATCHES more batches of the same pipelined step (outside the timed
     # region): per batch, from the start of its forward to the end of its tracker step
     step_ms = []
     if rank == 0 and args.latency_batches > 0:
         nl = args.latency_batches
-        lat0 = [torch.cuda.Event(enable_timing=True) for _ in range(nl)]
-        lat1 = [torch.cuda.Event(enable_timing=True) for _ in range(nl)]
-        lat_f = [torch.cuda.Event() for _ in range(nl)]
-        torch.cuda.synchronize()
+        t_lat = t
         for i in range(nl):
-            t = W + args.soak + (i % K)
-            if i >= 2:
-                F.wait_event(lat1[i - 2])
-            lat0[i].record(F)
-            jde.jde_forward(h, frames[i % NF], B, SRC_W, SRC_H, IN_W, IN_H, True, F)
-            lat_f[i].record(F)
-            P.wait_event(lat_f[i])
-            jde.jde_postprocess(h, heads[t], B, IN_W, IN_H, SRC_W, SRC_H, dets, P)
-            jde.jde_track_step(h, streams, dets, tracks, P)
-            lat1[i].record(P)
+            step(t, 2)
+            t += 1
         torch.cuda.synchronize()
-        step_ms = [lat0[i].elapsed_time(lat1[i]) for i in range(nl)]
+        step_ms = [fwd_start[u].elapsed_time(post_done[u]) for u in range(t_lat, t)]
+        drain()
+    F0 = F[0]
 
-    # batch sweep (the batches of the BF16 configuration), same pipelined step on n frames / n streams
+    # batch sweep (the batches of the BF16 configuration): the single-forward-stream pipelined step on
+    # n frames / n streams, one handle
     sweep = {}
     if rank == 0:
         for n in [b for b in (1, 4, 8, 16) if b <= B]:
@@ -612,20 +640,20 @@ def main():
             torch.cuda.synchronize()
             for i in range(ks + ws):
                 if i == ws:
-                    a0.record(F)
+                    a0.record(F0)
                     P.wait_event(a0)
-                t = W + args.soak + (i % K)
+                tt = (W + i) % len(heads)
                 if i >= 2:
-                    F.wait_event(ev1[i - 2])
-                ev0[i].record(F)
-                jde.jde_forward(h, frames[i % NF][:n], n, SRC_W, SRC_H, IN_W, IN_H, True, F)
-                evf[i].record(F)
+                    F0.wait_event(ev1[i - 2])
+                ev0[i].record(F0)
+                jde.jde_forward(h, frames[i % NF][:n], n, SRC_W, SRC_H, IN_W, IN_H, True, F0)
+                evf[i].record(F0)
                 P.wait_event(evf[i])
-                jde.jde_postprocess(h, [x[:n] for x in heads[t]], n, IN_W, IN_H, SRC_W, SRC_H, sub_dets, P)
+                jde.jde_postprocess(h, [x[:n] for x in heads[tt]], n, IN_W, IN_H, SRC_W, SRC_H, sub_dets, P)
                 jde.jde_track_step(h, list(range(n)), sub_dets, sub_tr, P)
                 ev1[i].record(P)
-            F.wait_event(ev1[ks + ws - 1])
-            a1.record(F)
+            F0.wait_event(ev1[ks + ws - 1])
+            a1.record(F0)
             torch.cuda.synchronize()
             lat = sorted(ev0[i].elapsed_time(ev1[i]) for i in range(ws, ws + ks))
             # device memory a handle sized for batches of n holds at this input size (the library's exact
@@ -672,10 +700,12 @@ def main():
         sweep["1_graph"] = {"fps": 1000.0 / graph_ms, "ms": graph_ms, "eager_ms": eager_ms}
         assert jde.jde_kernel_errors(h) == 0
 
-    # roofline of the convolutions (tcgen05 implicit GEMM): algorithmic FLOPs / measured conv time
+    # roofline of the convolutions (tcgen05 implicit GEMM): algorithmic FLOPs / measured conv time of the
+    # single-stream steps (each launch alone on the GPU); the pipelined aggregate is reported beside it
     flops_frame = conv_flops(table, IN_W, IN_H)
     peaks, peak_kind = measured_peaks()
-    achieved = flops_frame * B * K / (conv_ms / 1000.0) / 1e12
+    achieved = flops_frame * B / (conv_ms1 / 1000.0) / 1e12
+    agg = flops_frame * B * K / (total_ms / 1000.0) / 1e12
     # the conv phase is a few ms of dense MMA inside a step whose clocks are sampled: against the burst
     # figure (a cuBLAS GEMM timed alone) while the SM clock stays at its maximum with no power cap, the
     # sustained one (a GEMM loop under the power cap) is reported beside it
@@ -686,10 +716,16 @@ def main():
                 "traffic_unit": "bytes per step (77 conv launches), ncu dram__bytes_read.sum + dram__bytes_write.sum",
                 "traffic_source": CONV_DRAM_SOURCE,
                 "kernel": "stem_s2_kernel + conv_tc_kernel (77 launches per step, aggregated)",
+                "conv_time": f"conv phase of {K1} single-forward-stream steps, {conv_ms1:.3f} ms per step, CUDA events "
+                             "the library records around the convolutions on the launch stream",
                 "peak_kind": f"{peak_kind} bf16 burst (of measured)",
-                "peak_sustained": peak_s, "frac_sustained": achieved / peak_s}
+                "peak_sustained": peak_s, "frac_sustained": achieved / peak_s,
+                "pipelined": {"achieved": agg, "frac": agg / peak, "frac_sustained": agg / peak_s,
+                              "how": "conv FLOPs of the timed region / its wall time (two forward streams; the "
+                                     "wall time also covers the letterbox, post-processing and tracker kernels)"}}
 
-    # e2e: host frames in (pinned), tracks out to host, through the same C ABI
+    # e2e: host frames in (pinned), tracks out to host, through the same C ABI and the same two-handle
+    # pipeline: jde_forward copies each batch's frames from pinned host memory on its forward stream
     pinned = [f.cpu().pin_memory() for f in frames]
     tr_h = [np.zeros((B, tcap), np.int64), np.zeros((B, tcap, 4), np.float32), np.zeros((B, tcap), np.int32),
             np.zeros((B, tcap), np.int32), np.zeros(B, np.int32)]
@@ -697,23 +733,33 @@ def main():
     h2d = B * SRC_W * SRC_H * 3
     d2h = sum(x.nbytes for x in tr_h)
     torch.cuda.synchronize()
+
+    def fwd_host(u):
+        f = u % 2
+        if u - 4 in post_done:
+            F[f].wait_event(post_done[u - 4])
+        jde.jde_forward(hs[f], pinned[u % NF], B, SRC_W, SRC_H, IN_W, IN_H, False, F[f])
+        e = fwd_done[u] = torch.cuda.Event()
+        e.record(F[f])
+
     tt0 = time.perf_counter()
-    base = W + args.soak
-    jde.jde_forward(h, pinned[base % NF], B, SRC_W, SRC_H, IN_W, IN_H, False, F)
-    fwd_done[base].record(F)
+    base = t
+    fwd_host(base)
+    fwd_host(base + 1)
     for i in range(K):
-        t = base + i
-        if i + 1 < K:      # enqueue forward t+1 before the host waits on the tracks of t
-            if i >= 1:
-                F.wait_event(post_done[t - 1])
-            jde.jde_forward(h, pinned[(t + 1) % NF], B, SRC_W, SRC_H, IN_W, IN_H, False, F)
-            fwd_done[t + 1].record(F)
-        P.wait_event(fwd_done[t])
-        jde.jde_postprocess(h, heads[t], B, IN_W, IN_H, SRC_W, SRC_H, dets, P)
-        jde.jde_track_step(h, streams, dets, tracks_h, P)     # host outputs: synchronises P
-        post_done[t].record(P)
+        u = base + i
+        P.wait_event(fwd_done[u])
+        d = D[u % 2]
+        jde.jde_postprocess(hs[u % 2], heads[u % len(heads)], B, IN_W, IN_H, SRC_W, SRC_H, d, P)
+        e = post_done[u] = torch.cuda.Event()
+        e.record(P)
+        if i + 2 < K:      # enqueue forward u+2 before the host waits on the tracks of u
+            fwd_host(u + 2)
+        jde.jde_track_step(h, streams, d, tracks_h, P)     # host outputs: synchronises P
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - tt0
+    t = base + K
+    drain()
     e2e = {"value": world * B * K / e2e_s, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     # plain FP32 batch-1 comparator (no graph): same step, one frame / one stream
@@ -752,11 +798,11 @@ def main():
 
     sparse_cmp = None
     if rank == 0 and not args.no_fp8:
-        sparse_cmp = run_sparse_compare(torch, jde, dev, blob, F)
+        sparse_cmp = run_sparse_compare(torch, jde, dev, blob, F0)
 
     fp8 = None
     if not args.no_fp8 and rank == 0:
-        fp8 = run_fp8(torch, jde, dev, blob, F, table, autotune=not args.no_autotune)
+        fp8 = run_fp8(torch, jde, dev, blob, F0, table, autotune=not args.no_autotune)
 
     serving = None
     if args.serve_seconds > 0 and rank == 0:
@@ -781,10 +827,13 @@ def main():
             "latency_ms": {"p50": srt[len(srt) // 2] if srt else None,
                            "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))] if srt else None,
                            "batches": len(srt),
-                           "what": "per batch, from the start of its forward to the end of its tracker step "
-                                   "(two-stream pipeline: post-processing of batch t overlaps the forward of t+1), "
-                                   "over batches run after the timed region"},
-            "stages_ms_per_step": {"forward": fwd_ms / K, "convs": conv_ms / K},
+                           "what": "per batch, from the start of its forward to the end of its tracker step, "
+                                   "in the timed pipeline (two forward streams over two handles, batches "
+                                   "alternating; one stream post-processes and tracks them in order), over "
+                                   "batches run after the timed region"},
+            "pipeline": "two forward streams over two handles (same weights and tiles), batch t on handle t % 2; "
+                        "post-processing and tracker steps in order on a third stream with one tracker state",
+            "stages_ms_per_step_single_stream": {"forward": fwd_ms1, "convs": conv_ms1},
             "fp32_plain_batch1": fp32,
             "batch_sweep": sweep,
             "fp8_batch32": fp8,
@@ -799,6 +848,7 @@ def main():
         }
         print(json.dumps(line), flush=True)
     jde.jde_destroy(h)
+    jde.jde_destroy(h2)
     if dist:
         dist.destroy_process_group()
 
