@@ -95,6 +95,64 @@ __global__ void letterbox_bf16x4_kernel(const uint8_t* frames, int n, int src_w,
   *reinterpret_cast<uint2*>(static_cast<__nv_bfloat16*>(out.ptr) + tview_off(out, f, y, x)) = q;
 }
 
+// bf16 RGB0 as above, one block per (output row, frame): the block copies the two source rows the
+// output row samples into shared memory with coalesced loads (16-byte, 4-byte or 1-byte units, the
+// widest that every source row's start allows), then blends its pixels from there.  The arithmetic is
+// sample()'s, term for term.
+constexpr int LB_THREADS = 256;
+
+__global__ void __launch_bounds__(LB_THREADS) letterbox_bf16x4_rows_kernel(const uint8_t* frames, int src_w,
+                                                                           int src_h, const LbAxis* xs,
+                                                                           const LbAxis* ys, TView out, int unit) {
+  extern __shared__ __align__(16) uint8_t srow[];   // [2][row_bytes]
+  const int f = blockIdx.y, y = blockIdx.x;
+  const LbAxis ay = ys[y];
+  __nv_bfloat16* const o = static_cast<__nv_bfloat16*>(out.ptr);
+  const int row_bytes = src_w * 3;
+  if (ay.inside) {
+    const uint8_t* img = frames + (size_t)f * src_w * src_h * 3;
+    const uint8_t* rows[2] = {img + (size_t)ay.i0 * row_bytes, img + (size_t)ay.i1 * row_bytes};
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      uint8_t* dst = srow + r * row_bytes;
+      if (unit == 16) {
+        const uint4* src = reinterpret_cast<const uint4*>(rows[r]);
+        for (int w = threadIdx.x; w < row_bytes / 16; w += LB_THREADS)
+          reinterpret_cast<uint4*>(dst)[w] = __ldg(src + w);
+      } else if (unit == 4) {
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(rows[r]);
+        for (int w = threadIdx.x; w < row_bytes / 4; w += LB_THREADS)
+          reinterpret_cast<uint32_t*>(dst)[w] = __ldg(src + w);
+      } else {
+        for (int b = threadIdx.x; b < row_bytes; b += LB_THREADS) dst[b] = __ldg(rows[r] + b);
+      }
+    }
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < out.w; x += LB_THREADS) {
+    float v[3];
+    const LbAxis ax = xs[x];
+    if (!(ax.inside && ay.inside)) {
+      v[0] = v[1] = v[2] = 0.5f;
+    } else {
+      const uint8_t* r0 = srow;
+      const uint8_t* r1 = srow + row_bytes;
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        const float p00 = r0[ax.i0 * 3 + ch], p01 = r0[ax.i1 * 3 + ch];
+        const float p10 = r1[ax.i0 * 3 + ch], p11 = r1[ax.i1 * 3 + ch];
+        const float top = p00 * (1.f - ax.f) + p01 * ax.f;
+        const float bot = p10 * (1.f - ax.f) + p11 * ax.f;
+        v[ch] = (top * (1.f - ay.f) + bot * ay.f) / 255.f;
+      }
+    }
+    __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
+    __nv_bfloat162 b = __floats2bfloat162_rn(v[2], 0.f);
+    *reinterpret_cast<uint2*>(o + tview_off(out, f, y, x)) =
+        make_uint2(*reinterpret_cast<uint32_t*>(&a), *reinterpret_cast<uint32_t*>(&b));
+  }
+}
+
 }  // namespace
 
 void letterbox_tables_launch(LbAxis* xs, LbAxis* ys, int src_w, int src_h, int dst_w, int dst_h, double r, int nw,
@@ -113,7 +171,17 @@ void letterbox_f32_launch(const uint8_t* frames, int n, int src_w, int src_h, co
 
 void letterbox_bf16x4_launch(const uint8_t* frames, int n, int src_w, int src_h, const LbAxis* xs,
                              const LbAxis* ys, TView out, cudaStream_t st) {
-  const long long total = (long long)n * out.h * out.w;
+  // the row kernel holds two whole source rows in shared memory (up to 48 KB: src_w <= 8192)
+  const size_t smem = (size_t)2 * src_w * 3;
   jde_count_launch();
+  if (smem <= 48 * 1024 && out.h <= 65535 && n <= 65535) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(frames);
+    const size_t rb = (size_t)src_w * 3;
+    const int unit = (a % 16 == 0 && rb % 16 == 0) ? 16 : (a % 4 == 0 && rb % 4 == 0) ? 4 : 1;
+    dim3 grid((unsigned)out.h, (unsigned)n);
+    letterbox_bf16x4_rows_kernel<<<grid, LB_THREADS, smem, st>>>(frames, src_w, src_h, xs, ys, out, unit);
+    return;
+  }
+  const long long total = (long long)n * out.h * out.w;
   letterbox_bf16x4_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(frames, n, src_w, src_h, xs, ys, out);
 }
