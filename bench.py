@@ -56,6 +56,7 @@ def parse():
                    help="serving run: seconds of Poisson arrivals measured after a 2 s warm-up (0: skip)")
     p.add_argument("--serve-budget-gb", type=float, default=64.0, help="serving run: device memory budget")
     p.add_argument("--no-fp8", action="store_true", help="skip the E4M3 batch-32 line")
+    p.add_argument("--no-jpeg", action="store_true", help="skip the compressed-frame (device decode) e2e line")
     p.add_argument("--no-autotune", action="store_true", help="default tile rule instead of jde_autotune")
     p.add_argument("--profile-step", action="store_true",
                    help="after the warm-up, run one step inside cudaProfilerStart/Stop (for ncu --profile-from-start "
@@ -351,6 +352,102 @@ def fp8_gemm_peak(torch, n=8192, reps=30):
         best = min(best, e0.elapsed_time(e1))
     del a, b
     return 2.0 * n * n * n / (best * 1e-3) / 1e12
+
+
+def run_jpeg_e2e(torch, jde, dev, hs, F, P, D, heads, tracks_h, streams, B, K, post_done, fwd_done, t0):
+    """The pipelined step fed by Motion-JPEG bitstreams from host memory: per batch, the decoder of its
+    forward stream decodes B frames into that handle's device frame buffer, then forward, post-processing
+    and tracker step (host track outputs) as in the e2e line.  Also the decoder alone: B frames per
+    call, one stream, CUDA events."""
+    import synth
+    try:
+        decs = [jde.jde_decoder_create(dev.index or 0, B, True) for _ in range(2)]
+    except jde.JdeError as e:
+        return {"unavailable": f"nvJPEG: {e}"}
+    backend = {1: "hardware JPEG engines", 2: "GPU-assisted hybrid"}.get(jde.jde_decoder_backend(decs[0]), "?")
+    src = torch.from_numpy(synth.frames_smooth(3000, B, SRC_H, SRC_W)).to(dev)
+    bits = jde.jde_encode_jpeg(decs[0], src, B, SRC_W, SRC_H, 90, F[0])
+    del src
+    dframes = [torch.empty((B, SRC_H, SRC_W, 3), dtype=torch.uint8, device=dev) for _ in range(2)]
+    torch.cuda.synchronize()
+    # decoder alone
+    for _ in range(3):
+        jde.jde_decode_jpeg(decs[0], bits, SRC_W, SRC_H, dframes[0], F[0])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nd = 10
+    tt = time.perf_counter()
+    e0.record(F[0])
+    for _ in range(nd):
+        jde.jde_decode_jpeg(decs[0], bits, SRC_W, SRC_H, dframes[0], F[0])
+    e1.record(F[0])
+    torch.cuda.synchronize()
+    dec_wall = (time.perf_counter() - tt) / nd
+    dec_ms = e0.elapsed_time(e1) / nd
+
+    # A decode call returns when its batch is decoded, so each forward stream has a host thread that
+    # decodes its batches ahead: batch u is decoded (on F[u % 2]) once forward u - 2, which read the
+    # same frame buffer, has been enqueued before it on that stream; the main thread enqueues forward u
+    # once decode u has returned.  ctypes releases the GIL during the calls.
+    import threading
+    decoded = {}
+    fwd_enq = {}
+
+    def ev(dct, u):
+        return dct.setdefault(u, threading.Event())
+
+    def decoder_loop(f, first, last):
+        for u in range(first + f, last, 2):
+            if u - 2 >= first and not ev(fwd_enq, u - 2).wait(60):
+                return
+            jde.jde_decode_jpeg(decs[f], bits, SRC_W, SRC_H, dframes[f], F[f])
+            ev(decoded, u).set()
+
+    def fwd_jpeg(u):
+        f = u % 2
+        if not ev(decoded, u).wait(60):
+            raise RuntimeError("decode thread stalled")
+        if u - 4 in post_done:
+            F[f].wait_event(post_done[u - 4])
+        jde.jde_forward(hs[f], dframes[f], B, SRC_W, SRC_H, IN_W, IN_H, True, F[f])
+        e = fwd_done[u] = torch.cuda.Event()
+        e.record(F[f])
+        ev(fwd_enq, u).set()
+
+    def run(first, n, timed):
+        threads = [threading.Thread(target=decoder_loop, args=(f, first, first + n), daemon=True) for f in range(2)]
+        for th in threads:
+            th.start()
+        fwd_jpeg(first)
+        if n > 1:
+            fwd_jpeg(first + 1)
+        for i in range(n):
+            u = first + i
+            P.wait_event(fwd_done[u])
+            d = D[u % 2]
+            jde.jde_postprocess(hs[u % 2], heads[u % len(heads)], B, IN_W, IN_H, SRC_W, SRC_H, d, P)
+            e = post_done[u] = torch.cuda.Event()
+            e.record(P)
+            if i + 2 < n:
+                fwd_jpeg(u + 2)
+            jde.jde_track_step(hs[0], streams, d, tracks_h, P)
+        torch.cuda.synchronize()
+        for th in threads:
+            th.join(60)
+
+    run(t0, 4, False)               # warm both decoders on their streams
+    base = t0 + 4
+    tt0 = time.perf_counter()
+    run(base, K, True)
+    secs = time.perf_counter() - tt0
+    for d_ in decs:
+        jde.jde_decoder_destroy(d_)
+    nbytes = sum(len(b) for b in bits)
+    return {"value": B * K / secs, "unit": "frames/s", "h2d_bytes_per_step": nbytes,
+            "decoder": backend, "jpeg_quality": 90, "mean_bitstream_bytes": nbytes / B,
+            "decode_only": {"fps": B * 1000.0 / dec_ms, "ms_per_batch": dec_ms, "host_ms_per_call": dec_wall * 1000},
+            "what": "Motion-JPEG bitstreams (synth.frames_smooth, 1920x1080) in host memory decoded on the device "
+                    "into each forward stream's frame buffer, then the pipelined detect + track step, tracks to host"}
 
 
 def run_sparse_compare(torch, jde, dev, blob, stream, B=16, K=10):
@@ -797,6 +894,17 @@ def main():
     drain()
     e2e = {"value": world * B * K / e2e_s, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    # e2e from compressed frames: Motion-JPEG bitstreams in host memory (camera-like synthetic frames,
+    # quality 90, 4:2:0), decoded on the device (jde_decode_jpeg) on each forward stream into that
+    # handle's frame buffer, then the same pipeline; only the bitstreams cross the host link
+    jpeg = None
+    if rank == 0 and not args.no_jpeg:
+        jpeg = run_jpeg_e2e(torch, jde, dev, hs, F, P, D, heads, tracks_h, streams, B, K, post_done, fwd_done, t)
+        if "value" in jpeg:
+            jpeg["d2h_bytes_per_step"] = d2h
+        t += K + 4
+        drain()
+
     # plain FP32 batch-1 comparator (no graph): same step, one frame / one stream
     fp32 = None
     if not args.no_fp32 and rank == 0:
@@ -878,6 +986,7 @@ def main():
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "e2e_jpeg": jpeg,
             "gpu_launches": int(l1 - l0),
             "clocks": clocks,
         }

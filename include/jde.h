@@ -439,6 +439,44 @@ jde_status jde_server_device_bytes(jde_server* s, size_t* charged, size_t* held)
 /* Counters of the server: batches launched eagerly, graphs captured, graph replays. */
 jde_status jde_server_stats(jde_server* s, long long* eager, long long* captured, long long* replays);
 
+/* ---------------------------------------------------------------------------------------------
+ * Device decode of compressed frames (the capture stage of Sec. 4.4, on the GPU, for Motion-JPEG
+ * video streams).  A decoder turns baseline JPEG bitstreams in host memory into interleaved 8-bit
+ * RGB frames in device memory (n x h x w x 3, the layout jde_forward and jde_submit read) with
+ * nvJPEG: on the GPU's JPEG decode engines (JDE_DECODE_HARDWARE) when they are available, else with
+ * the GPU-assisted hybrid backend (JDE_DECODE_GPU_HYBRID).  libnvjpeg is loaded at run time; where
+ * it is absent every decoder call returns JDE_ERR_UNSUPPORTED.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct jde_decoder jde_decoder;
+enum { JDE_DECODE_HARDWARE = 1, JDE_DECODE_GPU_HYBRID = 2 };
+
+/* Create a decoder on `device` for batches of up to max_batch frames (1..1024); hardware = 1 asks
+ * for the JPEG engines.  JDE_ERR_UNSUPPORTED when nvJPEG cannot be loaded or set up. */
+jde_status jde_decoder_create(int device, int max_batch, int hardware, jde_decoder** out);
+
+/* Release the decoder (synchronises its device).  NULL is a no-op. */
+void jde_decoder_destroy(jde_decoder* d);
+
+/* Message of the last failed call on d. */
+const char* jde_decoder_last_error(jde_decoder* d);
+
+/* The backend in use: JDE_DECODE_HARDWARE or JDE_DECODE_GPU_HYBRID (0 for NULL). */
+int jde_decoder_backend(jde_decoder* d);
+
+/* Decode n (1..max_batch) JPEG bitstreams (host pointers and lengths; each must be a 3-component
+ * w x h image, checked on the host from its headers before any device work: JDE_ERR_INVALID_ARG
+ * otherwise) into frames (device, n x h x w x 3 uint8, frames contiguous) on `stream`.  The
+ * bitstreams must stay valid until the call returns. */
+jde_status jde_decode_jpeg(jde_decoder* d, const uint8_t* const* bitstreams, const size_t* lengths, int n, int w,
+                           int h, uint8_t* frames, void* stream);
+
+/* Encode n frames (device, n x h x w x 3 uint8 RGB) as baseline JPEG with 4:2:0 chroma subsampling at
+ * `quality` (1..100) into out[i] (host buffers; lengths[i] holds each buffer's capacity on entry and
+ * the bitstream's length on return).  A buffer too small returns JDE_ERR_CAPACITY with the length it
+ * needs in lengths[i].  Synchronises `stream`.  For making synthetic compressed streams. */
+jde_status jde_encode_jpeg(jde_decoder* d, const uint8_t* frames, int n, int w, int h, int quality,
+                           uint8_t* const* out, size_t* lengths, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

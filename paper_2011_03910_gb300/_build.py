@@ -11,7 +11,7 @@ ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libjde.so")
 SOURCES = ["jde.cu", "conv_simt.cu", "conv_tc.cu", "conv_fused.cu", "pre.cu", "post.cu", "track.cu",
-           "post_noalloc.cu", "server.cu"]
+           "post_noalloc.cu", "server.cu", "decode.cu"]
 HEADERS = ["common.cuh", "internal.h", "track.h"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",

@@ -110,6 +110,12 @@ _sig = {
     "jde_server_group_cost": (C.c_int, [C.POINTER(jde_server_config), C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
     "jde_server_device_bytes": (C.c_int, [_P, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
     "jde_server_stats": (C.c_int, [_P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+    "jde_decoder_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(_P)]),
+    "jde_decoder_destroy": (None, [_P]),
+    "jde_decoder_last_error": (C.c_char_p, [_P]),
+    "jde_decoder_backend": (C.c_int, [_P]),
+    "jde_decode_jpeg": (C.c_int, [_P, _P, C.POINTER(C.c_size_t), C.c_int, C.c_int, C.c_int, _P, _P]),
+    "jde_encode_jpeg": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_int, _P, C.POINTER(C.c_size_t), _P]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(lib, _name)
@@ -394,3 +400,54 @@ def jde_server_stats(s) -> tuple[int, int, int]:
     e, c, r = C.c_longlong(), C.c_longlong(), C.c_longlong()
     _check_server(s, lib.jde_server_stats(s, C.byref(e), C.byref(c), C.byref(r)))
     return e.value, c.value, r.value
+
+
+# ----------------------------------------------------------------------------- device decode
+JDE_DECODE_HARDWARE, JDE_DECODE_GPU_HYBRID = 1, 2
+
+
+def _check_decoder(d, status):
+    if status != JDE_OK:
+        raise JdeError(status, lib.jde_decoder_last_error(d).decode(errors="replace") if d else "decoder")
+
+
+def jde_decoder_create(device=0, max_batch=16, hardware=True):
+    out = _P()
+    st = lib.jde_decoder_create(device, max_batch, 1 if hardware else 0, C.byref(out))
+    if st != JDE_OK:
+        raise JdeError(st, "jde_decoder_create (nvJPEG unavailable or set-up failed)")
+    return out
+
+
+def jde_decoder_destroy(d) -> None:
+    lib.jde_decoder_destroy(d)
+
+
+def jde_decoder_backend(d) -> int:
+    return int(lib.jde_decoder_backend(d))
+
+
+def jde_decode_jpeg(d, bitstreams, w, h, frames, stream=None) -> None:
+    """bitstreams: list of host byte buffers (bytes or uint8 numpy arrays); frames: device tensor
+    [n, h, w, 3] uint8."""
+    n = len(bitstreams)
+    arrs = [np.frombuffer(b, np.uint8) if isinstance(b, (bytes, bytearray)) else b for b in bitstreams]
+    ptrs = (_P * n)(*[a.ctypes.data for a in arrs])
+    lens = (C.c_size_t * n)(*[a.nbytes for a in arrs])
+    _check_decoder(d, lib.jde_decode_jpeg(d, ptrs, lens, n, w, h, ptr(frames), stream_ptr(stream)))
+
+
+def jde_encode_jpeg(d, frames, n, w, h, quality=90, stream=None):
+    """Encode n device frames [n, h, w, 3] uint8; returns a list of n uint8 numpy bitstreams."""
+    cap = max(1 << 16, w * h * 3 // 2)
+    for _ in range(3):
+        bufs = [np.empty(cap, np.uint8) for _ in range(n)]
+        ptrs = (_P * n)(*[b.ctypes.data for b in bufs])
+        lens = (C.c_size_t * n)(*([cap] * n))
+        st = lib.jde_encode_jpeg(d, ptr(frames), n, w, h, quality, ptrs, lens, stream_ptr(stream))
+        if st == 4:        # JDE_ERR_CAPACITY: one frame needs a larger buffer
+            cap = max(int(lens[i]) for i in range(n)) + 1024
+            continue
+        _check_decoder(d, st)
+        return [bufs[i][:int(lens[i])].copy() for i in range(n)]
+    raise JdeError(4, "jde_encode_jpeg: bitstream buffers")

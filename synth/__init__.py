@@ -53,6 +53,33 @@ def frames_uniform(seed: int, n: int, h: int, w: int, first: int = 0) -> np.ndar
     return out
 
 
+def frames_smooth(seed: int, n: int, h: int, w: int, first: int = 0, waves: int = 6, noise: float = 3.0) -> np.ndarray:
+    """``n`` uint8 RGB frames ``[n, h, w, 3]`` with the spatial structure of camera frames rather than
+    of noise (for compressed-stream inputs, whose size and decode cost depend on the content): per
+    channel a mean level ~ U(60, 190) plus ``waves`` plane waves of amplitude ~ U(10, 35) and spatial
+    period ~ U(40, 600) px in a random direction, plus N(0, ``noise``) per pixel, rounded and clipped to
+    [0, 255].  Frame ``i`` is drawn from stream ``(seed, first + i, 7)``.
+    """
+    out = np.empty((n, h, w, 3), dtype=np.uint8)
+    x = np.arange(w, dtype=np.float64)
+    y = np.arange(h, dtype=np.float64)
+    for i in range(n):
+        g = _rng(seed, first + i, 7)
+        img = np.empty((h, w, 3), np.float32)
+        for c in range(3):
+            v = np.full((h, w), g.uniform(60.0, 190.0), np.float64)
+            for _ in range(waves):
+                amp, period, ang, ph = g.uniform(10, 35), g.uniform(40, 600), g.uniform(0, np.pi), g.uniform(0, 2 * np.pi)
+                k = 2 * np.pi / period
+                a = k * np.cos(ang) * x + ph           # cos(a + b) = cos a cos b - sin a sin b: separable
+                b = k * np.sin(ang) * y
+                v += amp * (np.outer(np.cos(b), np.cos(a)) - np.outer(np.sin(b), np.sin(a)))
+            v += g.normal(0.0, noise, (h, w))
+            img[..., c] = v
+        out[i] = np.clip(np.rint(img), 0, 255).astype(np.uint8)
+    return out
+
+
 # --------------------------------------------------------------------------- weights
 def load_tobj_shift() -> list:
     """Per-(detection head, anchor) shift added to the objectness-logit bias.

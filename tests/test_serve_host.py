@@ -135,3 +135,17 @@ def test_estimate_accounts_for_in_place_stages_the_fused_stem_and_the_sparse_emb
     dense = sum(2 * _act_bytes(n, sizes[l], 512, 4) for l in emb)
     copies = sum(2 * _act_bytes(n, sizes[l], table[l][0], 2) for l in emb)
     assert est(0, 0) - est(0, 1) == dense - copies
+
+
+def test_smooth_frames_are_seeded_and_structured():
+    """synth.frames_smooth: the same seed gives the same frames, other seeds others; neighbouring pixels
+    are close (structure, unlike uniform noise)."""
+    import synth
+    a = synth.frames_smooth(3, 2, 64, 96)
+    b = synth.frames_smooth(3, 2, 64, 96)
+    c = synth.frames_smooth(4, 2, 64, 96)
+    assert a.shape == (2, 64, 96, 3) and a.dtype == np.uint8
+    assert np.array_equal(a, b) and not np.array_equal(a, c)
+    step = np.abs(np.diff(a.astype(int), axis=2)).mean()
+    noise = np.abs(np.diff(synth.frames_uniform(3, 2, 64, 96).astype(int), axis=2)).mean()
+    assert step < 6 and noise > 60
