@@ -357,6 +357,10 @@ typedef struct {
   int collect_net_heads;     /* 1: the network's three detection maps of each frame are kept and can be
                                 returned through jde_frame_out.net_det */
   int use_graphs;            /* 1: replay each batch size's launch sequence as a CUDA graph */
+  int prewarm;               /* 1: a new group runs every batch size it can see (1 .. min(max_batch,
+                                max_streams_per_group)) once on zeroed inputs and captures its graph
+                                before its first stream is admitted, so no set-up or capture delays a
+                                served batch; its tracker slots are reset afterwards */
 } jde_server_config;
 
 /* Host buffers a frame's results are written to when jde_poll returns it (each optional, NULL to
@@ -383,7 +387,7 @@ typedef struct {
 } jde_frame_result;
 
 /* Fill *cfg with defaults: jde_default_config for the groups, 1920x1080 sources, 16 streams per group,
- * budget 64 GiB, det_cap 256, track_cap 256, network heads, no collection, graphs on. */
+ * budget 64 GiB, det_cap 256, track_cap 256, network heads, no collection, graphs on, prewarm on. */
 void jde_default_server_config(jde_server_config* cfg);
 
 /* Create a server (no device memory until a stream is opened).  `weights` is the blob of

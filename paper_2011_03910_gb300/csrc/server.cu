@@ -261,6 +261,61 @@ jde_status batch_sequence(jde_server* s, Group* g, int n, const std::vector<int>
   return JDE_OK;
 }
 
+// The CUDA graph of the group's batch of n frames, captured from batch_sequence if it is not there yet.
+jde_status ensure_graph(jde_server* s, Group* g, int n, const std::vector<int>& ids) {
+  if (g->graphs.count(n)) return JDE_OK;
+  cudaGraph_t graph = nullptr;
+  S_CUDA(s, cudaStreamBeginCapture(g->st, cudaStreamCaptureModeThreadLocal));
+  jde_status st = batch_sequence(s, g, n, ids);
+  const cudaError_t ce = cudaStreamEndCapture(g->st, &graph);
+  if (st != JDE_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (ce != cudaSuccess) return sfail(s, JDE_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce));
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) return sfail(s, JDE_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ie));
+  g->graphs[n] = exec;
+  s->captured += 1;
+  return JDE_OK;
+}
+
+// A new group runs every batch size it can see once (1 .. min(max_batch, tracker slots)) on zeroed
+// inputs, with slots 0 .. n-1, and captures its graph, so no plan, scratch allocation or capture
+// happens while streams are served; then it clears the error word and resets the slots it used.
+jde_status prewarm_group(jde_server* s, Group* g) {
+  const int B = s->cfg.group.max_batch < s->cfg.max_streams_per_group ? s->cfg.group.max_batch
+                                                                        : s->cfg.max_streams_per_group;
+  const size_t fbytes = (size_t)s->cfg.src_w * s->cfg.src_h * 3;
+  S_CUDA(s, cudaMemsetAsync(g->frames, 0, (size_t)B * fbytes, g->st));
+  for (int k = 0; k < 6 && s->cfg.caller_heads; ++k)
+    S_CUDA(s, cudaMemsetAsync(g->heads[k], 0, (size_t)B * g->head_bytes[k], g->st));
+  for (int n = 1; n <= B; ++n) {
+    std::vector<int> ids(n);
+    for (int i = 0; i < n; ++i) ids[i] = g->h_slots[i] = i;
+    S_CUDA(s, cudaMemcpyAsync(g->d_slots, g->h_slots, sizeof(int) * n, cudaMemcpyHostToDevice, g->st));
+    jde_status st = batch_sequence(s, g, n, ids);
+    if (st != JDE_OK) return st;
+    g->warmed[n] += 1;
+    if (s->cfg.use_graphs) {
+      st = ensure_graph(s, g, n, ids);
+      if (st != JDE_OK) return st;
+    }
+    S_CUDA(s, cudaStreamSynchronize(g->st));   // the pinned slot array is rewritten for the next n
+  }
+  int word = 0;
+  jde_status st = jde_kernel_errors(g->h, &word, g->st);
+  if (st != JDE_OK) return sfail(s, st, "error word: %s", jde_last_error(g->h));
+  for (int i = 0; i < B; ++i) {
+    st = jde_stream_reset(g->h, i, g->st);
+    if (st != JDE_OK) return sfail(s, st, "reset: %s", jde_last_error(g->h));
+  }
+  S_CUDA(s, cudaStreamSynchronize(g->st));
+  return JDE_OK;
+}
+
 jde_status launch_batch(jde_server* s, Group* g) {
   Batch b;
   std::deque<Pending> rest;
@@ -294,25 +349,9 @@ jde_status launch_batch(jde_server* s, Group* g) {
   }
   S_CUDA(s, cudaMemcpyAsync(g->d_slots, g->h_slots, sizeof(int) * n, cudaMemcpyHostToDevice, g->st));
   if (s->cfg.use_graphs && g->warmed[n] >= 1) {
-    auto it = g->graphs.find(n);
-    if (it == g->graphs.end()) {
-      cudaGraph_t graph = nullptr;
-      S_CUDA(s, cudaStreamBeginCapture(g->st, cudaStreamCaptureModeThreadLocal));
-      jde_status st = batch_sequence(s, g, n, ids);
-      const cudaError_t ce = cudaStreamEndCapture(g->st, &graph);
-      if (st != JDE_OK) {
-        if (graph) cudaGraphDestroy(graph);
-        return st;
-      }
-      if (ce != cudaSuccess) return sfail(s, JDE_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce));
-      cudaGraphExec_t exec = nullptr;
-      const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
-      cudaGraphDestroy(graph);
-      if (ie != cudaSuccess) return sfail(s, JDE_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ie));
-      it = g->graphs.emplace(n, exec).first;
-      s->captured += 1;
-    }
-    S_CUDA(s, cudaGraphLaunch(it->second, g->st));
+    jde_status st = ensure_graph(s, g, n, ids);
+    if (st != JDE_OK) return st;
+    S_CUDA(s, cudaGraphLaunch(g->graphs[n], g->st));
     s->replays += 1;
   } else {
     jde_status st = batch_sequence(s, g, n, ids);
@@ -414,6 +453,7 @@ void jde_default_server_config(jde_server_config* c) {
   c->caller_heads = 0;
   c->collect_net_heads = 0;
   c->use_graphs = 1;
+  c->prewarm = 1;
 }
 
 jde_status jde_server_create(const jde_server_config* cfg, const void* weights, size_t nbytes, jde_server** out) {
@@ -472,6 +512,13 @@ jde_status jde_stream_open(jde_server* s, int in_w, int in_h, int* stream_id) {
                    s->cfg.hbm_budget_bytes - s->used, s->cfg.hbm_budget_bytes);
     st = group_new(s, in_w, in_h, &g);
     if (st != JDE_OK) return st;
+    if (s->cfg.prewarm) {
+      st = prewarm_group(s, g);
+      if (st != JDE_OK) {
+        group_free(g);
+        return st;
+      }
+    }
     g->charged = cost;
     s->used += cost;
     s->groups[key] = g;

@@ -58,7 +58,8 @@ _P = C.c_void_p
 class jde_server_config(C.Structure):
     _fields_ = [("group", jde_config), ("src_w", C.c_int), ("src_h", C.c_int), ("max_streams_per_group", C.c_int),
                 ("hbm_budget_bytes", C.c_size_t), ("det_cap", C.c_int), ("track_cap", C.c_int),
-                ("caller_heads", C.c_int), ("collect_net_heads", C.c_int), ("use_graphs", C.c_int)]
+                ("caller_heads", C.c_int), ("collect_net_heads", C.c_int), ("use_graphs", C.c_int),
+                ("prewarm", C.c_int)]
 
 
 class jde_frame_out(C.Structure):

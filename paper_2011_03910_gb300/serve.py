@@ -97,7 +97,7 @@ class Server:
 
     def __init__(self, jde, torch, device, blob, budget_bytes, max_batch=16, max_streams_per_group=16,
                  det_cap=256, track_cap=256, precision=None, caller_heads=False, collect_net_heads=False,
-                 use_graphs=True):
+                 use_graphs=True, prewarm=True):
         self.jde, self.torch, self.device = jde, torch, device
         cfg = jde.jde_default_server_config()
         cfg.group.precision = jde.JDE_BF16 if precision is None else precision
@@ -110,6 +110,7 @@ class Server:
         cfg.caller_heads = int(caller_heads)
         cfg.collect_net_heads = int(collect_net_heads)
         cfg.use_graphs = int(use_graphs)
+        cfg.prewarm = int(prewarm)
         self.cfg = cfg
         self.det_cap, self.track_cap = det_cap, track_cap
         self.caller_heads, self.collect_net_heads = caller_heads, collect_net_heads
