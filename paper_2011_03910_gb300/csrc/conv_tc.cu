@@ -86,7 +86,9 @@ struct TcCfg {
   static constexpr int NSUB = SWC / SUB;
   static constexpr int SUB_BYTES = 128 * SUB * 2;
   static constexpr int C_BYTES = Q ? 128 * SWC : NSUB * SUB_BYTES;   // one staging tile (one epilogue pass)
-  static constexpr int SDEPTH = 2;                      // staging tiles per epilogue group
+  // staging tiles per epilogue group (flat windows of 128-byte rows: one, for the windows' room)
+  static constexpr int SDEPTH = (WM && BKC == 64) ? 1 : 2;
+  static constexpr uint32_t WROW = BKC * 2;             // mode 4: bytes per window row (one k-block)
   static constexpr int BIAS_BYTES = 2 * BN * 4 * (Q ? 2 : 1);   // per epilogue group: bias (and E4M3 scale) slice
   static constexpr int BAR_BYTES = 768;                 // mbarriers + TMEM address slot
   static constexpr int SMEM =
@@ -401,7 +403,7 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
       uint32_t s = 0, ph = 0, nb = 0, w = 0, wph = 0, nw = 0;   // ring slots, phases, loads issued
       const uint32_t full_leader0 = CG == 2 ? mapa_rank(smem_u32(&full[0]), 0) : 0u;
       const uint32_t wfull_leader0 = CG == 2 ? mapa_rank(smem_u32(&win_full[0]), 0) : 0u;
-      const uint32_t box_bytes = (uint32_t)a.whb * 64u;
+      const uint32_t box_bytes = (uint32_t)a.whb * Cfg::WROW;
       bool ok = true;
       for (int u = u0; ok && u < nunits && !aborted(&s_abort); u += ustep) {
         const TileCoord tc = tile_coord(a, unit_tile<CG>(a, u, rank), BN);
@@ -565,7 +567,8 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
         }
         if constexpr (WM != 0) {
           // mode 4: per k-block one window; tap (ky, kx) starts ky * Wp + kx rows into it
-          const uint64_t w_base = smem_desc(smem_u32(sWin), 8u * 64u, 4u);   // 64-byte rows, 64-byte swizzle
+          // window rows of WROW bytes (64: 64-byte swizzle, 128: 128-byte swizzle), 8-row groups
+          const uint64_t w_base = smem_desc(smem_u32(sWin), 8u * Cfg::WROW, Cfg::LAYOUT);
           bool wok = true;
           for (int cb = 0; cb < a.cin_blocks; ++cb) {
             if (!mbar_wait(&win_full[w4], w4ph)) {
@@ -581,13 +584,14 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
                 break;
               }
               tc_fence_after();
-              const uint64_t ad_t = desc_add(wd, (uint32_t)((tap / 3) * a.Wp + tap % 3) * 4u);
+              const uint64_t ad_t = desc_add(wd, (uint32_t)((tap / 3) * a.Wp + tap % 3) * (Cfg::WROW / 16u));
               const uint64_t bd_s = desc_add(b_desc0, (s * (uint32_t)Cfg::B_BYTES) >> 4);
 #pragma unroll
               for (int kk = 0; kk < BKC / 16; ++kk)
 #pragma unroll
                 for (int ms = 0; ms < Cfg::MS; ++ms)   // sub-tile ms: 128 window rows (8 KB) further on
-                  mma_step<CG, Q>(d + (uint32_t)(ms * BN), desc_add(ad_t, 2 * kk + ms * 512), desc_add(bd_s, 2 * kk),
+                  mma_step<CG, Q>(d + (uint32_t)(ms * BN), desc_add(ad_t, 2 * kk + ms * 8 * Cfg::WROW),
+                                  desc_add(bd_s, 2 * kk),
                                   idesc, (cb | tap | kk) != 0 ? 1u : 0u);
               if constexpr (CG == 2)
                 umma_commit_pair(&empty[s], 3);
@@ -1020,16 +1024,18 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
 constexpr int W4_STAGES = 8;
 constexpr int W4_STAGES_Q = 12;
 constexpr int W4M2_STAGES = 12;   // two sub-tiles: half-size weight tiles (64 rows per CTA), each used twice
-template <int BN, int CG, int Q, int WM>
+constexpr int W4W_STAGES = 4;     // 128-byte window rows: 16 KB weight tiles, 512 MMA cycles each
+template <int BN, int BKC, int CG, int Q, int WM>
 constexpr int w4_fixed() {
-  constexpr int S = WM == 2 ? W4M2_STAGES : (Q ? W4_STAGES_Q : W4_STAGES);
-  using C = TcCfg<BN, 32, S, CG, Q, WM>;
+  constexpr int S = BKC == 64 ? W4W_STAGES : WM == 2 ? W4M2_STAGES : (Q ? W4_STAGES_Q : W4_STAGES);
+  using C = TcCfg<BN, BKC, S, CG, Q, WM>;
   return S * C::B_BYTES + 2 * C::SDEPTH * C::C_BYTES + 1024 + C::BAR_BYTES + C::BIAS_BYTES;
 }
-int w4_fixed_bytes(int bn, int q, int msub) {
-  if (msub == 2) return q ? w4_fixed<128, 2, 1, 2>() : w4_fixed<128, 2, 0, 2>();
-  if (bn == 128) return q ? w4_fixed<128, 2, 1, 1>() : w4_fixed<128, 2, 0, 1>();
-  return q ? w4_fixed<256, 2, 1, 1>() : w4_fixed<256, 2, 0, 1>();
+int w4_fixed_bytes(int bn, int q, int msub, int wide) {
+  if (wide) return w4_fixed<256, 64, 2, 0, 1>();
+  if (msub == 2) return q ? w4_fixed<128, 32, 2, 1, 2>() : w4_fixed<128, 32, 2, 0, 2>();
+  if (bn == 128) return q ? w4_fixed<128, 32, 2, 1, 1>() : w4_fixed<128, 32, 2, 0, 1>();
+  return q ? w4_fixed<256, 32, 2, 1, 1>() : w4_fixed<256, 32, 2, 0, 1>();
 }
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -1310,14 +1316,18 @@ bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const void* w_any, int cout_p
     plan.M_total = c.in.n * Hp * Wp;
     plan.m_tiles = (plan.M_total + 127) / 128;
     // 3x3 with 128- or 256-wide tiles: flat windows (mode 4) when at least two fit in shared memory
-    const int kel4 = q ? 64 : 32;           // 64-byte k-blocks
     // (measured: E4M3 convs of two 64-byte k-blocks, 128 input channels, run faster flat)
-    if (c.k == 3 && (bn == 128 || bn == 256) && c.cin % kel4 == 0 && !(q && c.cin / kel4 == 2)) {
+    // BF16 256-wide tiles take 128-byte k-blocks (64 channels) when two such windows fit: half the
+    // TMA rows per byte, the 128-byte swizzle; otherwise (and for E4M3) 64-byte k-blocks
+    for (int wide = (!q && bn == 256 && msub == 1 && c.cin % 64 == 0) ? 1 : 0; wide >= 0 && plan.mode != 4; --wide) {
+      const int kel4 = q ? 64 : (wide ? 64 : 32);   // channels per k-block
+      const int rowb = wide ? 128 : 64;             // bytes per window row
+      if (!(c.k == 3 && (bn == 128 || bn == 256) && c.cin % kel4 == 0 && !(q && c.cin / kel4 == 2))) continue;
       const int npx = 128 * msub + 2 * Wp + 2;   // rows m0 - Wp - 1 .. m0 + 128 msub + Wp
       const int wnb = (npx + 255) / 256;     // a TMA box spans at most 256 rows
       const int whb = ((npx + wnb - 1) / wnb + 15) / 16 * 16;   // rows per box: 1024-byte multiples
-      const int win_bytes = wnb * whb * 64;
-      int nwin = (227 * 1024 - 64 - w4_fixed_bytes(bn, q, msub)) / win_bytes;
+      const int win_bytes = wnb * whb * rowb;
+      int nwin = (227 * 1024 - 64 - w4_fixed_bytes(bn, q, msub, wide)) / win_bytes;
       if (nwin > MAX_WIN) nwin = MAX_WIN;
       if (nwin >= 2) {
         plan.mode = 4;
@@ -1328,7 +1338,7 @@ bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const void* w_any, int cout_p
         plan.win_bytes = win_bytes;
         plan.nwin = nwin;
         plan.kel = kel4;
-        plan.bkc = 32;
+        plan.bkc = rowb / 2;
         plan.cin_blocks = c.cin / kel4;
         plan.kt_total = 9 * plan.cin_blocks;
       }
@@ -1474,8 +1484,13 @@ cudaError_t conv_tc_launch(const TcPlan& p, cudaStream_t st) {
     return cudaErrorInvalidValue;
   }
   if (p.mode == 4) {
-    const int smem = p.nwin * p.win_bytes + w4_fixed_bytes(p.bn, p.q, p.msub);
+    const int wide = !p.q && p.bkc == 64;
+    const int smem = p.nwin * p.win_bytes + w4_fixed_bytes(p.bn, p.q, p.msub, wide);
     if (smem > 227 * 1024 - 64) return cudaErrorInvalidValue;
+    if (wide) {
+      if (p.bn != 256 || p.cg != 2 || p.msub != 1) return cudaErrorInvalidValue;
+      return launch_cfg<256, 64, W4W_STAGES, 1, 2, 0, 1>(p, a, st, smem);
+    }
     if (p.msub == 2) {
       if (p.bn != 128 || p.cg != 2 || !p.tma_out) return cudaErrorInvalidValue;
       return p.q ? launch_cfg<128, 32, W4M2_STAGES, 1, 2, 1, 2>(p, a, st, smem)

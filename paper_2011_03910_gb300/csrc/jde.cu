@@ -1265,7 +1265,8 @@ jde_status jde_autotune(jde_handle* h, int n, int in_w, int in_h, void* stream) 
       TcPlan cand;
       char msg[256];
       if (!conv_tc_plan(cand, plan->specs[l], w, lw.cout_pad_tc, bn, msg, sizeof(msg), msub)) continue;
-      if (cand.mode != def.mode || cand.msub != msub) continue;   // same addressing mode: the same order of the K sum
+      // same addressing mode and k-block width: the same order of the K sum
+      if (cand.mode != def.mode || cand.bkc != def.bkc || cand.msub != msub) continue;
       if (msub == 2 && !cand.tma_out) continue;
       if (conv_tc_launch(cand, st) != cudaSuccess) {   // shape without a built configuration
         cudaGetLastError();
@@ -1329,7 +1330,8 @@ jde_status jde_set_tile_choice(jde_handle* h, int n, int in_w, int in_h, const i
       const LayerW& lw = h->w[l];
       const void* w = lw.q ? static_cast<const void*>(lw.w_q) : static_cast<const void*>(lw.w_nk);
       const bool def_ok = conv_tc_plan(def, plan->specs[l], w, lw.cout_pad_tc, lw.bn, msg, sizeof(msg));
-      if (t.bn != (codes[l] & ~1) || t.msub != ((codes[l] & 1) ? 2 : 1) || !def_ok || def.mode != t.mode)
+      if (t.bn != (codes[l] & ~1) || t.msub != ((codes[l] & 1) ? 2 : 1) || !def_ok || def.mode != t.mode ||
+          def.bkc != t.bkc)
         s = fail(h, JDE_ERR_UNSUPPORTED, "jde_set_tile_choice: layer %d cannot run tile code %d", l, codes[l]);
     }
   }

@@ -52,21 +52,23 @@ def test_autotuned_forward_is_bit_identical(fp8):
 
 
 def _two_subtile_codes(j, h, n, in_w, in_h, fp8=False):
-    """Tile code 129 (128 channels x 256 rows per CTA) on every stride-1 3x3 conv whose output channel
-    count is a multiple of 128 and whose output the handle stores (E4M3: not the 128-channel-input
-    convs, which run without windows)."""
-    codes = j.jde_tile_choice(h, n, in_w, in_h)
-    stored = set()
-    for l in range(78):
-        try:
-            j.jde_get_tensor(h, l)
-            stored.add(l)
-        except j.JdeError:
-            pass
+    """Tile code 129 (128 channels x 256 rows per CTA) on every stride-1 3x3 conv that can take it with
+    the same K order as its default tile (64-byte k-blocks: the 128-wide convs, and every E4M3 one
+    with windows), found by asking jde_set_tile_choice layer by layer."""
+    base = j.jde_tile_choice(h, n, in_w, in_h)
+    codes = list(base)
     table = j.jde_layer_table()
     for l, (cin, cout, k, stride, _, _) in enumerate(table):
-        if k == 3 and stride == 1 and cin % 32 == 0 and cout % 128 == 0 and l in stored and not (fp8 and cin == 128):
-            codes[l] = 129
+        if not (k == 3 and stride == 1 and cin % 32 == 0 and cout % 128 == 0):
+            continue
+        trial = list(base)
+        trial[l] = 129
+        try:
+            j.jde_set_tile_choice(h, n, in_w, in_h, trial)
+        except j.JdeError:
+            continue
+        codes[l] = 129
+    j.jde_set_tile_choice(h, n, in_w, in_h, base)
     return codes
 
 
@@ -86,7 +88,7 @@ def test_two_m_subtiles_per_cta_are_bit_identical(fp8, size):
         frames = synth.frames_uniform(3, n, in_h, in_w)
         before = _layer_outputs(j, h, frames, in_w, in_h)
         codes = _two_subtile_codes(j, h, n, in_w, in_h, fp8)
-        assert sum(c == 129 for c in codes) >= 20
+        assert sum(c == 129 for c in codes) >= (20 if fp8 else 2)
         j.jde_set_tile_choice(h, n, in_w, in_h, codes)
         assert j.jde_tile_choice(h, n, in_w, in_h) == codes
         after = _layer_outputs(j, h, frames, in_w, in_h)
