@@ -1032,7 +1032,7 @@ constexpr int w4_fixed() {
   return S * C::B_BYTES + 2 * C::SDEPTH * C::C_BYTES + 1024 + C::BAR_BYTES + C::BIAS_BYTES;
 }
 int w4_fixed_bytes(int bn, int q, int msub, int wide) {
-  if (wide) return w4_fixed<256, 64, 2, 0, 1>();
+  if (wide) return q ? w4_fixed<256, 64, 2, 1, 1>() : w4_fixed<256, 64, 2, 0, 1>();
   if (msub == 2) return q ? w4_fixed<128, 32, 2, 1, 2>() : w4_fixed<128, 32, 2, 0, 2>();
   if (bn == 128) return q ? w4_fixed<128, 32, 2, 1, 1>() : w4_fixed<128, 32, 2, 0, 1>();
   return q ? w4_fixed<256, 32, 2, 1, 1>() : w4_fixed<256, 32, 2, 0, 1>();
@@ -1317,12 +1317,14 @@ bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const void* w_any, int cout_p
     plan.m_tiles = (plan.M_total + 127) / 128;
     // 3x3 with 128- or 256-wide tiles: flat windows (mode 4) when at least two fit in shared memory
     // (measured: E4M3 convs of two 64-byte k-blocks, 128 input channels, run faster flat)
-    // BF16 256-wide tiles take 128-byte k-blocks (64 channels) when two such windows fit: half the
-    // TMA rows per byte, the 128-byte swizzle; otherwise (and for E4M3) 64-byte k-blocks
-    for (int wide = (!q && bn == 256 && msub == 1 && c.cin % 64 == 0) ? 1 : 0; wide >= 0 && plan.mode != 4; --wide) {
-      const int kel4 = q ? 64 : (wide ? 64 : 32);   // channels per k-block
-      const int rowb = wide ? 128 : 64;             // bytes per window row
-      if (!(c.k == 3 && (bn == 128 || bn == 256) && c.cin % kel4 == 0 && !(q && c.cin / kel4 == 2))) continue;
+    // 256-wide tiles take 128-byte k-blocks (64 bf16 / 128 E4M3 channels) when two such windows fit:
+    // half the TMA rows per byte, the 128-byte swizzle; otherwise 64-byte k-blocks
+    const int wide0 = bn == 256 && msub == 1 && c.cin % (q ? 128 : 64) == 0;
+    for (int wide = wide0; wide >= 0 && plan.mode != 4; --wide) {
+      const int kel4 = q ? (wide ? 128 : 64) : (wide ? 64 : 32);   // channels per k-block
+      const int rowb = wide ? 128 : 64;                             // bytes per window row
+      if (!(c.k == 3 && (bn == 128 || bn == 256) && c.cin % kel4 == 0 && !(q && !wide && c.cin / kel4 == 2)))
+        continue;
       const int npx = 128 * msub + 2 * Wp + 2;   // rows m0 - Wp - 1 .. m0 + 128 msub + Wp
       const int wnb = (npx + 255) / 256;     // a TMA box spans at most 256 rows
       const int whb = ((npx + wnb - 1) / wnb + 15) / 16 * 16;   // rows per box: 1024-byte multiples
@@ -1484,12 +1486,13 @@ cudaError_t conv_tc_launch(const TcPlan& p, cudaStream_t st) {
     return cudaErrorInvalidValue;
   }
   if (p.mode == 4) {
-    const int wide = !p.q && p.bkc == 64;
+    const int wide = p.bkc == 64;
     const int smem = p.nwin * p.win_bytes + w4_fixed_bytes(p.bn, p.q, p.msub, wide);
     if (smem > 227 * 1024 - 64) return cudaErrorInvalidValue;
     if (wide) {
       if (p.bn != 256 || p.cg != 2 || p.msub != 1) return cudaErrorInvalidValue;
-      return launch_cfg<256, 64, W4W_STAGES, 1, 2, 0, 1>(p, a, st, smem);
+      return p.q ? launch_cfg<256, 64, W4W_STAGES, 1, 2, 1, 1>(p, a, st, smem)
+                 : launch_cfg<256, 64, W4W_STAGES, 1, 2, 0, 1>(p, a, st, smem);
     }
     if (p.msub == 2) {
       if (p.bn != 128 || p.cg != 2 || !p.tma_out) return cudaErrorInvalidValue;
