@@ -86,11 +86,16 @@ struct TcCfg {
   static constexpr int NSUB = SWC / SUB;
   static constexpr int SUB_BYTES = 128 * SUB * 2;
   static constexpr int C_BYTES = Q ? 128 * SWC : NSUB * SUB_BYTES;   // one staging tile (one epilogue pass)
-  // staging tiles per epilogue group (flat windows of 128-byte rows: one, for the windows' room)
-  static constexpr int SDEPTH = (WM && BKC == 64) ? 1 : 2;
   static constexpr uint32_t WROW = BKC * 2;             // mode 4: bytes per window row (one k-block)
   static constexpr int BIAS_BYTES = 2 * BN * 4 * (Q ? 2 : 1);   // per epilogue group: bias (and E4M3 scale) slice
   static constexpr int BAR_BYTES = 768;                 // mbarriers + TMEM address slot
+  // staging tiles per epilogue group: two, unless the ring then leaves no room (flat windows of
+  // 128-byte rows, deep rings of 256-wide tiles): one
+  static constexpr int SDEPTH =
+      (WM && BKC == 64) ||
+              STAGES * STAGE_BYTES + 4 * C_BYTES + 1024 + BAR_BYTES + BIAS_BYTES > 227 * 1024 - 64
+          ? 1
+          : 2;
   static constexpr int SMEM =
       STAGES * STAGE_BYTES + 2 * SDEPTH * C_BYTES + 1024 /*align*/ + BAR_BYTES + BIAS_BYTES;
   static constexpr uint32_t LAYOUT = BKC == 64 ? 2u : 4u;     // SW128 : SW64 (MMA operand tiles)
@@ -1024,14 +1029,18 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
 constexpr int W4_STAGES = 8;
 constexpr int W4_STAGES_Q = 12;
 constexpr int W4M2_STAGES = 12;   // two sub-tiles: half-size weight tiles (64 rows per CTA), each used twice
-constexpr int W4W_STAGES = 4;     // 128-byte window rows: 16 KB weight tiles, 512 MMA cycles each
-template <int BN, int BKC, int CG, int Q, int WM>
+// 128-byte window rows: 16 KB weight tiles, 512 MMA cycles each; the deeper ring where two windows
+// still fit next to it (the narrower images), else the shallower one
+constexpr int W4W_STAGES = 5;
+constexpr int W4W_STAGES_DEEP = 7;
+template <int BN, int BKC, int CG, int Q, int WM, int SW = W4W_STAGES>
 constexpr int w4_fixed() {
-  constexpr int S = BKC == 64 ? W4W_STAGES : WM == 2 ? W4M2_STAGES : (Q ? W4_STAGES_Q : W4_STAGES);
+  constexpr int S = BKC == 64 ? SW : WM == 2 ? W4M2_STAGES : (Q ? W4_STAGES_Q : W4_STAGES);
   using C = TcCfg<BN, BKC, S, CG, Q, WM>;
   return S * C::B_BYTES + 2 * C::SDEPTH * C::C_BYTES + 1024 + C::BAR_BYTES + C::BIAS_BYTES;
 }
-int w4_fixed_bytes(int bn, int q, int msub, int wide) {
+int w4_fixed_bytes(int bn, int q, int msub, int wide, int deep = 0) {
+  if (wide && deep) return q ? w4_fixed<256, 64, 2, 1, 1, W4W_STAGES_DEEP>() : w4_fixed<256, 64, 2, 0, 1, W4W_STAGES_DEEP>();
   if (wide) return q ? w4_fixed<256, 64, 2, 1, 1>() : w4_fixed<256, 64, 2, 0, 1>();
   if (msub == 2) return q ? w4_fixed<128, 32, 2, 1, 2>() : w4_fixed<128, 32, 2, 0, 2>();
   if (bn == 128) return q ? w4_fixed<128, 32, 2, 1, 1>() : w4_fixed<128, 32, 2, 0, 1>();
@@ -1329,10 +1338,12 @@ bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const void* w_any, int cout_p
       const int wnb = (npx + 255) / 256;     // a TMA box spans at most 256 rows
       const int whb = ((npx + wnb - 1) / wnb + 15) / 16 * 16;   // rows per box: 1024-byte multiples
       const int win_bytes = wnb * whb * rowb;
-      int nwin = (227 * 1024 - 64 - w4_fixed_bytes(bn, q, msub, wide)) / win_bytes;
+      int deep = wide && (227 * 1024 - 64 - w4_fixed_bytes(bn, q, msub, wide, 1)) / win_bytes >= 2;
+      int nwin = (227 * 1024 - 64 - w4_fixed_bytes(bn, q, msub, wide, deep)) / win_bytes;
       if (nwin > MAX_WIN) nwin = MAX_WIN;
       if (nwin >= 2) {
         plan.mode = 4;
+        plan.w4deep = deep;
         plan.msub = msub;
         plan.m_tiles = (plan.M_total + 128 * msub - 1) / (128 * msub);
         plan.wnb = wnb;
@@ -1487,10 +1498,13 @@ cudaError_t conv_tc_launch(const TcPlan& p, cudaStream_t st) {
   }
   if (p.mode == 4) {
     const int wide = p.bkc == 64;
-    const int smem = p.nwin * p.win_bytes + w4_fixed_bytes(p.bn, p.q, p.msub, wide);
+    const int smem = p.nwin * p.win_bytes + w4_fixed_bytes(p.bn, p.q, p.msub, wide, p.w4deep);
     if (smem > 227 * 1024 - 64) return cudaErrorInvalidValue;
     if (wide) {
       if (p.bn != 256 || p.cg != 2 || p.msub != 1) return cudaErrorInvalidValue;
+      if (p.w4deep)
+        return p.q ? launch_cfg<256, 64, W4W_STAGES_DEEP, 1, 2, 1, 1>(p, a, st, smem)
+                   : launch_cfg<256, 64, W4W_STAGES_DEEP, 1, 2, 0, 1>(p, a, st, smem);
       return p.q ? launch_cfg<256, 64, W4W_STAGES, 1, 2, 1, 1>(p, a, st, smem)
                  : launch_cfg<256, 64, W4W_STAGES, 1, 2, 0, 1>(p, a, st, smem);
     }
