@@ -381,7 +381,9 @@ typedef struct {
   int stream_id;
   int n_dets;         /* detections kept (rows beyond det_cap were not written) */
   int n_tracks;       /* tracks alive after the step (beyond track_cap not reported) */
-  int errors;         /* kernel error word of the frame's batch (jde_kernel_errors), 0 if none */
+  int errors;         /* kernel error word of the frame's batch (jde_kernel_errors), 0 if none; -1
+                         when the batch could not be launched or did not complete (nothing else of
+                         the result is filled in) */
   float done_ms;      /* device time at which the frame's batch finished, ms after the server's clock
                          start (jde_server_create or jde_server_reset_clock) */
 } jde_frame_result;
@@ -425,7 +427,8 @@ jde_status jde_submit(jde_server* s, int stream_id, const uint8_t* frame, const 
 
 /* Advance the server without blocking (see above) and move up to cap results of finished frames
  * into results[0..*n), in completion order.  A failed launch or batch returns its status (the
- * message in jde_server_last_error). */
+ * message in jde_server_last_error); its frames still get their results, with errors = -1, so every
+ * submitted frame gets exactly one result. */
 jde_status jde_poll(jde_server* s, jde_frame_result* results, int cap, int* n);
 
 /* Device bytes a group of in_w x in_h is charged at creation: jde_estimate_device_bytes of its handle's

@@ -316,6 +316,23 @@ jde_status prewarm_group(jde_server* s, Group* g) {
   return JDE_OK;
 }
 
+// Frames whose batch could not be launched or did not complete: their results are returned with
+// errors = -1 (nothing else filled in), so every submitted frame gets exactly one result.
+void fail_frames(jde_server* s, const std::vector<Pending>& frames) {
+  for (const Pending& p : frames) {
+    jde_frame_result r;
+    memset(&r, 0, sizeof(r));
+    r.ticket = p.ticket;
+    r.stream_id = p.stream_id;
+    r.errors = -1;
+    s->ready.push_back(r);
+    auto it = s->streams.find(p.stream_id);
+    if (it != s->streams.end()) it->second.inflight -= 1;
+  }
+}
+
+jde_status launch_frames(jde_server* s, Group* g, Batch& b);
+
 jde_status launch_batch(jde_server* s, Group* g) {
   Batch b;
   std::deque<Pending> rest;
@@ -333,8 +350,19 @@ jde_status launch_batch(jde_server* s, Group* g) {
     }
   }
   g->queue.swap(rest);
-  const int n = (int)b.frames.size();
-  b.n = n;
+  b.n = (int)b.frames.size();
+  const jde_status st = launch_frames(s, g, b);
+  if (st != JDE_OK) {
+    if (b.done) cudaEventDestroy(b.done);
+    fail_frames(s, b.frames);
+  }
+  return st;
+}
+
+// Copies, launch sequence (graph or eager) and output copies of batch b; on success the batch is in
+// flight with its done event.
+jde_status launch_frames(jde_server* s, Group* g, Batch& b) {
+  const int n = b.n;
   const size_t fbytes = (size_t)s->cfg.src_w * s->cfg.src_h * 3;
   std::vector<int> ids(n);
   for (int i = 0; i < n; ++i) {
@@ -379,6 +407,7 @@ jde_status launch_batch(jde_server* s, Group* g) {
   S_CUDA(s, cudaEventCreateWithFlags(&b.done, cudaEventDefault));
   S_CUDA(s, cudaEventRecord(b.done, g->st));
   g->inflight.push_back(b);
+  b.done = nullptr;   // owned by the in-flight copy
   return JDE_OK;
 }
 
@@ -420,7 +449,13 @@ jde_status poll_groups(jde_server* s) {
     while (!g->inflight.empty()) {
       const cudaError_t q = cudaEventQuery(g->inflight.front().done);
       if (q == cudaErrorNotReady) break;
-      if (q != cudaSuccess) return sfail(s, JDE_ERR_CUDA, "batch: %s", cudaGetErrorString(q));
+      if (q != cudaSuccess) {
+        Batch& bad = g->inflight.front();
+        fail_frames(s, bad.frames);
+        cudaEventDestroy(bad.done);
+        g->inflight.pop_front();
+        return sfail(s, JDE_ERR_CUDA, "batch: %s", cudaGetErrorString(q));
+      }
       // the batch is done, so reading the handle's error word waits for nothing
       int word = 0;
       jde_status st = jde_kernel_errors(g->h, &word, g->st);
