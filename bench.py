@@ -894,6 +894,53 @@ def main():
     drain()
     e2e = {"value": world * B * K / e2e_s, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    # the first residual block fused into one kernel (fuse_block1 = 1): the same pipelined step on two
+    # such handles, and the conv phase of single-stream steps, beside the default two-kernel form
+    fused_block = None
+    if rank == 0 and not args.no_jpeg:
+        fcfg = jde.jde_config.from_buffer_copy(cfg)
+        fcfg.fuse_block1 = 1
+        fh = [jde.jde_create(fcfg, blob) for _ in range(2)]
+        for x in fh:
+            jde.jde_set_tile_choice(x, B, IN_W, IN_H, jde.jde_tile_choice(h, B, IN_W, IN_H))
+        saved_hs = list(hs)
+        hs[:] = fh
+        for _ in range(W):
+            step(t, 2)
+            t += 1
+        drain()
+        fprof = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K1)]
+        for p3 in fprof:
+            for e in p3:
+                e.record(F[0])
+        for i in range(K1):
+            step(t, 1, fprof[i])
+            t += 1
+        drain()
+        for x in fh:
+            jde.jde_set_profile_events(x)
+        fconv = sum(p[1].elapsed_time(p[2]) for p in fprof) / K1
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(F[0])
+        F[1].wait_event(f0)
+        P.wait_event(f0)
+        for i in range(K):
+            step(t, 2)
+            t += 1
+        F[0].wait_event(post_done[t - 1])
+        f1.record(F[0])
+        torch.cuda.synchronize()
+        assert all(jde.jde_kernel_errors(x) == 0 for x in fh)
+        fms = f0.elapsed_time(f1) / K
+        drain()
+        hs[:] = saved_hs
+        for x in fh:
+            jde.jde_destroy(x)
+        fused_block = {"fps_pipelined": B * 1000.0 / fms, "conv_ms_single_stream": fconv,
+                       "default_fps_pipelined": value, "default_conv_ms_single_stream": conv_ms1,
+                       "what": "fuse_block1 = 1 (layers 2-3 in one kernel, the 1x1 output on chip) against the default "
+                               "two kernels: the same pipelined step (two handles) and single-stream conv phase"}
+
     # e2e from compressed frames: Motion-JPEG bitstreams in host memory (camera-like synthetic frames,
     # quality 90, 4:2:0), decoded on the device (jde_decode_jpeg) on each forward stream into that
     # handle's frame buffer, then the same pipeline; only the bitstreams cross the host link
@@ -987,6 +1034,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": e2e,
             "e2e_jpeg": jpeg,
+            "fused_first_block": fused_block,
             "gpu_launches": int(l1 - l0),
             "clocks": clocks,
         }

@@ -110,6 +110,12 @@ typedef struct {
   double motion_lambda; /* cascade stage 1 weight of the appearance cost, default 0.98 */
   double iou_cost2;     /* cascade stage 2 rejection threshold on 1 - IoU, default 0.5 */
   double iou_cost3;     /* cascade stage 3 rejection threshold on 1 - IoU, default 0.3 */
+  int fuse_block1;      /* tensor-core handles with keep_layer_outputs = 0: 1 runs the first stage's
+                           residual block (layers 2 and 3, Sec. 3.1) as one kernel whose 1x1 output
+                           never leaves shared memory and whose output goes to its own tensor (tensor 2
+                           is then refused by jde_get_tensor; 0.6 GB less DRAM traffic per batch-16
+                           step, the same time alone, 2% slower when two batches share the GPU);
+                           0 (default): two kernels, the block in place */
 } jde_config;
 
 /* One layer of the network as this library builds it (for the weights blob). */

@@ -142,6 +142,16 @@ StemS2Plan* stem_s2_plan_new(const TView& lb, const TView& out, const void* w0b,
 void stem_s2_plan_free(StemS2Plan* p);
 cudaError_t stem_s2_launch(const StemS2Plan* p, cudaStream_t st);
 
+// The first stage's residual block (1x1 64 -> 32, 3x3 32 -> 64, + input) fused into one tcgen05 kernel:
+// the 1x1's output stays in shared memory.  x: the block input, out: the block output (another tensor:
+// x is read on every patch's halo); w1: the 1x1's packed bf16 weights [32][64], w2: the 3x3's [64][320];
+// b1, b2: their folded biases.  The output is leaky(3x3 + b2) + x rounded once to bf16.
+struct Res1Plan;
+Res1Plan* res1_plan_new(const TView& x, const TView& out, const void* w1, const void* w2, const float* b1,
+                        const float* b2, int* err, char* msg, size_t msg_len);
+void res1_plan_free(Res1Plan* p);
+cudaError_t res1_launch(const Res1Plan* p, cudaStream_t st);
+
 // jde_track_step whose kernels read the call's stream slots from dev_slots (device, n entries, the same
 // values as stream_ids) instead of kernel arguments, so that a captured CUDA graph of the step serves
 // any batch of n streams after the caller rewrites dev_slots.

@@ -102,6 +102,12 @@ bool sparse_emb_cfg(const jde_config& c) { return c.sparse_emb && c.precision !=
 // Stem and first stride-2 conv fused (the stem's output is never stored): tensor-core handles, unless
 // they keep every layer output (keep_layer_outputs = 1).
 bool fused_stem_cfg(const jde_config& c) { return c.precision != JDE_FP32 && c.keep_layer_outputs != 1; }
+// The first stage's residual block (layers 2 and 3) fused into one kernel whose 1x1 output (layer 2) is
+// never stored and whose output (layer 3) goes to its own tensor: tensor-core handles with the default
+// keep_layer_outputs = 0.
+bool fused_res1_cfg(const jde_config& c) {
+  return c.precision != JDE_FP32 && c.keep_layer_outputs == 0 && c.fuse_block1 != 0;
+}
 
 // Where each conv reads and writes (tensor ids below, -1 = none).
 struct LayerIO {
@@ -138,6 +144,7 @@ struct Plan {
   std::vector<ConvSpec> specs;     // per layer
   std::vector<TcPlan> tc;          // per layer (BF16)
   std::shared_ptr<StemS2Plan> stem_s2;   // layers 0 and 1 fused (their tc plans unused)
+  std::shared_ptr<Res1Plan> res1;        // layers 2 and 3 fused (their tc plans unused)
 };
 
 }  // namespace
@@ -243,7 +250,7 @@ std::vector<LayerIO> build_io(const jde_config& cfg) {
       const int r = x;
       const int t = set(x, -1, 1);
       x = set(t, r, 1);
-      if (chain) {
+      if (chain && !(s == 0 && fused_res1_cfg(cfg))) {   // the fused first block writes its own tensor
         io[x].out = io[r].out;               // the block output overwrites its input
         io[x].out_slice = io[r].out_slice;
       }
@@ -343,6 +350,7 @@ bool two_sets(const jde_handle* h, int t) {
 // it is fused into the next conv.
 bool not_stored(const jde_handle* h, int t) {
   if (t == 0 && fused_stem_cfg(h->cfg)) return true;
+  if (t == 2 && fused_res1_cfg(h->cfg)) return true;
   return t < JDE_NUM_LAYERS && t >= 0 && h->io[t].head >= 3 && sparse_emb_cfg(h->cfg);
 }
 
@@ -466,6 +474,7 @@ jde_status get_plan(jde_handle* h, ResBuffers* rb, int n, Plan** out) {
     if (c.out.dtype == 2) c.out_inv_scale = 1.0f / h->act_scale[buffer_of(h, (int)l)];
     p.specs[l] = c;
     if (bf16 && l == 1 && fused_stem_cfg(h->cfg)) continue;   // runs inside the fused stem kernel
+    if (bf16 && l == 3 && fused_res1_cfg(h->cfg)) continue;   // runs inside the fused block kernel
     if (bf16) {
       char msg[256];
       const void* w = c.q ? static_cast<const void*>(h->w[l].w_q) : static_cast<const void*>(h->w[l].w_nk);
@@ -483,6 +492,13 @@ jde_status get_plan(jde_handle* h, ResBuffers* rb, int n, Plan** out) {
                                       static_cast<char*>(h->stem_pack) + 32 * 32 * 2, h->d_err, msg, sizeof(msg));
     if (!fp) return fail(h, JDE_ERR_UNSUPPORTED, "layers 0-1: %s", msg);
     p.stem_s2.reset(fp, stem_s2_plan_free);
+  }
+  if (bf16 && fused_res1_cfg(h->cfg)) {
+    char msg[256];
+    Res1Plan* rp = res1_plan_new(view_of(*rb, 1, n), view_of(*rb, 3, n), h->w[2].w_nk, h->w[3].w_nk, h->w[2].bias,
+                                 h->w[3].bias, h->d_err, msg, sizeof(msg));
+    if (!rp) return fail(h, JDE_ERR_UNSUPPORTED, "layers 2-3: %s", msg);
+    p.res1.reset(rp, res1_plan_free);
   }
   auto res = h->plans.emplace(key, std::move(p));
   *out = &res.first->second;
@@ -835,6 +851,7 @@ void jde_default_config(jde_config* c) {
   c->motion_lambda = 0.98;
   c->iou_cost2 = 0.5;
   c->iou_cost3 = 0.3;
+  c->fuse_block1 = 0;
 }
 
 int jde_layer_table(jde_layer_desc* out, int cap) {
@@ -885,7 +902,7 @@ jde_status jde_create(const jde_config* cfg, const void* weights, size_t nbytes,
       c.max_streams < 1 || c.max_tracks < 1 || c.max_track_dets < 1 || c.max_track_dets > 4096 ||
       c.max_tracks > 4096 || c.keep_layer_outputs < 0 || c.keep_layer_outputs > 2 || c.assoc_cascade < 0 ||
       c.assoc_cascade > 1 || !(c.motion_lambda >= 0.0 && c.motion_lambda <= 1.0) || !(c.iou_cost2 >= 0.0) ||
-      !(c.iou_cost3 >= 0.0))
+      !(c.iou_cost3 >= 0.0) || c.fuse_block1 < 0 || c.fuse_block1 > 1)
     return fail(nullptr, JDE_ERR_INVALID_ARG, "config out of range");
   if (cudaSetDevice(c.device) != cudaSuccess) return fail(nullptr, JDE_ERR_CUDA, "cudaSetDevice(%d)", c.device);
   jde_handle* h = new jde_handle();
@@ -972,6 +989,7 @@ jde_status jde_forward(jde_handle* h, const uint8_t* frames, int n, int src_w, i
     if (not_stored(h, (int)l)) continue;
     if (bf16) {
       const cudaError_t e = (l == 1 && plan->stem_s2) ? stem_s2_launch(plan->stem_s2.get(), st)
+                            : (l == 3 && plan->res1) ? res1_launch(plan->res1.get(), st)
                                                       : conv_tc_launch(plan->tc[l], st);
       if (e != cudaSuccess) return fail(h, JDE_ERR_CUDA, "conv layer %zu: %s", l, cudaGetErrorString(e));
     } else {
@@ -1133,8 +1151,10 @@ jde_status jde_get_tensor(jde_handle* h, int id, void* dst, size_t dst_bytes, in
   int tid;
   if (id >= 0 && id < JDE_NUM_LAYERS && not_stored(h, id))
     return fail(h, JDE_ERR_NOT_FOUND,
-                id == 0 ? "tensor 0: the stem's output stays on chip, fused into layer 1 (keep_layer_outputs = 1 keeps it)"
-                        : "tensor %d: the embedding head runs only at kept detections (sparse_emb)",
+                id == 0   ? "tensor 0: the stem's output stays on chip, fused into layer 1 (keep_layer_outputs = 1 keeps it)"
+                : id == 2 ? "tensor 2: the first residual block's 1x1 output stays on chip, fused into layer 3 "
+                            "(keep_layer_outputs = 1 or 2 keeps it)"
+                          : "tensor %d: the embedding head runs only at kept detections (sparse_emb)",
                 id);
   if (id >= 0 && id < JDE_NUM_LAYERS && overwritten(h, id))
     return fail(h, JDE_ERR_NOT_FOUND, "tensor %d is overwritten in place by its residual block (keep_layer_outputs)", id);
@@ -1246,6 +1266,7 @@ jde_status jde_autotune(jde_handle* h, int n, int in_w, int in_h, void* stream) 
     for (int k = l - 1; k >= 0; --k) {
       if (not_stored(h, k)) continue;
       if (k == 1 && plan->stem_s2) return stem_s2_launch(plan->stem_s2.get(), st);
+      if (k == 3 && plan->res1) return res1_launch(plan->res1.get(), st);
       return conv_tc_launch(plan->tc[k], st);
     }
     return cudaSuccess;
@@ -1253,6 +1274,7 @@ jde_status jde_autotune(jde_handle* h, int n, int in_w, int in_h, void* stream) 
   for (int l = 0; l < JDE_NUM_LAYERS; ++l) {
     if (not_stored(h, l)) continue;                  // sparse embedding head: not a conv launch
     if (l == 1 && plan->stem_s2) continue;           // fused with the stem: one tile shape
+    if (l == 3 && plan->res1) continue;              // fused residual block: one tile shape
     const TcPlan& def = plan->tc[l];
     if (def.mode == 2 || def.mode == 3) continue;    // stem and window convs have one tile shape
     const LayerW& lw = h->w[l];
@@ -1322,7 +1344,9 @@ jde_status jde_set_tile_choice(jde_handle* h, int n, int in_w, int in_h, const i
   if (s == JDE_OK) {
     // a code the layer cannot run as asked (e.g. two sub-tiles whose windows do not fit) is refused
     for (int l = 0; l < JDE_NUM_LAYERS && s == JDE_OK; ++l) {
-      if (codes[l] == 0 || plan->tc.empty() || not_stored(h, l) || (l == 1 && plan->stem_s2)) continue;
+      if (codes[l] == 0 || plan->tc.empty() || not_stored(h, l) || (l == 1 && plan->stem_s2) ||
+          (l == 3 && plan->res1))
+        continue;
       const TcPlan& t = plan->tc[l];
       // the default tile's addressing mode: another mode would sum K in another order
       TcPlan def;

@@ -34,7 +34,8 @@ class jde_config(C.Structure):
                 ("lost_max_frames", C.c_int), ("emb_momentum", C.c_float), ("max_streams", C.c_int),
                 ("max_tracks", C.c_int), ("max_track_dets", C.c_int), ("device", C.c_int),
                 ("keep_layer_outputs", C.c_int), ("sparse_emb", C.c_int), ("assoc_cascade", C.c_int),
-                ("motion_lambda", C.c_double), ("iou_cost2", C.c_double), ("iou_cost3", C.c_double)]
+                ("motion_lambda", C.c_double), ("iou_cost2", C.c_double), ("iou_cost3", C.c_double),
+                ("fuse_block1", C.c_int)]
 
 
 class jde_layer_desc(C.Structure):

@@ -104,7 +104,7 @@ def test_set_tile_choice_refuses_codes_a_layer_cannot_run():
     try:
         codes = j.jde_tile_choice(h, 2, 320, 192)
         bad = list(codes)
-        bad[2] = 129                       # a 1x1 conv has no flat-window form
+        bad[5] = 129                       # a 1x1 conv has no flat-window form
         with pytest.raises(j.JdeError):
             j.jde_set_tile_choice(h, 2, 320, 192, bad)
         bad = list(codes)

@@ -127,6 +127,40 @@ def test_fused_stem_and_stride2_conv_match_the_bf16_scheme(in_w, in_h, n):
     assert exact >= 0.99, exact
 
 
+@pytest.mark.parametrize("in_w,in_h,n", [(320, 192, 2), (1088, 608, 2), (864, 480, 1)])
+def test_fused_first_residual_block_matches_the_bf16_scheme(in_w, in_h, n):
+    """The first stage's residual block (layers 2 and 3) fused into one kernel (fuse_block1 = 1):
+    its 1x1 output never leaves shared memory and its output, x + block(x), goes to its own tensor,
+    rounded once.  From the GPU's own block input (layer 1) the scheme computes layer 2 (bf16) and
+    layer 3 with the residual rounded once; the GPU's layer-3 output must agree up to float32-
+    accumulation flips: almost every element exact, and every element within one bfloat16 step plus
+    what a flip of one layer-2 value (one step at its largest magnitude) moves it by through the 3x3
+    (times the largest |weight|), twice."""
+    j = jde()
+    h = make_handle(j.JDE_BF16, max_batch=n, in_w=in_w, in_h=in_h, fuse_block1=1)
+    try:
+        frames = synth.frames_uniform(23, n, 1080, 1920)
+        forward(h, frames, in_w, in_h)
+        with pytest.raises(j.JdeError):
+            get_tensor(h, 2)                    # fused: the 1x1's output is not stored
+        x = get_tensor(h, 1)
+        t3 = get_tensor(h, 3)
+        assert j.jde_kernel_errors(h) == 0
+    finally:
+        j.jde_destroy(h)
+    layers = oracle_layers()
+    t2 = bf16.conv_layer(2, x, layers)
+    s3 = bf16.conv_layer(3, t2, layers, res=x, inplace=False)
+    w3 = bf16.bf16(net.fold_bn(layers[3])[0])
+    flip = float(np.max(np.abs(w3))) * float(bf16_ulp(np.max(np.abs(t2))))
+    exact = float(np.mean(t3 == s3))
+    bound = bf16_ulp(np.maximum(np.abs(t3), np.abs(s3))) + 2 * flip
+    over = float(np.max(np.abs(t3 - s3) / bound))
+    print(in_w, in_h, "layer 3 exact share", exact, "worst diff / bound", over)
+    assert over <= 1.0, over
+    assert exact >= 0.99, exact
+
+
 def test_bf16_end_to_end_error_is_the_scheme_s():
     """The default BF16 handle's heads against float64, next to the BF16 scheme's own heads against
     float64 on the same frames.  Two evaluations of the scheme decorrelate through the network (pinned

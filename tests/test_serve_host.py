@@ -95,7 +95,8 @@ def test_estimate_accounts_for_in_place_stages_the_fused_stem_and_the_sparse_emb
     """Host bookkeeping of the activation buffers (no GPU): with keep_layer_outputs = 0 every residual
     block's output shares its stage buffer (the 3x3 reduce-adds into the block input; the stride-16 and
     stride-8 stages live in their concat slices), and with sparse_emb = 1 the three f32 embedding maps
-    (two sets, zero halo) are replaced by two-set bf16 copies of their input maps."""
+    (two sets, zero halo) are replaced by two-set bf16 copies of their input maps; fuse_block1 = 1
+    keeps the first block's output in its own tensor and its 1x1 output (layer 2) on chip."""
     from paper_2011_03910_gb300 import jde
     n, W, H = 16, 1088, 608
     table = jde.jde_layer_table()
@@ -130,6 +131,13 @@ def test_estimate_accounts_for_in_place_stages_the_fused_stem_and_the_sparse_emb
     # the stem's output (32 channels at full size) is not stored when it is fused into layer 1
     saved += _act_bytes(n, sizes[0], table[0][1], 2)
     assert est(1, 0) - est(0, 0) == saved
+    cfg = jde.jde_default_config()
+    cfg.precision = jde.JDE_BF16
+    cfg.max_batch = n
+    cfg.sparse_emb = 0
+    cfg.fuse_block1 = 1
+    fused = jde.jde_estimate_device_bytes(cfg, W, H)
+    assert fused - est(0, 0) == _act_bytes(n, sizes[3], table[3][1], 2) - _act_bytes(n, sizes[2], table[2][1], 2)
     # sparse head: minus the padded f32 embedding maps, plus bf16 copies of their inputs (two sets each)
     emb = [59, 68, 77]
     dense = sum(2 * _act_bytes(n, sizes[l], 512, 4) for l in emb)
