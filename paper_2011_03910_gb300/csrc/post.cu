@@ -168,26 +168,42 @@ __device__ __forceinline__ bool iou_above(const float4& a, const float4& b, floa
 }
 
 // grid (col block, row block, frame), 64 threads: row i = rb*64 + t against columns cb*64 .. +63
-__global__ void nms_mask_kernel(const float4* boxes, const int* n_sorted, int kmax, float thr,
-                                unsigned long long* mask) {
-  const int n = blockIdx.z, rb = blockIdx.y, cb = blockIdx.x;
+// One block (two warps) per 64-row block of a frame's sorted candidates, looping over the column blocks
+// at or right of the diagonal that hold candidates: lane r of a warp holds row r's box and, per column
+// block, columns lane and lane + 32; for each of the warp's 32 rows the row box is broadcast and two
+// ballots give the row's 64-bit word (bit u: column cb * 64 + u comes later and overlaps it by IoU > thr),
+// which lane r keeps and stores.
+__global__ void __launch_bounds__(64) nms_mask_kernel(const float4* boxes, const int* n_sorted, int kmax, float thr,
+                                                      unsigned long long* mask) {
+  const int n = blockIdx.y, rb = blockIdx.x;
   const int K = n_sorted[n];
-  if (cb < rb || rb * 64 >= K || cb * 64 >= K) return;
-  __shared__ float4 cols[64];
-  const int t = threadIdx.x;
+  if (rb * 64 >= K) return;
+  const int nb = (K + 63) / 64, words = kmax / 64;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const float4* bx = boxes + (size_t)n * kmax;
-  if (cb * 64 + t < K) cols[t] = bx[cb * 64 + t];
-  __syncthreads();
-  const int i = rb * 64 + t;
-  if (i >= K) return;
-  const float4 bi = bx[i];
-  unsigned long long word = 0;
-  const int jend = min(64, K - cb * 64);
-  for (int u = 0; u < jend; ++u) {
-    const int j = cb * 64 + u;
-    if (j > i && iou_above(bi, cols[u], thr)) word |= 1ull << u;
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int row0 = rb * 64 + 32 * warp;
+  const int i_lane = row0 + lane;
+  const float4 mine = i_lane < K ? bx[i_lane] : zero;
+  const int rows = min(32, K - row0);   // warp-uniform; <= 0 for an empty half block
+  unsigned long long* out = mask + ((size_t)n * kmax + i_lane) * words;
+  for (int cb = rb; cb < nb; ++cb) {
+    const int j0 = cb * 64 + lane, j1 = j0 + 32;
+    const float4 c0 = j0 < K ? bx[j0] : zero, c1 = j1 < K ? bx[j1] : zero;
+    unsigned long long word = 0;
+    for (int r = 0; r < rows; ++r) {
+      const int i = row0 + r;
+      float4 bi;
+      bi.x = __shfl_sync(0xffffffffu, mine.x, r);
+      bi.y = __shfl_sync(0xffffffffu, mine.y, r);
+      bi.z = __shfl_sync(0xffffffffu, mine.z, r);
+      bi.w = __shfl_sync(0xffffffffu, mine.w, r);
+      const unsigned lo = __ballot_sync(0xffffffffu, j0 < K && j0 > i && iou_above(bi, c0, thr));
+      const unsigned hi = __ballot_sync(0xffffffffu, j1 < K && j1 > i && iou_above(bi, c1, thr));
+      if (lane == r) word = ((unsigned long long)hi << 32) | lo;
+    }
+    if (i_lane < K) out[cb] = word;
   }
-  mask[((size_t)n * kmax + i) * (kmax / 64) + cb] = word;
 }
 
 // one warp per frame: greedy scan of the bitmask in sorted order
@@ -548,7 +564,7 @@ cudaError_t post_launch(const float* const* heads, const HeadGeom& g, float conf
   jde_count_launch();
   prep_kernel<<<gp, 128, 0, st>>>(heads[0], heads[1], heads[2], g, b.sorted, b.n_sorted, b.kmax, b.boxes, b.conf,
                                   b.cls);
-  dim3 gm(b.kmax / 64, b.kmax / 64, n);
+  dim3 gm(b.kmax / 64, n);
   jde_count_launch();
   nms_mask_kernel<<<gm, 64, 0, st>>>(b.boxes, b.n_sorted, b.kmax, nms_iou, b.mask);
   const int wpb = 4;
