@@ -61,6 +61,13 @@ def parse():
     p.add_argument("--profile-step", action="store_true",
                    help="after the warm-up, run one step inside cudaProfilerStart/Stop (for ncu --profile-from-start "
                         "off) and exit without timing")
+    p.add_argument("--dependent-launch", type=int, default=-1, choices=[-1, 0, 1],
+                   help="jde_config.dependent_launch of the BF16 handles in the single-forward-stream steps "
+                        "(-1: the library default)")
+    p.add_argument("--fp8-dependent-launch", type=int, default=-1, choices=[-1, 0, 1],
+                   help="dependent_launch of the E4M3 handles (-1: the library default)")
+    p.add_argument("--pipeline-dependent-launch", type=int, default=0, choices=[0, 1],
+                   help="dependent_launch of the two BF16 handles while two forward streams share the GPU")
     p.add_argument("--latency-batches", type=int, default=220,
                    help="batches of the pipelined step whose latency percentiles are reported (0: skip)")
     return p.parse_args()
@@ -201,7 +208,7 @@ def build_heads_device(torch, clips, t, device):
     return dets + embs
 
 
-def run_fp8(torch, jde, dev, blob, stream, table, B=32, K=20, autotune=True, sparse_emb=0):
+def run_fp8(torch, jde, dev, blob, stream, table, B=32, K=20, autotune=True, sparse_emb=0, dependent_launch=-1):
     """E4M3 network at 1088x608, batch 32: activation amax from 64 seeded calibration frames run through
     a BF16 handle that keeps every layer output (jde_act_amax, elementwise max over 4 batches of 16),
     then letterbox + forward + decode + confidence filter + NMS (jde_detect_batch) captured in one
@@ -228,6 +235,8 @@ def run_fp8(torch, jde, dev, blob, stream, table, B=32, K=20, autotune=True, spa
     cfg.max_batch = B
     cfg.max_streams = 1
     cfg.device = dev.index or 0
+    if dependent_launch >= 0:
+        cfg.dependent_launch = dependent_launch
     # synthetic weights on noise frames keep ~1600 detections per frame after NMS (256 rows kept per
     # frame here); at that count the dense embedding maps cost less than the sparse head
     cfg.sparse_emb = sparse_emb
@@ -317,6 +326,7 @@ def run_fp8(torch, jde, dev, blob, stream, table, B=32, K=20, autotune=True, spa
     return {"fps": B * 1000.0 / ms, "ms_per_batch": ms, "batch": B, "steps": K, "graph": True,
             "streams": "two handles, one CUDA graph each, replayed on two streams with batches alternating",
             "fps_single_stream": B * 1000.0 / ms1,
+            "dependent_launch": int(cfg.dependent_launch),
             "autotuned_tiles_changed": changed,
             "what": "letterbox + E4M3 forward + decode + confidence filter + NMS + embedding L2, one CUDA graph "
                     "per batch; two handles with a graph each, replayed on two streams with batches alternating",
@@ -608,6 +618,8 @@ def main():
     # the timed post-processing reads planted head maps (embeddings included): the forward computes
     # the network's dense embedding maps too, so no part of the network is skipped
     cfg.sparse_emb = 0
+    if args.dependent_launch >= 0:
+        cfg.dependent_launch = args.dependent_launch
     h = jde.jde_create(cfg, blob)
     st = torch.cuda.current_stream()
     tiles = None
@@ -713,6 +725,11 @@ def main():
         jde.jde_set_profile_events(hh)
     conv_ms1 = sum(p[1].elapsed_time(p[2]) for p in prof) / K1
     fwd_ms1 = sum(p[0].elapsed_time(p[2]) for p in prof) / K1
+    # two forward streams: each fills the SMs the other's layer tails leave idle, which a dependent
+    # launch (its CTAs set up early and wait on those SMs) would take from it
+    single_dl = int(cfg.dependent_launch)
+    for hh in hs:
+        jde.jde_set_dependent_launch(hh, args.pipeline_dependent_launch)
 
     sampler = ClockSampler(local)
     sampler.start()
@@ -756,6 +773,8 @@ def main():
         step_ms = [fwd_start[u].elapsed_time(post_done[u]) for u in range(t_lat, t)]
         drain()
     F0 = F[0]
+    for hh in hs:
+        jde.jde_set_dependent_launch(hh, single_dl)
 
     # batch sweep (the batches of the BF16 configuration): the single-forward-stream pipelined step on
     # n frames / n streams, one handle
@@ -858,6 +877,8 @@ def main():
 
     # e2e: host frames in (pinned), tracks out to host, through the same C ABI and the same two-handle
     # pipeline: jde_forward copies each batch's frames from pinned host memory on its forward stream
+    for hh in hs:
+        jde.jde_set_dependent_launch(hh, args.pipeline_dependent_launch)
     pinned = [f.cpu().pin_memory() for f in frames]
     tr_h = [np.zeros((B, tcap), np.int64), np.zeros((B, tcap, 4), np.float32), np.zeros((B, tcap), np.int32),
             np.zeros((B, tcap), np.int32), np.zeros(B, np.int32)]
@@ -920,6 +941,8 @@ def main():
         for x in fh:
             jde.jde_set_profile_events(x)
         fconv = sum(p[1].elapsed_time(p[2]) for p in fprof) / K1
+        for x in fh:
+            jde.jde_set_dependent_launch(x, args.pipeline_dependent_launch)
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(F[0])
         F[1].wait_event(f0)
@@ -992,7 +1015,8 @@ def main():
 
     fp8 = None
     if not args.no_fp8 and rank == 0:
-        fp8 = run_fp8(torch, jde, dev, blob, F0, table, autotune=not args.no_autotune)
+        fp8 = run_fp8(torch, jde, dev, blob, F0, table, autotune=not args.no_autotune,
+                      dependent_launch=args.fp8_dependent_launch)
 
     serving = None
     if args.serve_seconds > 0 and rank == 0:
@@ -1013,6 +1037,7 @@ def main():
             "config": {"workload": f"JDE BF16, 1920x1080 uint8 -> 1088x608 letterbox, batch {B} ({B} streams), "
                                    f"{args.objects} planted objects/stream for post-processing + tracking",
                        "batch": B, "in": [IN_W, IN_H], "src": [SRC_W, SRC_H], "parallelism": f"replicas{world}",
+                       "dependent_launch": {"single_stream": single_dl, "pipelined": args.pipeline_dependent_launch},
                        "l2": "inputs larger than L2: ~5 GB of activations per step, 4 rotating 100 MB frame batches"},
             "latency_ms": {"p50": srt[len(srt) // 2] if srt else None,
                            "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))] if srt else None,

@@ -116,6 +116,11 @@ typedef struct {
                            is then refused by jde_get_tensor; 0.6 GB less DRAM traffic per batch-16
                            step, the same time alone, 2% slower when two batches share the GPU);
                            0 (default): two kernels, the block in place */
+  int dependent_launch; /* tensor-core handles, 1 (default): each convolution kernel is launched as a
+                           programmatic dependent of the kernel before it in the stream, so its launch and
+                           set-up (barriers, tensor memory, cluster) overlap the previous layer's last work
+                           units; it waits for that kernel to complete before it reads or writes global
+                           memory, so results are identical; 0: plain stream order */
 } jde_config;
 
 /* One layer of the network as this library builds it (for the weights blob). */
@@ -288,6 +293,13 @@ unsigned long long jde_launch_count(void);
  * convolution and conv_end after the last one, on the call's stream.  The
  * events stay owned by the caller. */
 jde_status jde_set_profile_events(jde_handle* h, void* forward_begin, void* conv_begin, void* conv_end);
+
+/* Sets the handle's jde_config.dependent_launch (0 or 1) for the launches it makes from now on (a CUDA
+ * graph captured earlier keeps the launches it captured).  Dependent launches shorten one forward
+ * stream's convolution chain; where two forwards share the GPU on two streams, plain stream order lets
+ * each fill the SMs the other's layer tails leave idle.  Results are identical either way.
+ * JDE_ERR_INVALID_ARG for another value. */
+jde_status jde_set_dependent_launch(jde_handle* h, int on);
 
 /* Failure-detection self-test (no counterpart in the paper).  Every kernel that waits on another warp
  * or CTA waits on an mbarrier with a cycle limit (about 2^32 SM cycles, two seconds); when the limit

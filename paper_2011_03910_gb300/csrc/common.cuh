@@ -50,6 +50,14 @@ JDE_DEV void flag_error(int* err, int bit) {
 
 JDE_DEV uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// ----------------------------------------------------------------------------- dependent launch
+// A kernel launched with programmatic stream serialization may start while the kernel before it
+// in the stream is still running; grid_dep_wait() returns once that kernel has completed and its
+// memory operations are visible (at once for a kernel launched without the attribute), and
+// grid_dep_trigger() lets the next kernel be scheduled before this one has finished.
+JDE_DEV void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+JDE_DEV void grid_dep_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ----------------------------------------------------------------------------- mbarrier
 JDE_DEV void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");

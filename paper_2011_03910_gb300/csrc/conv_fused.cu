@@ -363,6 +363,8 @@ __global__ void __launch_bounds__(F_THREADS, 1) stem_s2_kernel(const __grid_cons
     for (int u = u0; u < a.total; u += ustep, ++lt) {   // a failed wait ends it (bar_and below)
       const uint32_t ab = lt & 1u;
       bool ok = lane == 0 ? mbar_wait(&acc_full[ab], (lt >> 1) & 1u) : true;
+      // the CTA's last accumulator is complete: the next layer's kernel may launch and set up
+      if (u + ustep >= a.total && elected) grid_dep_trigger();
       ok = bar_and(ok, 1, 128);               // the four warps take one path
       if (!ok) {
         if (lane == 0) {

@@ -300,6 +300,9 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
   if constexpr (CG == 2) cluster_sync();   // both CTAs' barriers initialised before any remote signal
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  // launched as a dependent of the previous layer's kernel: the set-up above overlaps its tail, and
+  // no thread touches global memory (that kernel's output, or this one's) before it has completed
+  grid_dep_wait();
 
   if (warp < GW && a.mode == 2) {
     // ---------------- stem producer: gather warp w fills the stage of every GW-th tile with the
@@ -703,6 +706,9 @@ __global__ void __launch_bounds__(tc_threads(GW), 1) conv_tc_kernel(const __grid
         flag_error(c.err, KERR_TIMEOUT);
         atomicExch(&s_abort, 1);
       }
+      // the CTA's last accumulator is complete: only its epilogue is left, so the next layer's kernel
+      // may launch and set up (it waits for this grid before touching global memory)
+      if (u + ustep >= nunits && gtid == 0) grid_dep_trigger();
       ok = bar_and(ok, bar_id, 128);        // the group's four warps take the same path
       tc_fence_after();
       const TileCoord tc = tile_coord(a, tile, BN);
@@ -1125,15 +1131,30 @@ cudaError_t launch_cfg(const TcPlan& p, const TcArgs& a, cudaStream_t st, int sm
       attr_set[dev] = smem;
     }
   }
+  // p.pdl: a programmatic dependent of the kernel before it in the stream (its set-up overlaps that
+  // kernel's last work units; the kernel waits for it before touching global memory)
+  cudaLaunchAttribute dep;
+  dep.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  dep.val.programmaticStreamSerializationAllowed = 1;
   if (CG == 1) {
     const int tiles = p.m_tiles * p.n_tiles;
     const int grid = tiles < sms ? tiles : sms;
     jde_count_launch();
-    kernel<<<grid, tc_threads(GW), smem, st>>>(p, a);
-    return cudaGetLastError();
+    if (!p.pdl) {
+      kernel<<<grid, tc_threads(GW), smem, st>>>(p, a);
+      return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg1 = {};
+    cfg1.gridDim = dim3(grid);
+    cfg1.blockDim = dim3(tc_threads(GW));
+    cfg1.dynamicSmemBytes = (size_t)smem;
+    cfg1.stream = st;
+    cfg1.attrs = &dep;
+    cfg1.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg1, kernel, p, a);
   }
   // CTA pairs: 2-CTA clusters, as many as can be resident at once (persistent)
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = 2;
   attr[0].val.clusterDim.y = 1;
@@ -1161,6 +1182,10 @@ cudaError_t launch_cfg(const TcPlan& p, const TcArgs& a, cudaStream_t st, int sm
   }
   const int clusters = a.total_units < mc ? a.total_units : mc;
   cfg.gridDim = dim3(2 * clusters);
+  if (p.pdl) {
+    attr[1] = dep;
+    cfg.numAttrs = 2;
+  }
   jde_count_launch();
   return cudaLaunchKernelEx(&cfg, kernel, p, a);
 }

@@ -51,6 +51,7 @@ struct TcPlan {
   int kel;                       // elements of one k-block along K (bf16: bkc, E4M3: 2 * bkc)
   int msub;                      // mode 4: M tiles of 128 rows per CTA and work unit (1 or 2)
   int w4deep;                    // mode 4 with 128-byte k-blocks: 1 = the deeper weight ring
+  int pdl;                       // 1: launched as a programmatic dependent of the previous kernel
   ConvSpec spec;
 };
 // Fill plan (tensor maps and grid) for a conv whose input is a padded bf16

@@ -484,6 +484,7 @@ jde_status get_plan(jde_handle* h, ResBuffers* rb, int n, Plan** out) {
       // tile code: output channels per tile, + 1 for two 128-row M sub-tiles per CTA (flat-window 3x3)
       if (!conv_tc_plan(p.tc[l], c, w, h->w[l].cout_pad_tc, bn & ~1, msg, sizeof(msg), (bn & 1) ? 2 : 1))
         return fail(h, JDE_ERR_UNSUPPORTED, "layer %zu: %s", l, msg);
+      p.tc[l].pdl = h->cfg.dependent_launch;
     }
   }
   if (bf16 && fused_stem_cfg(h->cfg)) {
@@ -852,6 +853,7 @@ void jde_default_config(jde_config* c) {
   c->iou_cost2 = 0.5;
   c->iou_cost3 = 0.3;
   c->fuse_block1 = 0;
+  c->dependent_launch = 1;
 }
 
 int jde_layer_table(jde_layer_desc* out, int cap) {
@@ -902,7 +904,8 @@ jde_status jde_create(const jde_config* cfg, const void* weights, size_t nbytes,
       c.max_streams < 1 || c.max_tracks < 1 || c.max_track_dets < 1 || c.max_track_dets > 4096 ||
       c.max_tracks > 4096 || c.keep_layer_outputs < 0 || c.keep_layer_outputs > 2 || c.assoc_cascade < 0 ||
       c.assoc_cascade > 1 || !(c.motion_lambda >= 0.0 && c.motion_lambda <= 1.0) || !(c.iou_cost2 >= 0.0) ||
-      !(c.iou_cost3 >= 0.0) || c.fuse_block1 < 0 || c.fuse_block1 > 1)
+      !(c.iou_cost3 >= 0.0) || c.fuse_block1 < 0 || c.fuse_block1 > 1 || c.dependent_launch < 0 ||
+      c.dependent_launch > 1)
     return fail(nullptr, JDE_ERR_INVALID_ARG, "config out of range");
   if (cudaSetDevice(c.device) != cudaSuccess) return fail(nullptr, JDE_ERR_CUDA, "cudaSetDevice(%d)", c.device);
   jde_handle* h = new jde_handle();
@@ -1475,6 +1478,15 @@ jde_status jde_set_profile_events(jde_handle* h, void* forward_begin, void* conv
   h->prof[0] = static_cast<cudaEvent_t>(forward_begin);
   h->prof[1] = static_cast<cudaEvent_t>(conv_begin);
   h->prof[2] = static_cast<cudaEvent_t>(conv_end);
+  return JDE_OK;
+}
+
+jde_status jde_set_dependent_launch(jde_handle* h, int on) {
+  if (!h) return fail(nullptr, JDE_ERR_INVALID_ARG, "handle is NULL");
+  if (on != 0 && on != 1) return fail(h, JDE_ERR_INVALID_ARG, "jde_set_dependent_launch: %d is not 0 or 1", on);
+  h->cfg.dependent_launch = on;
+  for (auto& kv : h->plans)
+    for (TcPlan& t : kv.second.tc) t.pdl = on;
   return JDE_OK;
 }
 

@@ -35,7 +35,7 @@ class jde_config(C.Structure):
                 ("max_tracks", C.c_int), ("max_track_dets", C.c_int), ("device", C.c_int),
                 ("keep_layer_outputs", C.c_int), ("sparse_emb", C.c_int), ("assoc_cascade", C.c_int),
                 ("motion_lambda", C.c_double), ("iou_cost2", C.c_double), ("iou_cost3", C.c_double),
-                ("fuse_block1", C.c_int)]
+                ("fuse_block1", C.c_int), ("dependent_launch", C.c_int)]
 
 
 class jde_layer_desc(C.Structure):
@@ -96,6 +96,7 @@ _sig = {
     "jde_estimate_device_bytes": (C.c_int, [C.POINTER(jde_config), C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
     "jde_launch_count": (C.c_ulonglong, []),
     "jde_set_profile_events": (C.c_int, [_P, _P, _P, _P]),
+    "jde_set_dependent_launch": (C.c_int, [_P, C.c_int]),
     "jde_selftest_wait": (C.c_int, [_P, C.c_longlong, C.POINTER(C.c_int), _P]),
     "jde_postprocess_noalloc": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float, C.c_float,
                                           C.c_int, C.POINTER(jde_dets), _P, C.c_char_p, C.c_size_t]),
@@ -291,6 +292,10 @@ def jde_set_profile_events(h, forward_begin=None, conv_begin=None, conv_end=None
     """Events are torch.cuda.Event objects (recorded by the library on the call's stream) or None."""
     ev = [None if e is None else e.cuda_event for e in (forward_begin, conv_begin, conv_end)]
     _check(h, lib.jde_set_profile_events(h, *ev))
+
+
+def jde_set_dependent_launch(h, on):
+    _check(h, lib.jde_set_dependent_launch(h, int(on)))
 
 
 def jde_postprocess_noalloc(heads, n, in_w, in_h, src_w, src_h, conf_thresh, nms_iou, max_cand, dets: jde_dets,
