@@ -8,7 +8,9 @@
 //   * warp 0 / lane 0 loads the letterbox window (RGB0 bf16, 8 bytes per pixel) with one TMA box;
 //   * eight gather warps build the stem's im2col rows of the 561 window pixels (27 values, (ky, kx, c)
 //     order, then three 1.0 columns, padded to 32 bf16) in five 128-row, 64-byte-swizzled operand
-//     tiles in shared memory; a pixel outside the image gets an all-zero row;
+//     tiles in shared memory, one row per thread: warps 1-4 fill tiles 0, 2 and 4, warps 14-17
+//     tiles 1 and 3, each tile with its own full / empty barriers, so a tile is refilled for the next
+//     unit as soon as its own MMAs are done; a pixel outside the image gets an all-zero row;
 //   * the MMA warp issues the stem GEMM (5 tiles x M=128, N=32, K=32) into TMEM: the stem weights carry
 //     the folded BN bias in their K columns 27..29, split into three bfloat16 parts whose sum is the
 //     float32 bias, so the accumulator holds conv + bias, and exactly zero outside the image (the
@@ -22,7 +24,7 @@
 //     bf16 into a 128-byte-swizzled staging tile and TMA-store it.
 // The epilogues therefore do no per-element bias add and no per-element select.
 // Letterbox windows, stem accumulators, parity windows and output accumulators are double-buffered;
-// the im2col tiles are single-buffered (the stem MMAs free them quickly).  Every wait is bounded: on a
+// the im2col tiles are single-buffered, handed over tile by tile.  Every wait is bounded: on a
 // timeout the CTA flags the error word, stops issuing work, and releases TMEM.
 #include <stdio.h>
 
@@ -105,16 +107,16 @@ __global__ void __launch_bounds__(F_THREADS, 1) stem_s2_kernel(const __grid_cons
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + O_BAR);
   uint64_t* lb_full = bar;          // [2]
   uint64_t* lb_empty = bar + 2;     // [2]
-  uint64_t* col_full = bar + 4;     // [1]
-  uint64_t* col_empty = bar + 5;    // [1]
-  uint64_t* sacc_full = bar + 6;    // [2]
-  uint64_t* sacc_empty = bar + 8;   // [2]
-  uint64_t* win_full = bar + 10;    // [2]
-  uint64_t* win_empty = bar + 12;   // [2]
-  uint64_t* acc_full = bar + 14;    // [2]
-  uint64_t* acc_empty = bar + 16;   // [2]
-  uint64_t* w_full = bar + 18;      // [1]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 20);
+  uint64_t* col_full = bar + 4;     // [F_MT] im2col tile t gathered
+  uint64_t* col_empty = bar + 9;    // [F_MT] im2col tile t consumed by its MMAs
+  uint64_t* sacc_full = bar + 14;   // [2]
+  uint64_t* sacc_empty = bar + 16;  // [2]
+  uint64_t* win_full = bar + 18;    // [2]
+  uint64_t* win_empty = bar + 20;   // [2]
+  uint64_t* acc_full = bar + 22;    // [2]
+  uint64_t* acc_empty = bar + 24;   // [2]
+  uint64_t* w_full = bar + 26;      // [1]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 27);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -128,8 +130,10 @@ __global__ void __launch_bounds__(F_THREADS, 1) stem_s2_kernel(const __grid_cons
       mbar_init(&acc_full[i], 1);
       mbar_init(&acc_empty[i], 4);
     }
-    mbar_init(col_full, F_GATHER);
-    mbar_init(col_empty, 1);
+    for (int t = 0; t < F_MT; ++t) {
+      mbar_init(&col_full[t], F_GATHER / 2);   // the four warps of the tile's gather group
+      mbar_init(&col_empty[t], 1);
+    }
     mbar_init(w_full, 1);
     fence_barrier_init();
     s_abort = 0;
@@ -173,70 +177,70 @@ __global__ void __launch_bounds__(F_THREADS, 1) stem_s2_kernel(const __grid_cons
       }
     }
   } else if ((warp >= 1 && warp <= 4) || warp >= 14) {
-    // ---------------- gather: im2col rows of the stem window from the letterbox window
-    const int g = warp <= 4 ? threadIdx.x - 32 : threadIdx.x - 14 * 32 + 128;   // 0..255
+    // ---------------- gather: im2col rows of the stem window from the letterbox window; group 0
+    // (warps 1-4) fills tiles 0, 2, 4 and group 1 (warps 14-17) tiles 1, 3, one row per thread
+    const int grp = warp <= 4 ? 0 : 1;
+    const int rr = warp <= 4 ? threadIdx.x - 32 : threadIdx.x - 14 * 32;   // tile row 0..127
     uint32_t lt = 0;
     for (int u = u0; u < a.total; u += ustep, ++lt) {
       if (__shfl_sync(0xffffffffu, f_aborted(&s_abort) ? 1 : 0, 0)) break;   // warp-uniform
       const uint32_t b = lt & 1u;
-      bool ok = true;
-      if (lane == 0) {
-        ok = mbar_wait(&lb_full[b], (lt >> 1) & 1u);
-        if (ok && lt >= 1) ok = mbar_wait(col_empty, (lt - 1) & 1u);
-        if (!ok) {
+      bool ok = lane == 0 ? mbar_wait(&lb_full[b], (lt >> 1) & 1u) : true;
+      const uint8_t* lbw = sLB + b * F_LB_SLOT;
+      const int r_g = u % per_img;
+      const int oy0 = (r_g / a.tiles_x) * F_TH, ox0 = (r_g % a.tiles_x) * F_TW;
+      for (int t = grp; t < F_MT; t += 2) {
+        if (lane == 0 && ok && lt >= 1) ok = mbar_wait(&col_empty[t], (lt - 1) & 1u);   // the tile's last MMAs
+        if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;   // the warp takes one path
+        const int m = 128 * t + rr;            // window pixel = im2col row
+        if (m < F_WPIX) {
+          const int wy = m / F_WX, wx = m - (m / F_WX) * F_WX;
+          uint8_t* row = sCol + t * F_COL_TILE;
+          const int sy = 2 * oy0 - 1 + wy, sx = 2 * ox0 - 1 + wx;
+          // outside the image: an all-zero row (so a zero accumulator), selected without a branch; every tap
+          // of the window lies inside the loaded letterbox window, so the loads below are always in bounds
+          const uint32_t keep = (sy >= 0 && sy < a.H && sx >= 0 && sx < a.W) ? 0xFFFFFFFFu : 0u;
+          // tap (ky, kx) of window pixel (wy, wx): letterbox window row wy + ky, column wx + kx + 1; a tap is
+          // 8 bytes, lo = (R, G), hi = (B, 0) as bf16 pairs
+          uint2 q[9];
+          const uint8_t* src = lbw + wy * F_LB_ROW + (wx + 1) * 8;
+#pragma unroll
+          for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+            for (int kx = 0; kx < 3; ++kx) q[ky * 3 + kx] = *reinterpret_cast<const uint2*>(src + ky * F_LB_ROW + kx * 8);
+          // the 27 values (tap, channel) packed two per word, then 1.0 x 3 (the bias columns) and 0 x 2:
+          // taps 2i, 2i+1 give three words (R G | B R' | G' B')
+          uint32_t w[16];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const uint2 ta = q[2 * i], tb = q[2 * i + 1];
+            w[3 * i] = ta.x;
+            w[3 * i + 1] = __byte_perm(ta.y, tb.x, 0x5410);
+            w[3 * i + 2] = __byte_perm(tb.x, tb.y, 0x5432);
+          }
+          w[12] = q[8].x;
+          w[13] = (q[8].y & 0xFFFFu) | 0x3F800000u;
+          w[14] = 0x3F803F80u;
+          w[15] = 0u;
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            *reinterpret_cast<uint4*>(row + rr * 64 + ((k ^ ((rr >> 1) & 3)) << 4)) =
+                make_uint4(w[4 * k] & keep, w[4 * k + 1] & keep, w[4 * k + 2] & keep, w[4 * k + 3] & keep);
+        }
+        fence_proxy_async();   // generic-proxy writes -> visible to the MMAs
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&col_full[t]);
+      }
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;   // lane 0's waits decide for the warp
+      if (!ok) {
+        if (lane == 0) {
           flag_error(a.err, KERR_TIMEOUT);
           atomicExch(&s_abort, 1);
         }
+        break;
       }
-      if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;   // the warp takes one path
-      const uint8_t* lbw = sLB + b * F_LB_SLOT;
-      const int img_g = u / per_img, r_g = u % per_img;
-      const int oy0 = (r_g / a.tiles_x) * F_TH, ox0 = (r_g % a.tiles_x) * F_TW;
-      (void)img_g;
-#pragma unroll
-      for (int i = 0; i < (F_WPIX + 32 * F_GATHER - 1) / (32 * F_GATHER); ++i) {
-        const int m = g + 32 * F_GATHER * i;   // window pixel = im2col row
-        if (m >= F_WPIX) continue;
-        const int wy = m / F_WX, wx = m - (m / F_WX) * F_WX;
-        const int t = m >> 7, rr = m & 127;     // operand tile and its row
-        uint8_t* row = sCol + t * F_COL_TILE;
-        const int sy = 2 * oy0 - 1 + wy, sx = 2 * ox0 - 1 + wx;
-        // outside the image: an all-zero row (so a zero accumulator), selected without a branch; every tap
-        // of the window lies inside the loaded letterbox window, so the loads below are always in bounds
-        const uint32_t keep = (sy >= 0 && sy < a.H && sx >= 0 && sx < a.W) ? 0xFFFFFFFFu : 0u;
-        // tap (ky, kx) of window pixel (wy, wx): letterbox window row wy + ky, column wx + kx + 1; a tap is
-        // 8 bytes, lo = (R, G), hi = (B, 0) as bf16 pairs
-        uint2 q[9];
-        const uint8_t* src = lbw + wy * F_LB_ROW + (wx + 1) * 8;
-#pragma unroll
-        for (int ky = 0; ky < 3; ++ky)
-#pragma unroll
-          for (int kx = 0; kx < 3; ++kx) q[ky * 3 + kx] = *reinterpret_cast<const uint2*>(src + ky * F_LB_ROW + kx * 8);
-        // the 27 values (tap, channel) packed two per word, then 1.0 x 3 (the bias columns) and 0 x 2:
-        // taps 2i, 2i+1 give three words (R G | B R' | G' B')
-        uint32_t w[16];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const uint2 ta = q[2 * i], tb = q[2 * i + 1];
-          w[3 * i] = ta.x;
-          w[3 * i + 1] = __byte_perm(ta.y, tb.x, 0x5410);
-          w[3 * i + 2] = __byte_perm(tb.x, tb.y, 0x5432);
-        }
-        w[12] = q[8].x;
-        w[13] = (q[8].y & 0xFFFFu) | 0x3F800000u;
-        w[14] = 0x3F803F80u;
-        w[15] = 0u;
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-          *reinterpret_cast<uint4*>(row + rr * 64 + ((k ^ ((rr >> 1) & 3)) << 4)) =
-              make_uint4(w[4 * k] & keep, w[4 * k + 1] & keep, w[4 * k + 2] & keep, w[4 * k + 3] & keep);
-      }
-      fence_proxy_async();   // generic-proxy writes -> visible to the MMAs
       __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(col_full);
-        mbar_arrive(&lb_empty[b]);
-      }
+      if (lane == 0) mbar_arrive(&lb_empty[b]);   // the letterbox window is read
     }
   } else if (warp == 5) {
     // ---------------- MMA issuer: stem of unit lt, then the stride-2 conv of unit lt - 1
@@ -278,18 +282,21 @@ __global__ void __launch_bounds__(F_THREADS, 1) stem_s2_kernel(const __grid_cons
       };
       for (int u = u0; ok && u < a.total && !f_aborted(&s_abort); u += ustep, ++lt) {
         const uint32_t sb = lt & 1u;
-        ok = mbar_wait(col_full, lt & 1u);
-        if (ok && lt >= 2) ok = mbar_wait(&sacc_empty[sb], ((lt >> 1) - 1) & 1u);
+        if (lt >= 2) ok = mbar_wait(&sacc_empty[sb], ((lt >> 1) - 1) & 1u);
         if (!ok) break;
-        tc_fence_after();
         const uint32_t d0 = tmem + T_STEM + sb * (F_MT * 32);
+        // each im2col tile as soon as its gather group has filled it; its barrier frees it for the next unit
 #pragma unroll
-        for (int t = 0; t < F_MT; ++t)
+        for (int t = 0; t < F_MT; ++t) {
+          if (!(ok = mbar_wait(&col_full[t], lt & 1u))) break;
+          tc_fence_after();
 #pragma unroll
           for (int kk = 0; kk < 2; ++kk)
             umma_bf16(d0 + t * 32, desc_add(col_d, (uint32_t)(t * F_COL_TILE) / 16 + 2 * kk), desc_add(w0_d, 2 * kk),
                       id0, kk);
-        umma_commit(col_empty);
+          umma_commit(&col_empty[t]);
+        }
+        if (!ok) break;
         umma_commit(&sacc_full[sb]);
         if (lt >= 1) ok = stage2(lt - 1);
       }
