@@ -174,84 +174,90 @@ __global__ void prep_kernel(StepArgs a, Slots sl) {
 }
 
 // ---------------------------------------------------------------- cost + gate
-// 32 tracks x 32 detections per CTA, 256 threads: thread (tx, ty) owns det tx, tracks 4ty..4ty+3.
+// 32 tracks x 32 detections per tile, 256 threads: thread (tx, ty) owns det tx, tracks 4ty..4ty+3.
+// The blocks of a stream (blockIdx.y) loop over the tiles its track and detection counts need (the
+// counts live on the device), so the grid does not scale with the track and detection capacities.
+constexpr int COST_BLOCKS = 8;   // blocks per stream
 __global__ void cost_kernel(StepArgs a, Slots sl) {
-  const int b = blockIdx.z;
+  const int b = blockIdx.y;
   const int s = a.dslots ? a.dslots[b] : sl.stream[b];
   const int T = a.t.max_tracks;
   const int nt = a.t.n_tracks[s];
   const int D = det_count(a, b);
-  const int k0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
-  if (k0 >= nt || j0 >= D) return;
+  const int ntx = (nt + 31) / 32, nty = (D + 31) / 32;
   __shared__ float Es[32][33];
   __shared__ float Ds[32][33];
   __shared__ int slot_s[32];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  if (threadIdx.x < 32) slot_s[threadIdx.x] = k0 + threadIdx.x < nt ? a.t.order[(size_t)s * T + k0 + threadIdx.x] : -1;
-  __syncthreads();
-  // compensated f32 dot product: each product's rounding error (fma) and each sum's rounding error
-  // (Neumaier) go into c, so s + c is the dot product of the f32 inputs to ~1e-7, well inside the
-  // 1e-6 band in which a threshold decision counts as a tie
-  float acc[4] = {0.f, 0.f, 0.f, 0.f}, comp[4] = {0.f, 0.f, 0.f, 0.f};
-  const float* rows = a.rows + (size_t)b * a.cap * 518;
-  for (int c0 = 0; c0 < 512; c0 += 32) {
-    for (int e = threadIdx.x; e < 32 * 32; e += 256) {
-      const int r = e >> 5, cc = e & 31;
-      const int sl2 = slot_s[r];
-      Es[r][cc] = sl2 >= 0 ? a.t.emb[((size_t)s * T + sl2) * 512 + c0 + cc] : 0.f;
-      Ds[r][cc] = j0 + r < D ? rows[(size_t)(j0 + r) * 518 + 6 + c0 + cc] : 0.f;
-    }
+  for (int tile = blockIdx.x; tile < ntx * nty; tile += gridDim.x) {
+    const int k0 = (tile % ntx) * 32, j0 = (tile / ntx) * 32;
+    __syncthreads();   // the previous tile's reads of slot_s are done
+    if (threadIdx.x < 32) slot_s[threadIdx.x] = k0 + threadIdx.x < nt ? a.t.order[(size_t)s * T + k0 + threadIdx.x] : -1;
     __syncthreads();
-#pragma unroll 8
-    for (int cc = 0; cc < 32; ++cc) {
-      const float dv = Ds[tx][cc];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float ev = Es[ty * 4 + q][cc];
-        const float p = ev * dv;
-        const float pe = fmaf(ev, dv, -p);       // exact product error
-        const float t = acc[q] + p;
-        comp[q] += (fabsf(acc[q]) >= fabsf(p) ? (acc[q] - t) + p : (p - t) + acc[q]) + pe;
-        acc[q] = t;
+    // compensated f32 dot product: each product's rounding error (fma) and each sum's rounding error
+    // (Neumaier) go into c, so s + c is the dot product of the f32 inputs to ~1e-7, well inside the
+    // 1e-6 band in which a threshold decision counts as a tie
+    float acc[4] = {0.f, 0.f, 0.f, 0.f}, comp[4] = {0.f, 0.f, 0.f, 0.f};
+    const float* rows = a.rows + (size_t)b * a.cap * 518;
+    for (int c0 = 0; c0 < 512; c0 += 32) {
+      for (int e = threadIdx.x; e < 32 * 32; e += 256) {
+        const int r = e >> 5, cc = e & 31;
+        const int sl2 = slot_s[r];
+        Es[r][cc] = sl2 >= 0 ? a.t.emb[((size_t)s * T + sl2) * 512 + c0 + cc] : 0.f;
+        Ds[r][cc] = j0 + r < D ? rows[(size_t)(j0 + r) * 518 + 6 + c0 + cc] : 0.f;
       }
+      __syncthreads();
+#pragma unroll 8
+      for (int cc = 0; cc < 32; ++cc) {
+        const float dv = Ds[tx][cc];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float ev = Es[ty * 4 + q][cc];
+          const float p = ev * dv;
+          const float pe = fmaf(ev, dv, -p);       // exact product error
+          const float t = acc[q] + p;
+          comp[q] += (fabsf(acc[q]) >= fabsf(p) ? (acc[q] - t) + p : (p - t) + acc[q]) + pe;
+          acc[q] = t;
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
-  }
-  const int j = j0 + tx;
-  if (j >= D) return;
-  double z[4];
-  measurement(rows + (size_t)j * 518, z);
-  const bool trans = nt > D;
-  const int M = trans ? nt : D;
-  double* A = a.t.cost + (size_t)b * T * a.t.max_dets;
+    const int j = j0 + tx;
+    if (j >= D) continue;
+    double z[4];
+    measurement(rows + (size_t)j * 518, z);
+    const bool trans = nt > D;
+    const int M = trans ? nt : D;
+    double* A = a.t.cost + (size_t)b * T * a.t.max_dets;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int k = k0 + ty * 4 + q;
-    if (k >= nt) break;
-    const int slot = slot_s[ty * 4 + q];
-    const double* L = a.t.gate_l + ((size_t)b * T + slot) * 16;
-    const double* zh = a.t.gate_z + ((size_t)b * T + slot) * 4;
-    double w[4], d2 = 0.0;
+    for (int q = 0; q < 4; ++q) {
+      const int k = k0 + ty * 4 + q;
+      if (k >= nt) break;
+      const int slot = slot_s[ty * 4 + q];
+      const double* L = a.t.gate_l + ((size_t)b * T + slot) * 16;
+      const double* zh = a.t.gate_z + ((size_t)b * T + slot) * 4;
+      double w[4], d2 = 0.0;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      double v = z[i] - zh[i];
+      for (int i = 0; i < 4; ++i) {
+        double v = z[i] - zh[i];
 #pragma unroll
-      for (int c = 0; c < i; ++c) v -= L[i * 4 + c] * w[c];
-      w[i] = v / L[i * 4 + i];
+        for (int c = 0; c < i; ++c) v -= L[i * 4 + c] * w[c];
+        w[i] = v / L[i * 4 + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) d2 += w[i] * w[i];
+      double cost = 1.0 - ((double)acc[q] + (double)comp[q]);
+      if (a.cascade) {   // motion-fused cost, tracks x detections row-major
+        cost = d2 > a.gate ? INF_COST : a.lam * cost + (1.0 - a.lam) * d2;
+        A[(size_t)k * D + j] = cost;
+        continue;
+      }
+      if (d2 > a.gate) cost = INF_COST;
+      if (trans)
+        A[(size_t)j * M + k] = cost;
+      else
+        A[(size_t)k * M + j] = cost;
     }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) d2 += w[i] * w[i];
-    double cost = 1.0 - ((double)acc[q] + (double)comp[q]);
-    if (a.cascade) {   // motion-fused cost, tracks x detections row-major
-      cost = d2 > a.gate ? INF_COST : a.lam * cost + (1.0 - a.lam) * d2;
-      A[(size_t)k * D + j] = cost;
-      continue;
-    }
-    if (d2 > a.gate) cost = INF_COST;
-    if (trans)
-      A[(size_t)j * M + k] = cost;
-    else
-      A[(size_t)k * M + j] = cost;
   }
 }
 
@@ -396,12 +402,26 @@ __global__ void __launch_bounds__(256) assign_kernel(StepArgs a, Slots sl) {
   __syncthreads();
   if (s_fail) flag_error(a.err, KERR_TIMEOUT);
 
-  // Kalman update of assigned tracks, lost bookkeeping (one thread per track)
-  for (int k = tid; k < nt; k += blockDim.x) {
-    const int slot = a.t.order[(size_t)s * T + k];
-    const size_t ts = (size_t)s * T + slot;
-    const int d = trk_det[k];
-    if (d >= 0) {
+  // Kalman update of assigned tracks and lost bookkeeping: eight lanes per track (four tracks per
+  // warp), lane i forming row i of the gain K, of the mean and of the covariance; every element is
+  // computed with the operations, in the order, of the one-thread form (kalman_update)
+  {
+    const int row = lane & 7;
+    const unsigned gmask = 0xFFu << (lane & 24);   // the track's eight lanes
+    for (int k0 = warp * 4; k0 < nt; k0 += (blockDim.x / 32) * 4) {
+      const int k = k0 + (lane >> 3);
+      if (k >= nt) continue;                       // the whole eight-lane group takes this branch
+      const int slot = a.t.order[(size_t)s * T + k];
+      const size_t ts = (size_t)s * T + slot;
+      const int d = trk_det[k];
+      if (d < 0) {
+        if (row == 0) {
+          a.t.state[ts] = JDE_TRACK_LOST;
+          a.t.since[ts] += 1;
+          a.t.last_det[ts] = -1;
+        }
+        continue;
+      }
       double z[4];
       measurement(rows + (size_t)d * 518, z);
       double* m = a.t.mean + ts * 8;
@@ -416,48 +436,47 @@ __global__ void __launch_bounds__(256) assign_kernel(StepArgs a, Slots sl) {
       S[5] += rp;
       S[10] += 1e-1 * 1e-1;
       S[15] += rp;
-      // K row i solves (L L^T) k = (P H^T)[i]
-      double K[32];
-      for (int i = 0; i < 8; ++i) {
+      // row `row` of K solves (L L^T) k = (P H^T)[row]
+      double Kr[4];
+      {
         double t[4];
         for (int r = 0; r < 4; ++r) {
-          double vv = P[i * 8 + r];
+          double vv = P[row * 8 + r];
           for (int c = 0; c < r; ++c) vv -= L[r * 4 + c] * t[c];
           t[r] = vv / L[r * 4 + r];
         }
         for (int r = 3; r >= 0; --r) {
           double vv = t[r];
-          for (int c = r + 1; c < 4; ++c) vv -= L[c * 4 + r] * K[i * 4 + c];
-          K[i * 4 + r] = vv / L[r * 4 + r];
+          for (int c = r + 1; c < 4; ++c) vv -= L[c * 4 + r] * Kr[c];
+          Kr[r] = vv / L[r * 4 + r];
         }
       }
       double y[4];
       for (int r = 0; r < 4; ++r) y[r] = z[r] - m[r];
-      for (int i = 0; i < 8; ++i) {
+      __syncwarp(gmask);                           // every lane has read m and P before any writes them
+      {
         double acc = 0.0;
-        for (int r = 0; r < 4; ++r) acc += K[i * 4 + r] * y[r];
-        m[i] += acc;
+        for (int r = 0; r < 4; ++r) acc += Kr[r] * y[r];
+        m[row] += acc;
       }
-      double KS[32];
-      for (int i = 0; i < 8; ++i)
-        for (int c = 0; c < 4; ++c) {
-          double acc = 0.0;
-          for (int r = 0; r < 4; ++r) acc += K[i * 4 + r] * S[r * 4 + c];
-          KS[i * 4 + c] = acc;
-        }
-      for (int i = 0; i < 8; ++i)
-        for (int j = 0; j < 8; ++j) {
-          double acc = 0.0;
-          for (int c = 0; c < 4; ++c) acc += KS[i * 4 + c] * K[j * 4 + c];
-          P[i * 8 + j] -= acc;
-        }
-      a.t.state[ts] = JDE_TRACK_TRACKED;
-      a.t.since[ts] = 0;
-      a.t.last_det[ts] = d;
-    } else {
-      a.t.state[ts] = JDE_TRACK_LOST;
-      a.t.since[ts] += 1;
-      a.t.last_det[ts] = -1;
+      double KS[4];
+      for (int c = 0; c < 4; ++c) {
+        double acc = 0.0;
+        for (int r = 0; r < 4; ++r) acc += Kr[r] * S[r * 4 + c];
+        KS[c] = acc;
+      }
+      for (int j = 0; j < 8; ++j) {
+        double Kj[4];
+        for (int c = 0; c < 4; ++c) Kj[c] = __shfl_sync(gmask, Kr[c], (lane & 24) + j);
+        double acc = 0.0;
+        for (int c = 0; c < 4; ++c) acc += KS[c] * Kj[c];
+        P[row * 8 + j] -= acc;
+      }
+      if (row == 0) {
+        a.t.state[ts] = JDE_TRACK_TRACKED;
+        a.t.since[ts] = 0;
+        a.t.last_det[ts] = d;
+      }
     }
   }
   __syncthreads();
@@ -1021,7 +1040,7 @@ int track_step(TrackState& t, const jde_config& cfg, int n, const int32_t* strea
   dim3 gp((t.max_tracks + 127) / 128, n);
   jde_count_launch();
   prep_kernel<<<gp, 128, 0, st>>>(a, sl);
-  dim3 gc((t.max_tracks + 31) / 32, (t.max_dets + 31) / 32, n);
+  dim3 gc(COST_BLOCKS, n);
   jde_count_launch();
   cost_kernel<<<gc, 256, 0, st>>>(a, sl);
   jde_count_launch();
