@@ -253,7 +253,8 @@ jde_status jde_act_amax(jde_handle* h, float* amax, void* stream);
 
 /* Tile autotuner (tensor-core handles): for batches of n frames at in_w x in_h, times every
  * built tile width (64/128/256 output channels, 32 where that is the default; 256 runs on CTA
- * pairs; for the stride-1 3x3 convs also 128 channels x 256 rows per CTA, tile code 129) of every
+ * pairs; for the stride-1 3x3 convs also 128 channels x 256 rows per CTA, tile code 129; for the
+ * other BF16 convs of 128-byte k-blocks also 128 channels on CTA pairs, tile code 130) of every
  * convolution that has more than one, on `stream` with CUDA events on the handle's
  * activation buffers (the median of five launches, each right after a launch of the layer before it,
  * so the input is as cached as in a forward), and keeps the fastest for later forwards of that shape.  Results do not
@@ -264,14 +265,15 @@ jde_status jde_autotune(jde_handle* h, int n, int in_w, int in_h, void* stream);
 
 /* Tile code used per layer (bn[JDE_NUM_LAYERS]) for batches of n at in_w x in_h: the tuned
  * choice if jde_autotune ran for that shape, else the default rule.  The code is the tile's output
- * channel count, plus 1 when each CTA computes two 128-row sub-tiles (256 rows) per tile. */
+ * channel count, plus 1 when each CTA computes two 128-row sub-tiles (256 rows) per tile, plus 2
+ * when a 128-wide tile runs on a CTA pair. */
 jde_status jde_tile_choice(jde_handle* h, int n, int in_w, int in_h, int* bn);
 
 /* Set the tile code of every layer (bn[JDE_NUM_LAYERS]; 0 = the default rule) for batches of n at
  * in_w x in_h, as jde_autotune would (e.g. to reuse its choice, read with jde_tile_choice, in
  * another process).  Plans are rebuilt on the host at once: a code a layer cannot run (a width
- * its channel count is not a multiple of, a layer with one tile shape, or code 129 where the
- * windows do not fit) returns JDE_ERR_INVALID_ARG or JDE_ERR_UNSUPPORTED and keeps the previous
+ * its channel count is not a multiple of, a layer with one tile shape, code 129 where the
+ * windows do not fit, or code 130 on a flat-window or E4M3 conv) returns JDE_ERR_INVALID_ARG or JDE_ERR_UNSUPPORTED and keeps the previous
  * choice.  Results do not change (same K order for every tile). */
 jde_status jde_set_tile_choice(jde_handle* h, int n, int in_w, int in_h, const int* bn);
 

@@ -1200,7 +1200,7 @@ int conv_tc_pick_bn(int cout) {
 }
 
 bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const void* w_any, int cout_pad, int bn, char* msg,
-                  size_t msg_len, int msub) {
+                  size_t msg_len, int msub, int pair128) {
   const __nv_bfloat16* w = static_cast<const __nv_bfloat16*>(w_any);
   plan = TcPlan();
   plan.spec = c;
@@ -1416,6 +1416,13 @@ bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const void* w_any, int cout_p
   // 256-wide tiles run on CTA pairs (M = 256 per MMA, each CTA loads half of B)
   // CTA pairs: 256-wide tiles, and every flat-window tile (each CTA holds half of the weight tile)
   plan.cg = (bn == 256 && (bkc == 64 || plan.mode == 4)) || (bn == 128 && plan.mode == 4) ? 2 : 1;
+  if (pair128) {
+    if (bn != 128 || bkc != 64 || q || !(plan.mode == 0 || plan.mode == 1)) {
+      snprintf(msg, msg_len, "128-wide tiles on CTA pairs: stride-1 flat or stride-2 BF16 convs of 128-byte k-blocks only");
+      return false;
+    }
+    plan.cg = 2;
+  }
   {
     cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)cout_pad};
     cuuint64_t strides[1] = {(cuuint64_t)K * ie};
@@ -1576,7 +1583,9 @@ cudaError_t conv_tc_launch(const TcPlan& p, cudaStream_t st) {
     switch (p.bn) {
       case 32: return launch_cfg<32, 64, 9>(p, a, st);
       case 64: return launch_cfg<64, 64, 6>(p, a, st);
-      case 128: return launch_cfg<128, 64, 5>(p, a, st);
+      case 128:
+        if (p.cg == 2) return launch_cfg<128, 64, 8, 1, 2>(p, a, st);
+        return launch_cfg<128, 64, 5>(p, a, st);
       case 256:
         if (p.cg == 2) return launch_cfg<256, 64, 4, 1, 2>(p, a, st);
         return launch_cfg<256, 64, 3>(p, a, st);

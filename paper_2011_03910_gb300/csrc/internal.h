@@ -60,8 +60,10 @@ struct TcPlan {
 // w: [cout_pad][K] bf16, or E4M3 codes when c.q.
 // msub = 2 (flat-window 3x3 convs with bn = 128 only): each CTA computes 256 rows x bn columns per
 // work unit, two M=128 sub-tiles sharing every weight tile and one window.
+// pair128 = 1 (stride-1 flat and stride-2 patch convs with bn = 128 only): the 128-wide tiles run on CTA
+// pairs (M = 256 per MMA, each CTA loading half of every weight tile).
 bool conv_tc_plan(TcPlan& plan, const ConvSpec& c, const void* w, int cout_pad, int bn, char* msg,
-                  size_t msg_len, int msub = 1);
+                  size_t msg_len, int msub = 1, int pair128 = 0);
 cudaError_t conv_tc_launch(const TcPlan& plan, cudaStream_t st);
 // Point a planned conv at another output buffer of the same shape (the double-buffered heads);
 // re-encodes the output tensor map of a TMA-stored f32 head.  False if the map cannot be built.

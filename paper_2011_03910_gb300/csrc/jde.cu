@@ -482,7 +482,8 @@ jde_status get_plan(jde_handle* h, ResBuffers* rb, int n, Plan** out) {
       auto tb = h->tuned_bn.find(key);
       if (tb != h->tuned_bn.end() && tb->second[l] > 0) bn = tb->second[l];
       // tile code: output channels per tile, + 1 for two 128-row M sub-tiles per CTA (flat-window 3x3)
-      if (!conv_tc_plan(p.tc[l], c, w, h->w[l].cout_pad_tc, bn & ~1, msg, sizeof(msg), (bn & 1) ? 2 : 1))
+      if (!conv_tc_plan(p.tc[l], c, w, h->w[l].cout_pad_tc, bn & ~3, msg, sizeof(msg), (bn & 1) ? 2 : 1,
+                        (bn & 2) ? 1 : 0))
         return fail(h, JDE_ERR_UNSUPPORTED, "layer %zu: %s", l, msg);
       p.tc[l].pdl = h->cfg.dependent_launch;
     }
@@ -1283,13 +1284,13 @@ jde_status jde_autotune(jde_handle* h, int n, int in_w, int in_h, void* stream) 
     const LayerW& lw = h->w[l];
     const void* w = lw.q ? static_cast<const void*>(lw.w_q) : static_cast<const void*>(lw.w_nk);
     float best_ms = 1e30f;
-    for (int code : {32, 64, 128, 256, 129}) {
-      const int bn = code & ~1, msub = (code & 1) ? 2 : 1;
+    for (int code : {32, 64, 128, 256, 129, 130}) {
+      const int bn = code & ~3, msub = (code & 1) ? 2 : 1, pair128 = (code & 2) ? 1 : 0;
       // 32-wide tiles only where they are the default (the 24-channel heads, 32-channel outputs)
       if (lw.cout_pad_tc % bn || (bn == 32 && lw.bn != 32)) continue;
       TcPlan cand;
       char msg[256];
-      if (!conv_tc_plan(cand, plan->specs[l], w, lw.cout_pad_tc, bn, msg, sizeof(msg), msub)) continue;
+      if (!conv_tc_plan(cand, plan->specs[l], w, lw.cout_pad_tc, bn, msg, sizeof(msg), msub, pair128)) continue;
       // same addressing mode and k-block width: the same order of the K sum
       if (cand.mode != def.mode || cand.bkc != def.bkc || cand.msub != msub) continue;
       if (msub == 2 && !cand.tma_out) continue;
@@ -1331,7 +1332,8 @@ jde_status jde_set_tile_choice(jde_handle* h, int n, int in_w, int in_h, const i
     return fail(h, JDE_ERR_INVALID_ARG, "jde_set_tile_choice: bad arguments");
   std::vector<int> codes(bn, bn + JDE_NUM_LAYERS);
   for (int l = 0; l < JDE_NUM_LAYERS; ++l)
-    if (!(codes[l] == 0 || codes[l] == 32 || codes[l] == 64 || codes[l] == 128 || codes[l] == 256 || codes[l] == 129))
+    if (!(codes[l] == 0 || codes[l] == 32 || codes[l] == 64 || codes[l] == 128 || codes[l] == 256 || codes[l] == 129 ||
+          codes[l] == 130))
       return fail(h, JDE_ERR_INVALID_ARG, "jde_set_tile_choice: layer %d: tile code %d", l, codes[l]);
   ResBuffers* rb;
   jde_status s = get_res(h, in_w, in_h, &rb);
@@ -1357,8 +1359,8 @@ jde_status jde_set_tile_choice(jde_handle* h, int n, int in_w, int in_h, const i
       const LayerW& lw = h->w[l];
       const void* w = lw.q ? static_cast<const void*>(lw.w_q) : static_cast<const void*>(lw.w_nk);
       const bool def_ok = conv_tc_plan(def, plan->specs[l], w, lw.cout_pad_tc, lw.bn, msg, sizeof(msg));
-      if (t.bn != (codes[l] & ~1) || t.msub != ((codes[l] & 1) ? 2 : 1) || !def_ok || def.mode != t.mode ||
-          def.bkc != t.bkc)
+      if (t.bn != (codes[l] & ~3) || t.msub != ((codes[l] & 1) ? 2 : 1) || ((codes[l] & 2) && t.cg != 2) || !def_ok ||
+          def.mode != t.mode || def.bkc != t.bkc)
         s = fail(h, JDE_ERR_UNSUPPORTED, "jde_set_tile_choice: layer %d cannot run tile code %d", l, codes[l]);
     }
   }

@@ -42,7 +42,7 @@ def test_autotuned_forward_is_bit_identical(fp8):
         default = j.jde_tile_choice(h, 2, 320, 192)
         j.jde_autotune(h, 2, 320, 192, torch.cuda.current_stream())
         tuned = j.jde_tile_choice(h, 2, 320, 192)
-        assert all(b in (32, 64, 128, 256, 129) for b in tuned)
+        assert all(b in (32, 64, 128, 256, 129, 130) for b in tuned)
         print("tile widths changed on", sum(a != b for a, b in zip(default, tuned)), "layers:", tuned)
         after = _layer_outputs(j, h, frames)
         for l, (a, b) in enumerate(zip(before, after)):
@@ -98,6 +98,44 @@ def test_two_m_subtiles_per_cta_are_bit_identical(fp8, size):
         j.jde_destroy(h)
 
 
+@pytest.mark.parametrize("size", [(320, 192), (1088, 608)])
+def test_128_wide_tiles_on_cta_pairs_are_bit_identical(size):
+    """Code 130 runs a 128-wide BF16 tile of a stride-1 flat or stride-2 conv on a CTA pair (M = 256 per
+    MMA, each CTA loading half of every weight tile); every output is the same K sum in the same order,
+    so every layer is bit-identical to the default tiles.  Layers that take it are found by asking
+    jde_set_tile_choice layer by layer; flat-window 3x3 convs refuse it."""
+    j = jde()
+    in_w, in_h = size
+    n = 2 if in_w == 320 else 1
+    h = make_handle(j.JDE_BF16, max_batch=n, in_w=in_w, in_h=in_h, src_w=in_w, src_h=in_h, keep_layer_outputs=1)
+    try:
+        frames = synth.frames_uniform(5, n, in_h, in_w)
+        before = _layer_outputs(j, h, frames, in_w, in_h)
+        base = j.jde_tile_choice(h, n, in_w, in_h)
+        codes = list(base)
+        table = j.jde_layer_table()
+        for l, (cin, cout, k, stride, _, _) in enumerate(table):
+            if cout % 128 or cin % 64:
+                continue
+            trial = list(base)
+            trial[l] = 130
+            try:
+                j.jde_set_tile_choice(h, n, in_w, in_h, trial)
+            except j.JdeError:
+                assert k == 3 and stride == 1 or l < 2, l   # only flat-window convs (and the fused stem) refuse
+                continue
+            codes[l] = 130
+        j.jde_set_tile_choice(h, n, in_w, in_h, base)
+        assert sum(c == 130 for c in codes) >= 10
+        j.jde_set_tile_choice(h, n, in_w, in_h, codes)
+        assert j.jde_tile_choice(h, n, in_w, in_h) == codes
+        after = _layer_outputs(j, h, frames, in_w, in_h)
+        for l, (a, b) in enumerate(zip(before, after)):
+            np.testing.assert_array_equal(a, b, err_msg=f"layer {l} (code {codes[l]})")
+    finally:
+        j.jde_destroy(h)
+
+
 def test_set_tile_choice_refuses_codes_a_layer_cannot_run():
     j = jde()
     h = make_handle(j.JDE_BF16, max_batch=2, src_w=320, src_h=192)
@@ -105,6 +143,10 @@ def test_set_tile_choice_refuses_codes_a_layer_cannot_run():
         codes = j.jde_tile_choice(h, 2, 320, 192)
         bad = list(codes)
         bad[5] = 129                       # a 1x1 conv has no flat-window form
+        with pytest.raises(j.JdeError):
+            j.jde_set_tile_choice(h, 2, 320, 192, bad)
+        bad = list(codes)
+        bad[6] = 130                       # a flat-window 3x3 conv has no CTA-pair 128-wide form
         with pytest.raises(j.JdeError):
             j.jde_set_tile_choice(h, 2, 320, 192, bad)
         bad = list(codes)
