@@ -37,7 +37,7 @@ STRIDES = (32, 16, 8)
 METRIC = "JDE FPS at 1088x608: BF16/FP8 batched vs FP32 plain on one GB300; p99 latency"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the 78 conv launches of one BF16
 # batch-16 step, from one ncu capture of this build; re-take it (or set None) when the conv kernels change
-CONV_DRAM_BYTES_PER_STEP = 8.458e9   # ncu dram__bytes_read.sum + dram__bytes_write.sum, 77 conv launches, autotuned tiles
+CONV_DRAM_BYTES_PER_STEP = 8.462e9   # ncu dram__bytes_read.sum + dram__bytes_write.sum, 77 conv launches, autotuned tiles
 CONV_DRAM_SOURCE = "profiles/dram_bf16_b16_1088x608.md (autotuned tiles, the profiled step of this bench)"
 
 
