@@ -53,6 +53,16 @@ def test_create_rejects_bad_config_without_gpu(jde):
     jde.jde_destroy(None)      # NULL is a no-op
 
 
+def test_dependent_launch_option_is_validated_without_gpu(jde):
+    c = jde.jde_default_config()
+    assert c.dependent_launch == 1 and c.fuse_block1 == 0
+    c.dependent_launch = 2     # only 0 or 1: rejected before any CUDA call
+    with pytest.raises(jde.JdeError) as e:
+        jde.jde_create(c, b"JDEW")
+    assert e.value.status == 1
+    assert jde.lib.jde_set_dependent_launch(None, 1) == 1     # NULL handle: JDE_ERR_INVALID_ARG
+
+
 def test_binding_structs_match_the_header_layout(jde, tmp_path):
     """The ctypes structures of the binding have the sizes and field offsets the C compiler gives the
     header's structs (compiled here with gcc against include/jde.h)."""
