@@ -277,9 +277,10 @@ __device__ __forceinline__ void argmin_warp(double& v, int& j) {
 // Shortest-augmenting-path Hungarian with row and column potentials on the R x M cost matrix A
 // (row-major, R <= M), run by one warp.  On return p[j] is the 1-based row assigned to column j (0 =
 // none).  Columns are scanned in ascending order and the first minimum wins.  Returns false when a step
-// finds no finite free column (the matrix holds NaN).
-__device__ bool hungarian_warp(const double* A, int R, int M, double* u, double* v, double* minv, int* p, int* way,
-                               uint8_t* used) {
+// finds no finite free column (the matrix holds NaN).  This form keeps every column's state in shared
+// memory (any M); hungarian_warp_reg keeps it in the registers of the column's lane.
+__device__ bool hungarian_warp_smem(const double* A, int R, int M, double* u, double* v, double* minv, int* p, int* way,
+                                    uint8_t* used) {
   const int lane = threadIdx.x & 31;
   for (int j = lane; j <= M; j += 32) {
     v[j] = 0.0;
@@ -348,6 +349,103 @@ __device__ bool hungarian_warp(const double* A, int R, int M, double* u, double*
     __syncwarp();
   }
   return !fail;
+}
+
+// The same algorithm with the state of column j (1-based) held by lane (j - 1) % 32 in registers: its
+// potential v, its slack minv and whether it is used; way and p stay in shared memory (lane 0 walks
+// them to augment, every lane reads p for the row potentials).  Columns are visited, compared and
+// updated with the same operations in the same order as in hungarian_warp_smem, so the assignment is
+// the same.  M <= 32 * CPL.
+template <int CPL>
+__device__ bool hungarian_warp_reg(const double* A, int R, int M, double* u, int* p, int* way) {
+  const int lane = threadIdx.x & 31;
+  double vr[CPL], mr[CPL];
+  bool ur[CPL];
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) vr[c] = 0.0;
+  for (int j = lane; j <= M; j += 32) {
+    p[j] = 0;
+    way[j] = 0;
+  }
+  for (int i = lane; i <= R; i += 32) u[i] = 0.0;
+  __syncwarp();
+  bool fail = false;
+  for (int i = 1; i <= R && !fail; ++i) {
+    if (lane == 0) p[0] = i;
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+      mr[c] = INFINITY;
+      ur[c] = false;
+    }
+    __syncwarp();
+    int j0 = 0;
+    for (int iter = 0; iter <= M; ++iter) {
+      if (j0 > 0 && ((j0 - 1) & 31) == lane) {   // column j0 becomes used (column 0 always is)
+#pragma unroll
+        for (int c = 0; c < CPL; ++c)
+          if (c == ((j0 - 1) >> 5)) ur[c] = true;
+      }
+      const int i0 = p[j0];
+      const double ui0 = u[i0];
+      const double* arow = A + (size_t)(i0 - 1) * M;
+      double best = INFINITY;
+      int bestj = 0x7fffffff;
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) {
+        const int j = lane + 1 + 32 * c;
+        if (j <= M && !ur[c]) {
+          const double cur = (arow[j - 1] - ui0) - vr[c];
+          if (cur < mr[c]) {
+            mr[c] = cur;
+            way[j] = j0;
+          }
+          if (mr[c] < best) {
+            best = mr[c];
+            bestj = j;
+          }
+        }
+      }
+      argmin_warp(best, bestj);
+      if (bestj == 0x7fffffff) {   // no finite free column
+        fail = true;
+        break;
+      }
+      const double delta = best;
+      if (lane == 0) u[p[0]] += delta;   // column 0 (the row being added) is used
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) {
+        const int j = lane + 1 + 32 * c;
+        if (j > M) continue;
+        if (ur[c]) {
+          u[p[j]] += delta;
+          vr[c] -= delta;
+        } else {
+          mr[c] -= delta;
+        }
+      }
+      __syncwarp();
+      j0 = bestj;
+      if (p[j0] == 0) break;
+    }
+    __syncwarp();
+    if (lane == 0 && !fail) {
+      int jj = j0;
+      for (int guard = 0; guard <= M && jj; ++guard) {
+        const int j1 = way[jj];
+        p[jj] = p[j1];
+        jj = j1;
+      }
+    }
+    __syncwarp();
+  }
+  return !fail;
+}
+
+__device__ bool hungarian_warp(const double* A, int R, int M, double* u, double* v, double* minv, int* p, int* way,
+                               uint8_t* used) {
+  if (M <= 64) return hungarian_warp_reg<2>(A, R, M, u, p, way);
+  if (M <= 128) return hungarian_warp_reg<4>(A, R, M, u, p, way);
+  return hungarian_warp_smem(A, R, M, u, v, minv, p, way, used);
 }
 
 __global__ void __launch_bounds__(256) assign_kernel(StepArgs a, Slots sl) {
